@@ -1,0 +1,174 @@
+/*
+ * tsqr.h — C ABI of the GB300 (sm_103a) tall-skinny QR library.
+ *
+ * The library computes the QR factorization A = Q R of a tall, skinny, column-major
+ * m-by-n FP64 matrix (m >= n, n <= 128) by TSQR, "Tall and Skinny QR": the rows are
+ * split into P block-rows ("domains", the leaves), each leaf is factored by
+ * Householder reflections, and the leaves' n-by-n triangular R factors are reduced
+ * by a tree whose basic operation is the QR factorization of stacked triangles
+ * (paper §2.3). The reduce operator is associative, so every tree shape yields the
+ * same R; the library returns R with a non-negative diagonal, which makes it unique
+ * for full-rank A (paper §2.2). Q is kept implicitly as the set of Householder
+ * reflectors H = I - tau v v^T of every leaf and tree node (paper §2.2), and can be
+ * applied (Q^T B, Q B) or formed explicitly (thin Q, paper §4 Table 2 / Property 1).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major: element (i, j) of X is X[i + j*ldx], ldx >= rows.
+ *   - Pointers to matrix data are DEVICE pointers (memory allocated by the caller,
+ *     e.g. through PyTorch or cudaMalloc) unless an entry point says otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Every call is stream-ordered and asynchronous: it returns after enqueuing the
+ *     work; results are valid once the stream reaches that point. Argument errors are
+ *     detected on the host and returned before anything is enqueued.
+ *   - The caller owns A, B, R, Q, X. The library owns a tsqr_factors object until
+ *     tsqr_free(). A factor set must only be used on the device it was created on.
+ *   - Numerical range: entries are squared without rescaling, so matrices with
+ *     entries of magnitude above about 1e150 or columns whose squared norms
+ *     underflow (below about 1e-300) are outside the supported range.
+ */
+#ifndef TSQR_H
+#define TSQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSQR_OK = 0,
+  TSQR_ERR_ARG = 1,         /* invalid argument (see each entry point) */
+  TSQR_ERR_OOM = 2,         /* device allocation failed */
+  TSQR_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  TSQR_ERR_SINGULAR = 4,    /* least squares: R has an exactly zero diagonal entry */
+  TSQR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  TSQR_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve */
+} tsqr_status;
+
+typedef enum {
+  TSQR_FP64 = 0,  /* every operation in FP64 */
+  TSQR_MIXED = 1  /* leaves in FP32 (3xTF32 tensor-core updates), tree and
+                     refinement in FP64 (least squares only) */
+} tsqr_prec;
+
+/* flags for tsqr_factor */
+enum {
+  TSQR_INPLACE = 1,   /* the reflectors overwrite A (A is then not const) */
+  TSQR_TWO_LEVEL = 2  /* two-level tree: a flat chain over the leaves inside each
+                         CTA, then the arity-k tree across CTAs (the GPU form of the
+                         paper's topology-aware tree, §2.3 and §3) */
+};
+
+typedef struct tsqr_factors tsqr_factors; /* opaque factor set */
+
+/*
+ * tsqr_factor — TSQR factorization A = Q R (paper §2.3; reflectors §2.2).
+ *
+ *   A       device, m-by-n column-major FP64, leading dimension lda >= m. Read only,
+ *           unless flags has TSQR_INPLACE, in which case it receives the reflectors.
+ *   m, n    1 <= n <= 128, m >= n.
+ *   leaf_h  rows per leaf (domain), n <= leaf_h. P = max(1, floor(m / leaf_h)) leaves;
+ *           the last leaf takes the remaining m - (P-1)*leaf_h rows. A leaf taller
+ *           than the on-chip tile limit is itself factored as a flat chain of tiles.
+ *   arity   tree over the leaves (or over the CTA chains with TSQR_TWO_LEVEL):
+ *           2..16 = k-ary tree, level by level, consecutive siblings grouped;
+ *           0 = flat tree (one left-to-right chain). A trailing group of size one
+ *           passes up unchanged.
+ *   prec    TSQR_FP64 only (TSQR_MIXED is accepted by tsqr_lstsq).
+ *   flags   TSQR_INPLACE | TSQR_TWO_LEVEL.
+ *   stream  cudaStream_t.
+ *   F       out: the new factor set (host pointer to an opaque handle).
+ *   R       device, n-by-n column-major, ldr >= n, out: the R factor with
+ *           diag(R) >= 0 (sign(0) = +1) and zeros below the diagonal. May be NULL.
+ *   Errors: TSQR_ERR_ARG for n < 1, n > 128, m < n, leaf_h < n, lda < m, ldr < n,
+ *           arity not in {0, 2..16}, null A or F, unknown prec/flags;
+ *           TSQR_ERR_UNSUPPORTED for prec = TSQR_MIXED; TSQR_ERR_OOM; TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h,
+                        int32_t arity, int32_t prec, int32_t flags, void *stream,
+                        tsqr_factors **F, double *R, int64_t ldr);
+
+/*
+ * tsqr_apply_qt — B <- Q^T B for the m-by-m orthogonal Q of F (paper §4, Table 2).
+ *   B  device, m-by-k column-major, ldb >= m, 1 <= k. Rows 0..n-1 of the result are
+ *      Q_thin^T B with the sign convention diag(R) >= 0; the other rows hold B's
+ *      coordinates in an orthogonal complement that depends on the tree.
+ *   Errors: TSQR_ERR_ARG (null F/B, k < 1, ldb < m), TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k,
+                          void *stream);
+
+/* tsqr_apply_q — B <- Q B (the inverse of tsqr_apply_qt). Same arguments. */
+tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t k,
+                         void *stream);
+
+/*
+ * tsqr_form_q — the thin Q = Q [I_n; 0] (m-by-n, orthonormal columns) with
+ * A = Q R and diag(R) >= 0 (paper §4, Property 1: "Q and R" costs about twice "R").
+ *   Q  device, m-by-n column-major, ldq >= m, out.
+ */
+tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *stream);
+
+/*
+ * tsqr_lstsq — X = argmin ||A X - B||_F column by column: X = R^{-1} (Q^T B)[0:n].
+ *   A          device m-by-n (lda >= m), not modified.
+ *   B          device m-by-k (ldb >= m, 1 <= k <= 64), not modified.
+ *   X          device n-by-k (ldx >= n), out.
+ *   leaf_h, arity, flags as in tsqr_factor (TSQR_INPLACE is ignored).
+ *   prec       TSQR_FP64: FP64 TSQR of [A | B] (Q^T B fused into the factorization),
+ *              then back substitution.
+ *              TSQR_MIXED: FP32 leaf factorizations, FP64 tree, and FP64 augmented-
+ *              system iterative refinement (at most max_refine corrections).
+ *   info       host array of length max_refine + 1 or NULL: info[s] = ||dX||_F/||X||_F
+ *              after correction s (TSQR_MIXED), info[0] = 0 for TSQR_FP64. Filling it
+ *              synchronizes the stream.
+ *   Errors: TSQR_ERR_ARG, TSQR_ERR_SINGULAR (some r_jj == 0; X is then undefined),
+ *           TSQR_ERR_OOM, TSQR_ERR_CUDA. Detecting a singular R synchronizes the
+ *           stream.
+ */
+tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const double *B,
+                       int64_t ldb, int32_t k, double *X, int64_t ldx, int32_t leaf_h,
+                       int32_t arity, int32_t prec, int32_t flags, int32_t max_refine,
+                       void *stream, double *info);
+
+/* tsqr_free — releases F (stream-ordered on the stream F was created on). NULL is
+ * accepted. */
+tsqr_status tsqr_free(tsqr_factors *F);
+
+/* tsqr_factors_info — host-side description of F: out[0] = m, out[1] = n,
+ * out[2] = number of leaves P, out[3] = tile rows, out[4] = number of jobs,
+ * out[5] = number of tiles, out[6] = number of kernel launches of a factorization,
+ * out[7] = CTAs per SM of the factor kernel. `out` is a host array of 8 int64. */
+tsqr_status tsqr_factors_info(const tsqr_factors *F, int64_t *out);
+
+/*
+ * tsqr_plan_describe — host only, touches no GPU: the leaf partition and reduction
+ * tree tsqr_factor (nc = n) or the fused least-squares factorization (nc = n + k)
+ * would build on a device with `sms` SMs and the given shared-memory sizes in bytes
+ * (per SM, reserved per block, opt-in maximum per block).
+ *   out       host int64[8], as tsqr_factors_info.
+ *   tiles     host int64 array of 5*max_tiles or NULL: for tile t in execution order
+ *             {row0, rows, kind (0 leaf QR, 1 triangle-on-tile, 2 triangle-on-triangle),
+ *             job, launch}.
+ *   jobs      host int64 array of 4*max_jobs or NULL: {pivot row, first tile, tiles, launch}.
+ * Errors: TSQR_ERR_ARG as tsqr_factor, or when max_tiles / max_jobs is too small while
+ * the array is non-NULL (out is filled first so the caller can size the arrays).
+ */
+tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h, int32_t arity,
+                               int32_t flags, int32_t sms, int64_t smem_per_sm,
+                               int64_t smem_reserved, int64_t smem_optin, int64_t *out,
+                               int64_t *tiles, int64_t max_tiles, int64_t *jobs,
+                               int64_t max_jobs);
+
+/* tsqr_strerror — static description of a status code. */
+const char *tsqr_strerror(tsqr_status s);
+
+/* tsqr_last_error — host string describing the last error of the calling thread
+ * (empty when none). */
+const char *tsqr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSQR_H */

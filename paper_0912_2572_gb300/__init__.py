@@ -1,0 +1,158 @@
+"""GB300 (sm_103a) tall-skinny QR — Python binding of the C-ABI library libtsqr.so.
+
+TSQR (paper §2.3): the rows of a tall m-by-n matrix are split into leaves (domains),
+each leaf is factored by Householder reflections (paper §2.2), and the leaves' R factors
+are reduced by a tree whose operator is "QR of stacked triangles, keep R". The same
+names as the C ABI (include/tsqr.h): factor, apply_qt, apply_q, form_q, lstsq.
+
+This module only marshals arguments: PyTorch provides device memory and the current
+stream; every step of the computation runs in the library's CUDA kernels. Matrices are
+column-major float64 CUDA tensors of shape (rows, cols) with stride(0) == 1; use
+``colmajor`` to obtain one.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+
+__all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
+           "TSQRError"]
+
+FP64 = 0
+MIXED = 1
+INPLACE = 1
+TWO_LEVEL = 2
+TSQRError = _lib.TSQRError
+
+
+def colmajor(t):
+    """A column-major (Fortran-ordered) copy of a 2-D tensor, or t itself if it already is."""
+    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_mat(t, name, rows=None, cols=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 CUDA tensor")
+    if t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); use colmajor()")
+    if rows is not None and t.shape[0] != rows:
+        raise ValueError(f"{name} has {t.shape[0]} rows, expected {rows}")
+    if cols is not None and t.shape[1] != cols:
+        raise ValueError(f"{name} has {t.shape[1]} columns, expected {cols}")
+    return max(t.stride(1), max(1, t.shape[0]))
+
+
+class Factors:
+    """A factor set: the implicit Q (reflectors of every leaf and tree node) and R."""
+
+    def __init__(self, handle, m, n, R, A_ref, stream):
+        self._h = handle
+        self.m, self.n = m, n
+        self.R = R
+        self._A_ref = A_ref  # keeps in-place reflector storage alive
+        self._stream = stream
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        _lib.check(_lib.load().tsqr_factors_info(self._h, out), "tsqr_factors_info")
+        keys = ["m", "n", "leaves", "tile_rows", "jobs", "tiles", "launches", "ctas_per_sm"]
+        return dict(zip(keys, list(out)))
+
+    def apply_qt(self, B, stream=None):
+        """B <- Q^T B in place (B: m-by-k column-major)."""
+        ldb = _check_mat(B, "B", rows=self.m)
+        _lib.check(_lib.load().tsqr_apply_qt(self._h, B.data_ptr(), ldb, B.shape[1], _stream(stream)),
+                   "tsqr_apply_qt")
+        return B
+
+    def apply_q(self, B, stream=None):
+        """B <- Q B in place."""
+        ldb = _check_mat(B, "B", rows=self.m)
+        _lib.check(_lib.load().tsqr_apply_q(self._h, B.data_ptr(), ldb, B.shape[1], _stream(stream)),
+                   "tsqr_apply_q")
+        return B
+
+    def form_q(self, Q=None, stream=None):
+        """The thin Q (m-by-n, orthonormal columns, A = Q R with diag(R) >= 0)."""
+        import torch
+        if Q is None:
+            Q = torch.empty((self.n, self.m), dtype=torch.float64, device="cuda").t()
+        ldq = _check_mat(Q, "Q", rows=self.m, cols=self.n)
+        _lib.check(_lib.load().tsqr_form_q(self._h, Q.data_ptr(), ldq, _stream(stream)), "tsqr_form_q")
+        return Q
+
+    def free(self):
+        if self._h:
+            _lib.load().tsqr_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace: bool = False,
+           R=None, stream=None) -> Factors:
+    """TSQR factorization of a column-major m-by-n float64 CUDA tensor A (paper §2.3).
+
+    leaf_h: rows per leaf; arity: 2..16 (k-ary tree) or 0 (flat); two_level: a flat chain
+    inside each CTA followed by the arity-k tree across CTAs. Returns a Factors object
+    whose ``R`` (n-by-n, diag >= 0) is valid once the stream reaches this point.
+    """
+    import torch
+    lib = _lib.load()
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    ldr = _check_mat(R, "R", rows=n, cols=n)
+    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0)
+    h = ctypes.c_void_p()
+    st = lib.tsqr_factor(A.data_ptr(), m, n, lda, leaf_h, arity, FP64, flags, _stream(stream),
+                         ctypes.byref(h), R.data_ptr(), ldr)
+    _lib.check(st, "tsqr_factor")
+    return Factors(h, m, n, R, A if inplace else None, stream)
+
+
+def lstsq(A, B, leaf_h: int = 256, arity: int = 2, two_level: bool = True, prec: int = FP64,
+          max_refine: int = 10, X=None, stream=None, info: bool = False):
+    """X = argmin ||A X - B|| for column-major float64 CUDA tensors (A m-by-n, B m-by-k).
+
+    prec FP64: TSQR of [A | B] with Q^T B fused, then back substitution. MIXED: FP32
+    leaves, FP64 tree, FP64 iterative refinement. With ``info`` also returns the list of
+    ||dX||/||X|| per refinement step.
+    """
+    import torch
+    lib = _lib.load()
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    ldb = _check_mat(B, "B", rows=m)
+    k = B.shape[1]
+    if X is None:
+        X = torch.empty((k, n), dtype=torch.float64, device=A.device).t()
+    ldx = _check_mat(X, "X", rows=n, cols=k)
+    hist = (ctypes.c_double * (max_refine + 1))()
+    flags = TWO_LEVEL if two_level else 0
+    st = lib.tsqr_lstsq(A.data_ptr(), m, n, lda, B.data_ptr(), ldb, k, X.data_ptr(), ldx, leaf_h, arity,
+                        prec, flags, max_refine, _stream(stream), hist if info else None)
+    _lib.check(st, "tsqr_lstsq")
+    if info:
+        return X, list(hist)
+    return X

@@ -1,0 +1,287 @@
+// FP64 TSQR factorization kernel (sm_103a).
+//
+// One CTA runs one job (a chain of tiles sharing n pivot rows, see tsqr_internal.h).
+// Each tile is staged in shared memory and factored column by column with Householder
+// reflections (paper §2.2); the pivot row of reflector j is the tile's own row j (GEQRT,
+// a leaf) or row j of the job's running triangle R held in global memory (TSQRT: the
+// flat-tree step [R; tile], TTQRT: the tree combine [R; R_child], paper §2.3).
+//
+// GB300 design notes. FP64 runs on a narrow pipe (2 DFMA/clk/SM, one warp instruction
+// per 16 cycles per SM) and a warp instruction costs the same with masked lanes, so the
+// kernel keeps warps full and spends FP64 issue slots only on the update itself:
+//   * per column step j the dot products p_k = sum_i b_ij b_ik (k >= j, including the
+//     squared norm at k = j) are one fused Gram-row pass, so one reduction per step;
+//   * half-warp h owns column pairs; each lane walks 1/16 of the rows, so a value is
+//     reduced over only 16 lanes, by a transpose-reduce that spends about one DADD per
+//     value instead of four;
+//   * reflectors are stored unscaled with (tau, scale) beside them, so the update of a
+//     trailing element is exactly one DFMA: b_ik -= (tau*scale*w_k) * b_ij;
+//   * the scalar work of a step (sqrt, division) runs on one lane of warp 0 while the
+//     other CTA resident on the SM keeps the FP64 pipe busy (2 CTAs/SM by design).
+#include "tsqr_internal.h"
+
+namespace tsqr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Transpose-reduce over the 16 lanes of a half-warp: each lane holds C partial sums
+// (C a power of two <= 16). Stage s exchanges half of the values with the lane whose
+// bit (8 >> s) differs and adds, until one value is left, then plain butterflies
+// finish the sum. The lane ends with the half-warp total of value `idx`.
+template <int C>
+__device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
+  idx = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int m = 8 >> s;
+    const int cs = (C >> s) > 1 ? (C >> s) : 1;
+    if (cs > 1) {
+      const int half = cs >> 1;
+      const bool up = (hl & m) != 0;
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i) {
+        if (i < half) {
+          const double send = up ? v[i] : v[i + half];
+          const double keep = up ? v[i + half] : v[i];
+          v[i] = keep + __shfl_xor_sync(kFull, send, m);
+        }
+      }
+      if (up) idx += half;
+    } else {
+      v[0] += __shfl_xor_sync(kFull, v[0], m);
+    }
+  }
+  return v[0];
+}
+
+// Gram row of step j: Pg[c] = sum_{i in [lo,hi)} T[j][i] * T[c][i] for c in [j, nc).
+template <int C>
+__device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, int j, int nc,
+                                         int lo, int hi, int hw, int hl, int warp,
+                                         double *__restrict__ Pg) {
+  const int cb = j + hw;
+  if (j + 2 * warp >= nc) return;  // warp-uniform: no column for this warp
+  double acc[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) acc[t] = 0.0;
+  const double *Tj = T + (size_t)j * ldt;
+  for (int i = lo + hl; i < hi; i += 16) {
+    const double x = Tj[i];
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      const int c = cb + 16 * t;
+      if (c < nc) acc[t] = fma(x, T[(size_t)c * ldt + i], acc[t]);
+    }
+  }
+  int idx;
+  const double s = treduce16<C>(acc, hl, idx);
+  const int c = cb + 16 * idx;
+  if ((hl & (16 / C - 1)) == 0 && c < nc) Pg[c] = s;
+}
+
+// Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c in (j, nc), i in [lo, hi).
+template <int C>
+__device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt, int j, int nc,
+                                                int lo, int hi, int hw, int hl, int warp,
+                                                const double *__restrict__ CF) {
+  const int cb = j + 1 + hw;
+  if (j + 1 + 2 * warp >= nc) return;
+  double cf[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int c = cb + 16 * t;
+    cf[t] = (c < nc) ? CF[c] : 0.0;
+  }
+  const double *Tj = T + (size_t)j * ldt;
+  for (int i = lo + hl; i < hi; i += 16) {
+    const double x = Tj[i];
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      const int c = cb + 16 * t;
+      if (c < nc) {
+        double *q = T + (size_t)c * ldt + i;
+        *q = fma(-cf[t], x, *q);
+      }
+    }
+  }
+}
+
+template <int CMAX>
+__device__ __forceinline__ void gram_row_dispatch(const double *T, int ldt, int j, int nc, int lo,
+                                                  int hi, int hw, int hl, int warp, double *Pg) {
+  const int slots = (nc - j + 15) >> 4;
+  if (slots <= 1 || CMAX == 1) gram_row<1>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+  else if (slots <= 2 || CMAX == 2) gram_row<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+  else if (slots <= 4 || CMAX == 4) gram_row<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+  else gram_row<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+}
+
+template <int CMAX>
+__device__ __forceinline__ void update_dispatch(double *T, int ldt, int j, int nc, int lo, int hi,
+                                                int hw, int hl, int warp, const double *CF) {
+  const int slots = (nc - j - 1 + 15) >> 4;
+  if (slots <= 0) return;
+  if (slots <= 1 || CMAX == 1) trailing_update<1>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+  else if (slots <= 2 || CMAX == 2) trailing_update<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+  else if (slots <= 4 || CMAX == 4) trailing_update<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+  else trailing_update<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+}
+
+template <int CMAX>
+__global__ void __launch_bounds__(kThreads) k_factor(const FactorParams p) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = p.n, nc = p.nc, ldt = p.ldt;
+  const int ncp = (nc + 7) & ~7;
+  double *T = sm;                       // tile, column-major, nc columns of ldt rows
+  double *Pg = T + (size_t)nc * ldt;    // Gram row of the current step
+  double *CF = Pg + ncp;                // update coefficients tau*scale*w_k
+  double *PV = CF + ncp;                // staged pivot row (TSQRT / TTQRT)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hw = tid >> 4, hl = tid & 15;
+  const JobDesc job = p.jobs[p.job0 + blockIdx.x];
+  const int64_t pr = job.piv_row;
+
+  // pivot-row element (row pr + j, column c) in global memory
+  auto piv_ptr = [&](int j, int c) -> double * {
+    return (c < n) ? p.V + pr + j + (int64_t)c * p.ldv : p.B + pr + j + (int64_t)(c - n) * p.ldb;
+  };
+  constexpr int PFN = (CMAX * 16 + 31) / 32;
+
+  for (int tt = 0; tt < job.tile_count; ++tt) {
+    const TileDesc td = p.tiles[job.tile_begin + tt];
+    const int ht = td.nrows, kind = td.kind;
+    const int64_t r0 = td.row0;
+    const bool ge = (kind == GEQRT);
+
+    // stage the tile: GEQRT/TSQRT tiles come from A (first touch), TTQRT from V
+    for (int c = warp; c < nc; c += kThreads / 32) {
+      const double *src = (c < n) ? ((kind == TTQRT) ? p.V + r0 + (int64_t)c * p.ldv
+                                                     : p.A + r0 + (int64_t)c * p.lda)
+                                  : p.B + r0 + (int64_t)(c - n) * p.ldb;
+      double *dst = T + (size_t)c * ldt;
+      for (int i = lane; i < ht; i += 32) dst[i] = src[i];
+    }
+    if (!ge)
+      for (int c = tid; c < nc; c += kThreads) PV[c] = __ldcg(piv_ptr(0, c));
+    __syncthreads();
+
+    for (int j = 0; j < n; ++j) {
+      int lo, hi;
+      refl_rows(kind, j, ht, lo, hi);
+      // warp 1 prefetches pivot row j+1 (not written before step j+1)
+      double pf[PFN];
+      const bool do_pf = (!ge) && warp == 1 && (j + 1 < n);
+      if (do_pf) {
+#pragma unroll
+        for (int q = 0; q < PFN; ++q) {
+          const int c = j + 1 + lane + 32 * q;
+          pf[q] = (c < nc) ? __ldcg(piv_ptr(j + 1, c)) : 0.0;
+        }
+      }
+
+      gram_row_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+      __syncthreads();
+
+      if (warp == 0) {
+        double tau = 0.0, scale = 0.0, beta = 0.0;
+        if (lane == 0) {
+          const double alpha = ge ? T[(size_t)j * ldt + j] : PV[j];
+          const double s2 = Pg[j];
+          beta = alpha;
+          if (s2 != 0.0) {
+            const double nrm = sqrt(fma(alpha, alpha, s2));
+            beta = (alpha < 0.0) ? nrm : -nrm;  // -sign(alpha)*||x||, sign(0) = +1
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+          }
+        }
+        tau = __shfl_sync(kFull, tau, 0);
+        scale = __shfl_sync(kFull, scale, 0);
+        beta = __shfl_sync(kFull, beta, 0);
+        const double ts = tau * scale;
+        for (int c = j + 1 + lane; c < nc; c += 32) {
+          const double pk = ge ? T[(size_t)c * ldt + j] : PV[c];
+          const double w = fma(scale, Pg[c], pk);  // v^T x over pivot row + tail
+          const double npk = fma(-tau, w, pk);
+          CF[c] = ts * w;
+          if (ge)
+            T[(size_t)c * ldt + j] = npk;
+          else
+            *piv_ptr(j, c) = npk;
+        }
+        if (lane == 0) {
+          if (ge)
+            T[(size_t)j * ldt + j] = beta;
+          else
+            *piv_ptr(j, j) = beta;
+          p.tau[td.refl + j] = tau;
+          p.scl[td.refl + j] = scale;
+        }
+      }
+      __syncthreads();
+
+      update_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+      if (do_pf) {
+#pragma unroll
+        for (int q = 0; q < PFN; ++q) {
+          const int c = j + 1 + lane + 32 * q;
+          if (c < nc) PV[c] = pf[q];
+        }
+      }
+      __syncthreads();
+    }
+
+    // write the tile back: GEQRT -> R above / V below the diagonal, TSQRT -> dense
+    // reflector tails, TTQRT -> the upper triangle only (the child's own leaf
+    // reflectors live below its diagonal)
+    for (int c = warp; c < nc; c += kThreads / 32) {
+      double *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
+      const double *src = T + (size_t)c * ldt;
+      const int lim = (kind == TTQRT && c < n) ? min(ht, c + 1) : ht;
+      for (int i = lane; i < lim; i += 32) dst[i] = src[i];
+    }
+    __syncthreads();
+  }
+}
+
+template <int CMAX>
+cudaError_t launch_factor_t(const FactorParams &p, int njobs, cudaStream_t s) {
+  const size_t bytes = factor_smem_bytes(p.nc, p.ldt);
+  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_factor<CMAX><<<njobs, kThreads, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t factor_smem_bytes(int nc, int ldt) {
+  const size_t ncp = (size_t)((nc + 7) & ~7);
+  return sizeof(double) * ((size_t)nc * (size_t)ldt + 3 * ncp);
+}
+
+int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
+                    size_t optin_per_block) {
+  if (ctas_per_sm < 1) return 0;
+  size_t per_cta = smem_per_sm / (size_t)ctas_per_sm;
+  if (per_cta <= reserved_per_block) return 0;
+  per_cta -= reserved_per_block;
+  if (per_cta > optin_per_block) per_cta = optin_per_block;
+  const size_t extra = factor_smem_bytes(nc, 0);
+  if (per_cta <= extra) return 0;
+  int rows = (int)((per_cta - extra) / (sizeof(double) * (size_t)nc));
+  return rows & ~7;
+}
+
+cudaError_t launch_factor(const FactorParams &p, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  if (p.nc <= 16) return launch_factor_t<1>(p, njobs, s);
+  if (p.nc <= 32) return launch_factor_t<2>(p, njobs, s);
+  if (p.nc <= 64) return launch_factor_t<4>(p, njobs, s);
+  return launch_factor_t<8>(p, njobs, s);
+}
+
+}  // namespace tsqr

@@ -1,0 +1,87 @@
+// Small kernels around the TSQR path (sm_103a): sign normalisation of R (paper §2.2:
+// the factorization is unique once diag(R) > 0), the sign scaling of Q^T B / Q B, the
+// root block of the thin-Q formation, and the triangular solve of least squares.
+#include "tsqr_internal.h"
+
+namespace tsqr {
+namespace {
+
+// d_j = sign(R_jj) (sign(0) = +1); R_out = D * R (upper), zeros below the diagonal.
+__global__ void k_extract_r(const double *__restrict__ V, int64_t ldv, int n, double *R, int64_t ldr,
+                            double *d) {
+  const int j = blockIdx.x;  // column
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = (V[i + (int64_t)i * ldv] < 0.0) ? -1.0 : 1.0;
+    if (j == 0 && d) d[i] = di;
+    if (R) R[i + (int64_t)j * ldr] = (i <= j) ? di * V[i + (int64_t)j * ldv] : 0.0;
+  }
+}
+
+// rows 0..n-1 of B (k columns) <- D * rows
+__global__ void k_scale_rows(double *B, int64_t ldb, int n, int k, const double *__restrict__ d) {
+  const int c = blockIdx.x;
+  if (c >= k) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) B[i + (int64_t)c * ldb] *= d[i];
+}
+
+// rows 0..n-1 of Q <- diag(d) (the root block of Q [I_n; 0] with the sign convention)
+__global__ void k_formq_init(double *Q, int64_t ldq, int n, const double *__restrict__ d) {
+  const int j = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Q[i + (int64_t)j * ldq] = (i == j) ? d[j] : 0.0;
+}
+
+// X(:, c) = R^{-1} C(:, c) by back substitution, one CTA per right-hand side. R is the
+// upper triangle of an n-by-n block (n <= 1024). A zero pivot sets *status = 4.
+__global__ void k_trsv(const double *__restrict__ R, int64_t ldr, int n, const double *__restrict__ C,
+                       int64_t ldc, double *X, int64_t ldx, int32_t *status) {
+  extern __shared__ double xs[];
+  const int c = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = C[i + (int64_t)c * ldc];
+  __syncthreads();
+  __shared__ double xi_s;
+  for (int i = n - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      const double rii = R[i + (int64_t)i * ldr];
+      if (rii == 0.0) {
+        if (status) atomicExch(status, 4);
+        xi_s = 0.0;
+      } else {
+        xi_s = xs[i] / rii;
+      }
+      xs[i] = xi_s;
+    }
+    __syncthreads();
+    const double xi = xi_s;
+    for (int t = threadIdx.x; t < i; t += blockDim.x) xs[t] = fma(-R[t + (int64_t)i * ldr], xi, xs[t]);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[i + (int64_t)c * ldx] = xs[i];
+}
+
+}  // namespace
+
+cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr, double *d,
+                             cudaStream_t s) {
+  k_extract_r<<<n, 128, 0, s>>>(V, ldv, n, R, ldr, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double *d, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_scale_rows<<<k, 128, 0, s>>>(B, ldb, n, k, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s) {
+  k_formq_init<<<n, 128, 0, s>>>(Q, ldq, n, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc, int k,
+                        double *X, int64_t ldx, int32_t *status, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_trsv<<<k, 128, sizeof(double) * (size_t)n, s>>>(R, ldr, n, C, ldc, X, ldx, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,0 +1,520 @@
+// C ABI of the TSQR library: argument checking, the planner (leaf partition, chains,
+// reduction tree) and the factor-set object. Every public entry point is declared and
+// documented in include/tsqr.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tsqr.h"
+#include "tsqr_internal.h"
+
+using namespace tsqr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tsqr_status fail(tsqr_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? TSQR_ERR_OOM : TSQR_ERR_CUDA,         \
+                  "%s failed: %s", #expr, cudaGetErrorString(e_));                        \
+  } while (0)
+
+struct DeviceInfo {
+  int sms = 0;
+  size_t smem_sm = 0, reserved = 0, optin = 0;
+};
+
+DeviceInfo device_info(int dev) {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1);
+  DeviceInfo &d = cache[dev];
+  if (d.sms == 0) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+      d.sms = prop.multiProcessorCount;
+      d.smem_sm = prop.sharedMemPerMultiprocessor;
+      d.reserved = prop.reservedSharedMemPerBlock;
+      d.optin = prop.sharedMemPerBlockOptin;
+    }
+  }
+  return d;
+}
+
+// Stream-ordered allocations come from the device's default pool, kept cached so
+// that repeated factorizations do not return memory to the driver.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
+  if (bytes == 0) bytes = 16;
+  return cudaMallocAsync(p, bytes, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- plan
+struct Plan {
+  int64_t m = 0;
+  int n = 0, nc = 0, leaf_h = 0, arity = 0, flags = 0, tile_h = 0, ctas_per_sm = 0;
+  int64_t leaves = 0;
+  std::vector<TileDesc> tiles;
+  std::vector<JobDesc> jobs;
+  std::vector<LaunchDesc> launches;  // launch 0: chains; 1..: tree levels
+};
+
+static void plan_build(Plan &pl, int64_t chains_target) {
+  const int64_t m = pl.m, h = pl.leaf_h;
+  const int64_t P = std::max<int64_t>(1, m / h);
+  pl.leaves = P;
+  auto leaf_begin = [&](int64_t i) { return i * h; };
+  auto leaf_end = [&](int64_t i) { return (i == P - 1) ? m : (i + 1) * h; };
+  int64_t G;
+  if (pl.flags & TSQR_TWO_LEVEL)
+    G = std::max<int64_t>(1, std::min<int64_t>(P, chains_target));
+  else if (pl.arity == 0)
+    G = 1;
+  else
+    G = P;
+  std::vector<int64_t> piv;
+  piv.reserve(G);
+  pl.launches.push_back({0, 0});
+  for (int64_t c = 0; c < G; ++c) {
+    const int64_t la = c * P / G, lb = (c + 1) * P / G;  // leaves [la, lb)
+    JobDesc job{leaf_begin(la), (int32_t)pl.tiles.size(), 0};
+    bool first = true;
+    for (int64_t l = la; l < lb; ++l) {
+      int64_t r = leaf_begin(l);
+      const int64_t r1 = leaf_end(l);
+      while (r < r1) {
+        const int hh = (int)std::min<int64_t>(pl.tile_h, r1 - r);
+        pl.tiles.push_back({r, (int64_t)pl.tiles.size() * pl.n, hh, first ? GEQRT : TSQRT});
+        first = false;
+        r += hh;
+      }
+    }
+    job.tile_count = (int32_t)pl.tiles.size() - job.tile_begin;
+    pl.jobs.push_back(job);
+    piv.push_back(job.piv_row);
+  }
+  pl.launches[0].job_count = (int32_t)pl.jobs.size();
+  while (piv.size() > 1) {
+    LaunchDesc ld{(int32_t)pl.jobs.size(), 0};
+    std::vector<int64_t> next;
+    const size_t k = (pl.arity == 0) ? piv.size() : (size_t)pl.arity;
+    for (size_t g = 0; g < piv.size(); g += k) {
+      const size_t ge = std::min(piv.size(), g + k);
+      next.push_back(piv[g]);
+      if (ge - g < 2) continue;  // a lone node passes up unchanged
+      JobDesc job{piv[g], (int32_t)pl.tiles.size(), 0};
+      for (size_t c = g + 1; c < ge; ++c)
+        pl.tiles.push_back({piv[c], (int64_t)pl.tiles.size() * pl.n, pl.n, TTQRT});
+      job.tile_count = (int32_t)pl.tiles.size() - job.tile_begin;
+      pl.jobs.push_back(job);
+    }
+    ld.job_count = (int32_t)pl.jobs.size() - ld.job_begin;
+    pl.launches.push_back(ld);
+    piv.swap(next);
+  }
+}
+
+// Chooses the tile height and CTAs per SM of the factor kernel for nc columns: two
+// resident CTAs when the tile still holds at least n rows (one CTA's scalar phase is
+// then hidden behind the other's updates), otherwise one.
+static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &tile_h, int &cps) {
+  for (int c = 2; c >= 1; --c) {
+    int rows = factor_max_rows(nc, c, di.smem_sm, di.reserved, di.optin);
+    rows = std::min(rows, 512);  // the apply kernels stage at most 512 rows per tile
+    if (rows >= n && rows >= 8) {
+      tile_h = std::min(rows, std::max(leaf_h, n));
+      cps = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+struct tsqr_factors {
+  Plan plan;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double *V = nullptr;  // reflector storage (== user A when in place)
+  int64_t ldv = 0;
+  bool owns_V = false;
+  double *tau = nullptr, *scl = nullptr, *d = nullptr;
+  JobDesc *jobs = nullptr;
+  TileDesc *tiles = nullptr;
+  void *block = nullptr;  // one allocation for tau, scl, d, jobs, tiles
+};
+
+static tsqr_status factors_alloc(tsqr_factors *F, cudaStream_t s) {
+  const Plan &pl = F->plan;
+  const size_t nrefl = pl.tiles.size() * (size_t)pl.n;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_tau = up(sizeof(double) * nrefl), b_d = up(sizeof(double) * pl.n);
+  const size_t b_jobs = up(sizeof(JobDesc) * pl.jobs.size());
+  const size_t b_tiles = up(sizeof(TileDesc) * pl.tiles.size());
+  const size_t total = 2 * b_tau + b_d + b_jobs + b_tiles;
+  CUDA_TRY(pool_alloc(&F->block, total, s));
+  char *base = (char *)F->block;
+  F->tau = (double *)base;
+  F->scl = (double *)(base + b_tau);
+  F->d = (double *)(base + 2 * b_tau);
+  F->jobs = (JobDesc *)(base + 2 * b_tau + b_d);
+  F->tiles = (TileDesc *)(base + 2 * b_tau + b_d + b_jobs);
+  CUDA_TRY(cudaMemcpyAsync(F->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(),
+                           cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(F->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(),
+                           cudaMemcpyHostToDevice, s));
+  return TSQR_OK;
+}
+
+static void factors_release(tsqr_factors *F) {
+  if (!F) return;
+  if (F->block) cudaFreeAsync(F->block, F->stream);
+  if (F->owns_V && F->V) cudaFreeAsync(F->V, F->stream);
+  delete F;
+}
+
+// Runs the factorization launches of F on A (first touch) and optional extra columns B.
+static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, double *B, int64_t ldb,
+                              cudaStream_t s) {
+  const Plan &pl = F->plan;
+  FactorParams p{};
+  p.A = A;
+  p.lda = lda;
+  p.V = F->V;
+  p.ldv = F->ldv;
+  p.B = B;
+  p.ldb = ldb;
+  p.jobs = F->jobs;
+  p.tiles = F->tiles;
+  p.tau = F->tau;
+  p.scl = F->scl;
+  p.n = pl.n;
+  p.nc = pl.nc;
+  p.ldt = pl.tile_h;
+  for (const LaunchDesc &ld : pl.launches) {
+    p.job0 = ld.job_begin;
+    CUDA_TRY(launch_factor(p, ld.job_count, s));
+  }
+  return TSQR_OK;
+}
+
+static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
+                             cudaStream_t s) {
+  const Plan &pl = F->plan;
+  ApplyParams p{};
+  p.V = F->V;
+  p.ldv = F->ldv;
+  p.B = B;
+  p.ldb = ldb;
+  p.jobs = F->jobs;
+  p.tiles = F->tiles;
+  p.tau = F->tau;
+  p.scl = F->scl;
+  p.n = pl.n;
+  p.ldt = pl.tile_h;
+  p.trans = trans;
+  p.formq = formq;
+  const int nl = (int)pl.launches.size();
+  // B is processed in groups of at most 64 columns (8 for the warp kernel path)
+  const int group = (k <= 8) ? 8 : 64;
+  for (int c0 = 0; c0 < k; c0 += group) {
+    p.col0 = c0;
+    p.k = std::min(group, k - c0);
+    for (int q = 0; q < nl; ++q) {
+      const LaunchDesc &ld = pl.launches[trans ? q : nl - 1 - q];
+      p.job0 = ld.job_begin;
+      CUDA_TRY(launch_apply(p, ld.job_count, s));
+    }
+  }
+  return TSQR_OK;
+}
+
+static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
+                                int arity, int flags) {
+  pl.m = m;
+  pl.n = n;
+  pl.nc = nc;
+  pl.leaf_h = leaf_h;
+  pl.arity = arity;
+  pl.flags = flags;
+  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm))
+    return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
+  const int64_t chains = (int64_t)di.sms * pl.ctas_per_sm * 4;
+  try {
+    plan_build(pl, chains);
+  } catch (const std::bad_alloc &) {
+    return fail(TSQR_ERR_OOM, "host allocation failed while planning");
+  }
+  return TSQR_OK;
+}
+
+static tsqr_status make_plan(Plan &pl, int64_t m, int n, int nc, int leaf_h, int arity, int flags) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  return make_plan_on(di, pl, m, n, nc, leaf_h, arity, flags);
+}
+
+static tsqr_status check_factor_args(const void *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h,
+                                     int32_t arity) {
+  if (!A) return fail(TSQR_ERR_ARG, "A is NULL");
+  if (n < 1 || n > 128) return fail(TSQR_ERR_ARG, "n=%d outside [1, 128]", n);
+  if (m < n) return fail(TSQR_ERR_ARG, "m=%lld < n=%d", (long long)m, n);
+  if (lda < m) return fail(TSQR_ERR_ARG, "lda=%lld < m=%lld", (long long)lda, (long long)m);
+  if (leaf_h < n) return fail(TSQR_ERR_ARG, "leaf_h=%d < n=%d", leaf_h, n);
+  if (!(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "arity=%d not in {0, 2..16}", arity);
+  return TSQR_OK;
+}
+
+extern "C" {
+
+const char *tsqr_strerror(tsqr_status s) {
+  switch (s) {
+    case TSQR_OK: return "success";
+    case TSQR_ERR_ARG: return "invalid argument";
+    case TSQR_ERR_OOM: return "out of device memory";
+    case TSQR_ERR_CUDA: return "CUDA error";
+    case TSQR_ERR_SINGULAR: return "R is singular";
+    case TSQR_ERR_TIMEOUT: return "device wait timed out";
+    case TSQR_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *tsqr_last_error(void) { return g_last_error.c_str(); }
+
+tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h, int32_t arity,
+                        int32_t prec, int32_t flags, void *stream, tsqr_factors **F, double *R, int64_t ldr) {
+  g_last_error.clear();
+  tsqr_status st = check_factor_args(A, m, n, lda, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if (!F) return fail(TSQR_ERR_ARG, "F is NULL");
+  if (R && ldr < n) return fail(TSQR_ERR_ARG, "ldr=%lld < n=%d", (long long)ldr, n);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "tsqr_factor: TSQR_MIXED is served by tsqr_lstsq");
+  if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
+  *F = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  tsqr_factors *f = new (std::nothrow) tsqr_factors();
+  if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
+  f->stream = s;
+  cudaGetDevice(&f->device);
+  st = make_plan(f->plan, m, n, n, leaf_h, arity, flags);
+  if (st == TSQR_OK) st = factors_alloc(f, s);
+  if (st == TSQR_OK) {
+    if (flags & TSQR_INPLACE) {
+      f->V = const_cast<double *>(A);
+      f->ldv = lda;
+    } else {
+      cudaError_t e = pool_alloc((void **)&f->V, sizeof(double) * (size_t)m * n, s);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_OOM, "V allocation failed: %s", cudaGetErrorString(e));
+      f->owns_V = true;
+      f->ldv = m;
+    }
+  }
+  if (st == TSQR_OK) st = run_factor(f, A, lda, nullptr, 0, s);
+  if (st == TSQR_OK) {
+    cudaError_t e = launch_extract_r(f->V, f->ldv, n, R, ldr, f->d, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "extract_r: %s", cudaGetErrorString(e));
+  }
+  if (st != TSQR_OK) {
+    factors_release(f);
+    return st;
+  }
+  *F = f;
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
+  g_last_error.clear();
+  if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
+  if (k < 1 || ldb < F->plan.m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  cudaStream_t s = (cudaStream_t)stream;
+  tsqr_status st = run_apply(F, B, ldb, k, 1, 0, s);
+  if (st != TSQR_OK) return st;
+  CUDA_TRY(launch_scale_rows(B, ldb, F->plan.n, k, F->d, s));
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
+  g_last_error.clear();
+  if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
+  if (k < 1 || ldb < F->plan.m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_scale_rows(B, ldb, F->plan.n, k, F->d, s));
+  return run_apply(F, B, ldb, k, 0, 0, s);
+}
+
+tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *stream) {
+  g_last_error.clear();
+  if (!F || !Q) return fail(TSQR_ERR_ARG, "NULL factor set or Q");
+  if (ldq < F->plan.m) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_formq_init(Q, ldq, F->plan.n, F->d, s));
+  return run_apply(F, Q, ldq, F->plan.n, 0, 1, s);
+}
+
+tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const double *B, int64_t ldb,
+                       int32_t k, double *X, int64_t ldx, int32_t leaf_h, int32_t arity, int32_t prec,
+                       int32_t flags, int32_t max_refine, void *stream, double *info) {
+  g_last_error.clear();
+  tsqr_status st = check_factor_args(A, m, n, lda, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if (!B || !X) return fail(TSQR_ERR_ARG, "B or X is NULL");
+  if (k < 1 || k > 64) return fail(TSQR_ERR_ARG, "k=%d outside [1, 64]", k);
+  if (ldb < m || ldx < n) return fail(TSQR_ERR_ARG, "bad ldb/ldx");
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (max_refine < 0) return fail(TSQR_ERR_ARG, "max_refine < 0");
+  if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_MIXED is not built yet");
+  if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
+  flags &= ~TSQR_INPLACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  tsqr_factors *f = new (std::nothrow) tsqr_factors();
+  if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
+  f->stream = s;
+  double *W = nullptr;  // Q^T B workspace (m-by-k)
+  int32_t *status = nullptr;
+  const bool fused = (n + k) <= 128;
+  st = make_plan(f->plan, m, n, fused ? n + k : n, leaf_h, arity, flags);
+  if (st == TSQR_OK) st = factors_alloc(f, s);
+  if (st == TSQR_OK) {
+    cudaError_t e = pool_alloc((void **)&f->V, sizeof(double) * (size_t)m * n, s);
+    if (e == cudaSuccess) e = pool_alloc((void **)&W, sizeof(double) * (size_t)m * k, s);
+    if (e == cudaSuccess) e = pool_alloc((void **)&status, sizeof(int32_t), s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_OOM, "workspace allocation failed");
+    f->owns_V = true;
+    f->ldv = m;
+  }
+  if (st == TSQR_OK) {
+    cudaError_t e = cudaMemcpy2DAsync(W, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, k,
+                                      cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "workspace init: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK) {
+    if (fused) {
+      st = run_factor(f, A, lda, W, m, s);  // Q^T B computed with the factorization
+    } else {
+      st = run_factor(f, A, lda, nullptr, 0, s);
+      if (st == TSQR_OK) st = run_apply(f, W, m, k, 1, 0, s);
+    }
+  }
+  if (st == TSQR_OK) {
+    cudaError_t e = launch_trsv(f->V, f->ldv, n, W, m, k, X, ldx, status, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "trsv: %s", cudaGetErrorString(e));
+  }
+  int32_t hstatus = 0;
+  if (st == TSQR_OK) {
+    cudaError_t e = cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK && info) info[0] = 0.0;
+  if (W) cudaFreeAsync(W, s);
+  if (status) cudaFreeAsync(status, s);
+  factors_release(f);
+  if (st == TSQR_OK && hstatus == 4) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
+  return st;
+}
+
+tsqr_status tsqr_free(tsqr_factors *F) {
+  factors_release(F);
+  return TSQR_OK;
+}
+
+static void plan_info(const Plan &pl, int64_t *out) {
+  out[0] = pl.m;
+  out[1] = pl.n;
+  out[2] = pl.leaves;
+  out[3] = pl.tile_h;
+  out[4] = (int64_t)pl.jobs.size();
+  out[5] = (int64_t)pl.tiles.size();
+  out[6] = (int64_t)pl.launches.size() + 1;
+  out[7] = pl.ctas_per_sm;
+}
+
+tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h, int32_t arity, int32_t flags,
+                               int32_t sms, int64_t smem_per_sm, int64_t smem_reserved, int64_t smem_optin,
+                               int64_t *out, int64_t *tiles, int64_t max_tiles, int64_t *jobs,
+                               int64_t max_jobs) {
+  g_last_error.clear();
+  int dummy = 0;
+  tsqr_status st = check_factor_args(&dummy, m, n, m, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if (!out) return fail(TSQR_ERR_ARG, "out is NULL");
+  if (nc < n || nc > 256) return fail(TSQR_ERR_ARG, "nc=%d outside [n, 256]", nc);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (sms < 1 || smem_per_sm < 1 || smem_reserved < 0 || smem_optin < 1)
+    return fail(TSQR_ERR_ARG, "bad device description");
+  DeviceInfo di;
+  di.sms = sms;
+  di.smem_sm = (size_t)smem_per_sm;
+  di.reserved = (size_t)smem_reserved;
+  di.optin = (size_t)smem_optin;
+  Plan pl;
+  st = make_plan_on(di, pl, m, n, nc, leaf_h, arity, flags);
+  if (st != TSQR_OK) return st;
+  plan_info(pl, out);
+  if (tiles && (int64_t)pl.tiles.size() > max_tiles) return fail(TSQR_ERR_ARG, "max_tiles too small");
+  if (jobs && (int64_t)pl.jobs.size() > max_jobs) return fail(TSQR_ERR_ARG, "max_jobs too small");
+  for (size_t l = 0; l < pl.launches.size(); ++l) {
+    const LaunchDesc &ld = pl.launches[l];
+    for (int32_t jb = ld.job_begin; jb < ld.job_begin + ld.job_count; ++jb) {
+      const JobDesc &jd = pl.jobs[jb];
+      if (jobs) {
+        jobs[4 * jb + 0] = jd.piv_row;
+        jobs[4 * jb + 1] = jd.tile_begin;
+        jobs[4 * jb + 2] = jd.tile_count;
+        jobs[4 * jb + 3] = (int64_t)l;
+      }
+      if (tiles) {
+        for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t) {
+          tiles[5 * t + 0] = pl.tiles[t].row0;
+          tiles[5 * t + 1] = pl.tiles[t].nrows;
+          tiles[5 * t + 2] = pl.tiles[t].kind;
+          tiles[5 * t + 3] = jb;
+          tiles[5 * t + 4] = (int64_t)l;
+        }
+      }
+    }
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_factors_info(const tsqr_factors *F, int64_t *out) {
+  if (!F || !out) return fail(TSQR_ERR_ARG, "NULL argument");
+  plan_info(F->plan, out);
+  return TSQR_OK;
+}
+
+}  // extern "C"

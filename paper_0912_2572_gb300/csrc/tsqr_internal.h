@@ -1,0 +1,109 @@
+// Internal declarations shared by the TSQR host code and kernels (not part of the C ABI).
+//
+// Execution model. A factorization is a list of launches; each launch runs a list of
+// independent jobs, one CTA per job. A job owns a block of n "pivot rows" (the rows that
+// end up holding its R) and walks a sequence of tiles:
+//   GEQRT  dense Householder QR of a leaf's first tile; the pivot rows are the tile's own
+//          first n rows (paper §2.2, a domain factorization);
+//   TSQRT  QR of [R; tile]: an upper triangle on top of a dense tile (the flat-tree step
+//          of paper §2.3, triangle-on-square);
+//   TTQRT  QR of [R; R_child]: two stacked triangles (the binary reduce operator of
+//          paper §2.3).
+// A chain job = GEQRT + TSQRT...: a leaf taller than one tile, or a flat tree over
+// leaves. A combine job = TTQRT...: one node of the reduction tree (k-1 children folded
+// into the first child's rows). Reflector j of every tile has the form
+// v = [1 at pivot row j; scale_j * (tile column j on its tail rows)], H = I - tau_j v v^T.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsqr {
+
+enum TileKind : int32_t { GEQRT = 0, TSQRT = 1, TTQRT = 2 };
+
+struct TileDesc {
+  int64_t row0;   // first global row of the tile
+  int64_t refl;   // index of reflector 0 of this tile in the tau/scale arrays
+  int32_t nrows;  // rows in the tile (TTQRT: n)
+  int32_t kind;   // TileKind
+};
+
+struct JobDesc {
+  int64_t piv_row;     // first of the n pivot rows
+  int32_t tile_begin;  // index into the tile array
+  int32_t tile_count;
+};
+
+struct LaunchDesc {
+  int32_t job_begin;
+  int32_t job_count;
+};
+
+// Tail rows [lo, hi) of reflector j within a tile of `ht` rows.
+__host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int &hi) {
+  if (kind == GEQRT) {
+    lo = j + 1;
+    hi = ht;
+  } else if (kind == TSQRT) {
+    lo = 0;
+    hi = ht;
+  } else {
+    lo = 0;
+    hi = j + 1;
+  }
+}
+
+// ----------------------------------------------------------------- factor kernel
+struct FactorParams {
+  const double *A;  // first-touch input for GEQRT/TSQRT tiles
+  int64_t lda;
+  double *V;        // reflector and R storage, m-by-n
+  int64_t ldv;
+  double *B;        // optional extra columns (Q^T B fused), m-by-(nc-n), in place
+  int64_t ldb;
+  const JobDesc *jobs;
+  const TileDesc *tiles;
+  double *tau;
+  double *scl;
+  int32_t n;
+  int32_t nc;   // n + extra columns
+  int32_t ldt;  // tile capacity in rows (shared-memory leading dimension)
+  int32_t job0; // first job of this launch
+};
+
+size_t factor_smem_bytes(int nc, int ldt);
+cudaError_t launch_factor(const FactorParams &p, int njobs, cudaStream_t s);
+int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
+                    size_t optin_per_block);
+
+// ------------------------------------------------------------------ apply kernels
+struct ApplyParams {
+  const double *V;
+  int64_t ldv;
+  double *B;  // m-by-k target
+  int64_t ldb;
+  const JobDesc *jobs;
+  const TileDesc *tiles;
+  const double *tau;
+  const double *scl;
+  int32_t n;
+  int32_t k;         // columns of B handled by this launch
+  int32_t col0;      // first column of B (wide kernel passes)
+  int32_t ldt;       // max tile rows
+  int32_t job0;
+  int32_t trans;     // 1: Q^T (forward order), 0: Q (reverse order)
+  int32_t formq;     // 1: forming the thin Q (tiles start at zero, column j >= ref j only)
+};
+
+cudaError_t launch_apply(const ApplyParams &p, int njobs, cudaStream_t s);
+
+// ------------------------------------------------------------------- small kernels
+cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,
+                             double *d, cudaStream_t s);
+cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double *d,
+                              cudaStream_t s);
+cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s);
+cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc,
+                        int k, double *X, int64_t ldx, int32_t *status, cudaStream_t s);
+
+}  // namespace tsqr

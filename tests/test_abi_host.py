@@ -1,0 +1,173 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports every symbol the
+public header declares, argument errors are reported before any CUDA work, and the
+planner builds the leaf partition and reduction tree of paper §2.3 (k-ary, flat, and
+the two-level tree) correctly."""
+import ctypes
+import math
+
+import pytest
+
+from paper_0912_2572_gb300 import _lib, build
+
+# a GB300-like device description: 152 SMs, 228 KiB shared memory per SM
+GB300 = dict(sms=152, smem=233472, reserved=1024, optin=232448)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _lib.declared_functions()
+    assert {"tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q", "tsqr_lstsq",
+            "tsqr_free"} <= set(names)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_strerror(lib):
+    assert lib.tsqr_strerror(0) == b"success"
+    assert lib.tsqr_strerror(1) == b"invalid argument"
+    assert lib.tsqr_strerror(4) == b"R is singular"
+
+
+FAKE = 4096  # a non-null address that must never be dereferenced by argument checks
+
+
+@pytest.mark.parametrize("kw,why", [
+    (dict(A=0), "A is NULL"),
+    (dict(n=0), "n=0"),
+    (dict(n=129), "n=129"),
+    (dict(m=10, n=11, leaf_h=11), "m=10 < n"),
+    (dict(lda=99), "lda=99"),
+    (dict(leaf_h=8), "leaf_h=8 < n"),
+    (dict(arity=1), "arity=1"),
+    (dict(arity=17), "arity=17"),
+    (dict(F=False), "F is NULL"),
+    (dict(ldr=3), "ldr=3"),
+    (dict(flags=8), "unknown flags"),
+    (dict(prec=7), "unknown prec"),
+])
+def test_factor_argument_errors(lib, kw, why):
+    a = dict(A=FAKE, m=100, n=16, lda=100, leaf_h=32, arity=2, prec=0, flags=0, F=True, ldr=16)
+    a.update(kw)
+    h = ctypes.c_void_p()
+    st = lib.tsqr_factor(a["A"], a["m"], a["n"], a["lda"], a["leaf_h"], a["arity"], a["prec"], a["flags"],
+                         None, ctypes.byref(h) if a["F"] else None, FAKE, a["ldr"])
+    assert st == 1
+    assert why.split()[0] in lib.tsqr_last_error().decode()
+    assert not h.value
+
+
+def test_factor_mixed_is_unsupported(lib):
+    h = ctypes.c_void_p()
+    st = lib.tsqr_factor(FAKE, 100, 16, 100, 32, 2, 1, 0, None, ctypes.byref(h), FAKE, 16)
+    assert st == 6
+
+
+def test_other_entry_points_reject_null(lib):
+    assert lib.tsqr_apply_qt(None, FAKE, 10, 1, None) == 1
+    assert lib.tsqr_apply_q(None, FAKE, 10, 1, None) == 1
+    assert lib.tsqr_form_q(None, FAKE, 10, None) == 1
+    assert lib.tsqr_free(None) == 0
+    assert lib.tsqr_factors_info(None, None) == 1
+    # least squares: k outside [1, 64], null X, bad ldx
+    assert lib.tsqr_lstsq(FAKE, 100, 8, 100, FAKE, 100, 0, FAKE, 8, 32, 2, 0, 0, 0, None, None) == 1
+    assert lib.tsqr_lstsq(FAKE, 100, 8, 100, FAKE, 100, 65, FAKE, 8, 32, 2, 0, 0, 0, None, None) == 1
+    assert lib.tsqr_lstsq(FAKE, 100, 8, 100, FAKE, 100, 1, None, 8, 32, 2, 0, 0, 0, None, None) == 1
+    assert lib.tsqr_lstsq(FAKE, 100, 8, 100, FAKE, 100, 1, FAKE, 7, 32, 2, 0, 0, 0, None, None) == 1
+
+
+def describe(lib, m, n, h, arity, flags, nc=None, dev=GB300):
+    nc = n if nc is None else nc
+    out = (ctypes.c_int64 * 8)()
+    st = lib.tsqr_plan_describe(m, n, nc, h, arity, flags, dev["sms"], dev["smem"], dev["reserved"],
+                                dev["optin"], out, None, 0, None, 0)
+    assert st == 0, lib.tsqr_last_error()
+    ntiles, njobs = out[5], out[4]
+    tiles = (ctypes.c_int64 * (5 * ntiles))()
+    jobs = (ctypes.c_int64 * (4 * njobs))()
+    st = lib.tsqr_plan_describe(m, n, nc, h, arity, flags, dev["sms"], dev["smem"], dev["reserved"],
+                                dev["optin"], out, tiles, ntiles, jobs, njobs)
+    assert st == 0
+    info = dict(zip(["m", "n", "leaves", "tile_rows", "jobs", "tiles", "launches", "cps"], list(out)))
+    T = [tuple(tiles[5 * t:5 * t + 5]) for t in range(ntiles)]
+    J = [tuple(jobs[4 * j:4 * j + 4]) for j in range(njobs)]
+    return info, T, J
+
+
+def check_plan(m, n, h, arity, flags, info, T, J):
+    P = max(1, m // h)
+    assert info["leaves"] == P
+    th = info["tile_rows"]
+    assert n <= th <= 512
+    # launch 0: the chains cover every row exactly once, tiles in row order per job
+    chain_jobs = [j for j in J if j[3] == 0]
+    covered = []
+    for piv, tb, tc, _ in chain_jobs:
+        tl = T[tb:tb + tc]
+        assert tl[0][2] == 0 and tl[0][0] == piv and tl[0][1] >= n  # leaf QR first, >= n rows
+        assert all(t[2] == 1 for t in tl[1:])                      # then triangle-on-tile
+        for r0, rows, kind, job, launch in tl:
+            assert 1 <= rows <= th
+            covered.append((r0, r0 + rows))
+    covered.sort()
+    assert covered[0][0] == 0 and covered[-1][1] == m
+    assert all(a[1] == b[0] for a, b in zip(covered, covered[1:]))
+    # the tree: every chain result is merged into the root (row 0) exactly once
+    sets = {j[0]: {j[0]} for j in chain_jobs}
+    nlaunch = max(j[3] for j in J)
+    for lvl in range(1, nlaunch + 1):
+        for piv, tb, tc, launch in (j for j in J if j[3] == lvl):
+            assert tc >= 1 and (arity == 0 or tc <= arity - 1)
+            for r0, rows, kind, job, _ in T[tb:tb + tc]:
+                assert kind == 2 and rows == n
+                assert r0 in sets and piv in sets and r0 != piv
+                sets[piv] |= sets.pop(r0)
+    assert list(sets) == [0] and sets[0] == {j[0] for j in chain_jobs}
+    return chain_jobs, nlaunch
+
+
+@pytest.mark.parametrize("m,n,h,arity", [(4096, 16, 256, 2), (4096, 16, 256, 4), (4096, 16, 256, 0),
+                                         (10000, 7, 100, 3), (1000, 64, 64, 2), (130, 128, 128, 2),
+                                         (2049, 1, 1, 2), (64, 64, 64, 2), (4_194_304, 64, 208, 2)])
+def test_pure_trees(lib, m, n, h, arity):
+    info, T, J = describe(lib, m, n, h, arity, 0)
+    chain_jobs, nlaunch = check_plan(m, n, h, arity, 0, info, T, J)
+    P = max(1, m // h)
+    if arity == 0:
+        assert len(chain_jobs) == 1 and nlaunch == 0
+    else:
+        assert len(chain_jobs) == P
+        assert nlaunch == (0 if P == 1 else math.ceil(math.log(P, arity) - 1e-9))
+
+
+@pytest.mark.parametrize("m,n,h,arity", [(4_194_304, 64, 208, 2), (4_194_304, 64, 208, 4),
+                                         (4_194_304, 64, 1024, 0), (16_777_216, 32, 512, 2),
+                                         (5000, 64, 208, 2)])
+def test_two_level_tree(lib, m, n, h, arity):
+    info, T, J = describe(lib, m, n, h, arity, 2)
+    chain_jobs, _ = check_plan(m, n, h, arity, 2, info, T, J)
+    P = max(1, m // h)
+    G = min(P, GB300["sms"] * info["cps"] * 4)
+    assert len(chain_jobs) == G
+    sizes = [sum(1 for t in T[tb:tb + tc]) for _, tb, tc, _ in chain_jobs]
+    # balanced chains: leaf counts differ by at most one, and the last leaf (which takes
+    # the remainder rows) may need one more tile
+    assert max(sizes) - min(sizes) <= 2 * math.ceil(h / info["tile_rows"])
+
+
+def test_tile_capacity_choice(lib):
+    # n = 64: two CTAs per SM fit a 216-row tile; n = 128 needs one CTA per SM
+    info, _, _ = describe(lib, 100_000, 64, 1024, 2, 2)
+    assert info["cps"] == 2 and info["tile_rows"] == 216
+    info, _, _ = describe(lib, 100_000, 128, 1024, 2, 2)
+    assert info["cps"] == 1 and info["tile_rows"] >= 128
+    # the fused least-squares factorization sees n + k columns
+    info, _, _ = describe(lib, 100_000, 64, 1024, 2, 2, nc=72)
+    assert info["tile_rows"] < 216
+    # the leaf height caps the tile
+    info, _, _ = describe(lib, 100_000, 16, 100, 2, 0)
+    assert info["tile_rows"] == 100

@@ -1,0 +1,56 @@
+"""FP64 TSQR factorization on the GPU vs the oracle (paper §2.2-§2.3): R with a
+non-negative diagonal, the thin Q, Q^T b, and the backward / orthogonality errors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_2572_gb300 import inputs
+from conftest import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+R_TOL = 1e-12      # relative Frobenius error of R against the oracle
+BE_TOL = 1e-13     # ||A - QR||_F / ||A||_F and ||Q^T Q - I||_F
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+CASES = [
+    # (m, n, leaf_h, arity, two_level)
+    (4096, 16, 256, 2, False),
+    (4096, 16, 256, 2, True),
+    (4096, 16, 256, 4, False),
+    (4096, 16, 256, 0, False),
+    (3000, 7, 100, 2, False),
+    (1000, 33, 64, 3, False),
+    (777, 64, 128, 2, False),
+    (5000, 64, 208, 2, True),
+    (2049, 1, 1, 2, False),
+    (130, 128, 128, 2, False),
+    (1100, 100, 300, 2, True),
+    (64, 64, 64, 2, False),
+]
+
+
+@pytest.mark.parametrize("m,n,h,arity,two", CASES)
+def test_factor_matches_oracle(cuda_lib, m, n, h, arity, two):
+    import paper_0912_2572_gb300 as ts
+    A = inputs.gaussian(m, n, seed=m + n)
+    Ad = to_dev(A)
+    F = ts.factor(Ad, leaf_h=h, arity=arity, two_level=two)
+    Q = F.form_q()
+    R = to_host(F.R)
+    Qh = to_host(Q)
+    Qo, Ro, _ = oracle.qr(A)
+    assert np.all(np.diag(R) >= 0)
+    assert np.all(np.tril(R, -1) == 0)
+    assert _rel(R, Ro) <= R_TOL
+    assert _rel(Qh, Qo) <= R_TOL  # well-conditioned: the thin Q is entry-wise unique
+    assert oracle.backward_error(A, Qh, R) <= BE_TOL
+    assert oracle.orth_error(Qh) <= BE_TOL
+    # input untouched (not in place)
+    assert np.array_equal(to_host(Ad), A)
+    F.free()
