@@ -1,0 +1,399 @@
+"""Benchmark of the FP64 TSQR hot path on GB300.
+
+Workload: A = G diag(sigma) V^T, 4,194,304 x 64 FP64 (G iid N(0,1), sigma log-spaced
+from 1 to 1e-6, V Haar orthogonal), generated on the host from fixed seeds. One step is
+one pass of the whole FP64 path on that matrix: the TSQR factorization (leaf QRs and
+reduction tree, sign-normalised R), the explicit thin Q, Q^T b for one right-hand side
+and the least-squares solve x = R^{-1} (Q^T b)[0:n].
+
+Metric: TSQR Gflop/s with the paper's flop counts (§4, Tables 1-2): 2mn^2 - 2n^3/3 for
+R, the same again for Q, 4mnk - 2n^2k for Q^T b and n^2 k for the solve; the extra flops
+of the reduction tree are not credited. Inputs (2.1 GB) are larger than L2 (129 MB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ours,reference}]
+
+With N > 1 (torchrun, one process per GPU) every rank factors its own copy of the
+workload: the method has no exchange between GPUs, so this is replicas only (weak
+scaling). --impl reference times the CPU oracle on a bounded row sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TSQR Gflop/s & %roofline (4M×64 fp64); served LSQ solves/s, p99 vs plain path"
+FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20 TFLOP/s at 2.0 GHz)
+
+
+def flops_step(m, n, k=1):
+    f = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+    return {"factor": f, "form_q": f, "apply_qt": 4.0 * m * n * k - 2.0 * n * n * k, "solve": float(n * n * k)}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=4_194_304)
+    p.add_argument("--n", type=int, default=64)
+    p.add_argument("--leaf-h", type=int, default=0, help="rows per leaf; 0 = the on-chip tile height")
+    p.add_argument("--arity", type=int, default=2)
+    p.add_argument("--tree", default="two-level", choices=["two-level", "pure"])
+    p.add_argument("--decades", type=float, default=6.0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--sweep", default="", help="write a leaf-height x tree sweep (factor only) to this file")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- workload
+def make_workload(m, n, decades):
+    from paper_0912_2572_gb300 import inputs
+    A = inputs.graded(m, n, decades, seed_g=0, seed_v=1)
+    b = inputs.gaussian(m, 1, seed=2)
+    return A, b
+
+
+def dev_colmajor(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+
+def host_pinned_colmajor(a):
+    import torch
+    t = torch.empty((a.shape[1], a.shape[0]), dtype=torch.float64, pin_memory=True)
+    t.numpy()[:] = a.T
+    return t.t()
+
+
+def run_step(ts, Ad, bd, b0, Q, x, leaf_h, arity, two_level):
+    """One pass of the FP64 path; returns the factor set (caller frees)."""
+    F = ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two_level)
+    F.form_q(Q)
+    bd.copy_(b0)
+    F.apply_qt(bd)
+    F.solve_r(bd, X=x)
+    return F
+
+
+def oracle_step(oracle, A, b):
+    """The oracle's pass over the same path: one Householder factorization, the thin Q,
+    Q^T b and the back substitution."""
+    VR, tau = oracle.householder(A)
+    oracle.form_q(VR, tau)
+    c = oracle.apply_qt(VR, tau, b)
+    n = A.shape[1]
+    return oracle.trsv_upper(np.triu(VR[:n, :n]), c[:n, 0])
+
+
+def cpu_baseline(m, n, decades, budget_s=12.0):
+    """The oracle as it stands on a bounded row sample: factor, thin Q, Q^T b, solve."""
+    import oracle
+    from paper_0912_2572_gb300 import inputs
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    ms_ = 32768
+    while True:
+        A = inputs.graded(ms_, n, decades, seed_g=0, seed_v=1)
+        b = inputs.gaussian(ms_, 1, seed=2)
+        t0 = time.perf_counter()
+        oracle_step(oracle, A, b)
+        t = time.perf_counter() - t0
+        if t >= budget_s / 4 or ms_ * 2 > m:
+            break
+        ms_ *= 2
+    fl = sum(flops_step(ms_, n).values())
+    return {"value": fl / t / 1e9, "unit": "Gflop/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ms_} x {n} rows of the same generator (factor + thin Q + Q^T b + solve), "
+                      f"{t:.2f} s"}
+
+
+# ------------------------------------------------------------------ reference
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_0912_2572_gb300 import inputs
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    ms_ = 65536
+    A = inputs.graded(ms_, args.n, args.decades, seed_g=0, seed_v=1)
+    b = inputs.gaussian(ms_, 1, seed=2)
+
+    def step():
+        oracle_step(oracle, A, b)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t = time.perf_counter() - t0
+    fl = sum(flops_step(ms_, args.n).values())
+    val = fl * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gflop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"tsqr_fp64 {args.m}x{args.n} graded (sigma 1..1e-{args.decades:g}); "
+                                   f"reference = CPU oracle on a {ms_}-row sample per step"},
+            "cpu_baseline": {"value": val, "unit": "Gflop/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{ms_} x {args.n} rows per step (factor + thin Q + Q^T b + solve)"},
+            "e2e": {"value": val, "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- ours
+def sweep(args, ts, Ad, path):
+    import torch
+    rows = []
+    for tree in ("pure", "two-level"):
+        for arity in (2, 4, 0):
+            for h in (64, 128, 256, 512, 1024):
+                if tree == "pure" and arity == 0 and h < 1024:
+                    continue  # a flat tree is one sequential chain: one point is enough
+                two = tree == "two-level"
+                for _ in range(1):
+                    F = ts.factor(Ad, leaf_h=h, arity=arity, two_level=two)
+                    F.free()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 1 if (arity == 0 and not two) else 3
+                e0.record()
+                for _ in range(reps):
+                    F = ts.factor(Ad, leaf_h=h, arity=arity, two_level=two)
+                    F.free()
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / reps
+                g = flops_step(args.m, args.n)["factor"] / (t * 1e-3) / 1e9
+                rows.append({"tree": tree, "arity": arity, "leaf_h": h, "ms": t, "gflops": g})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    with open(path, "w") as f:
+        for r in rows:
+            f.write(json.dumps(r) + "\n")
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_0912_2572_gb300 as ts
+    from paper_0912_2572_gb300 import build as tsbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(os.path.join(ROOT, "paper_0912_2572_gb300", "libtsqr.so")) and rank == 0:
+        tsbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    m, n = args.m, args.n
+    two = args.tree == "two-level"
+    leaf_h = args.leaf_h or ts.plan_describe(m, n, 4096, args.arity, two)["tile_rows"]
+    A, b = make_workload(m, n, args.decades)
+    Ad = dev_colmajor(A)
+    bd = dev_colmajor(b)
+    b0 = bd.clone()
+    Q = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+    x = torch.empty((1, n), dtype=torch.float64, device="cuda").t()
+    fl = flops_step(m, n)
+    fl_step = sum(fl.values())
+
+    if args.sweep and rank == 0:
+        sweep(args, ts, Ad, args.sweep)
+
+    for _ in range(args.warmup):
+        run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two).free()
+    torch.cuda.synchronize()
+    info = ts.factor(Ad, leaf_h=leaf_h, arity=args.arity, two_level=two)
+    plan = info.info()
+    info.free()
+    torch.cuda.synchronize()
+
+    # --- timed region: K steps, CUDA events on the launching stream, launch profile live
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        def timed():
+            ev0.record(stream)
+            for _ in range(args.steps):
+                run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two).free()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        _, prof = ts.profile_collect(timed)
+    if world > 1:
+        dist.barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = fl_step * args.steps * world / (t_max * 1e-3) / 1e9
+
+    # --- per-phase times from the launch profile
+    phase_ms = {}
+    for kind, ms in prof:
+        phase_ms[kind] = phase_ms.get(kind, 0.0) + ms
+    chain = [ms for kind, ms in prof if kind == "factor_chains"]
+    chain_ms = sum(chain) / max(1, len(chain))
+    # chain launch algorithmic flops: every chain is a Householder QR of its own rows
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if two:
+        n_chains = min(plan["leaves"], sms * plan["ctas_per_sm"] * 4)
+    else:
+        n_chains = 1 if args.arity == 0 else plan["leaves"]
+    chain_flops = 2.0 * m * n * n - n_chains * 2.0 * n ** 3 / 3.0
+    achieved = chain_flops / (chain_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    peak = sms * FP64_SM_FLOPS_PER_CLK * 2.070e9 / 1e12
+    factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
+
+    # --- end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Ah = host_pinned_colmajor(A)
+        bh = host_pinned_colmajor(b)
+        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        xh = torch.empty((1, n), dtype=torch.float64, pin_memory=True).t()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            Ad.copy_(Ah, non_blocking=True)
+            b0.copy_(bh, non_blocking=True)
+            F = run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two)
+            Qh.copy_(Q, non_blocking=True)
+            Rh.copy_(F.R, non_blocking=True)
+            xh.copy_(x, non_blocking=True)
+            F.free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": fl_step * args.e2e_steps * world / (te * 1e-3) / 1e9, "unit": "Gflop/s",
+               "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
+               "ms_per_step": te / args.e2e_steps}
+        del Ah, Qh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(m, n, args.decades)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tsqr_fp64 {m}x{n} A=G*diag(sigma)*V^T, sigma 1..1e-{args.decades:g}; "
+                                   "step = factor + thin Q + Q^T b + solve",
+                       "m": m, "n": n, "leaf_h": leaf_h, "arity": args.arity, "tree": args.tree,
+                       "tile_rows": plan["tile_rows"], "chains": n_chains, "ctas_per_sm": plan["ctas_per_sm"],
+                       "l2": "inputs (2.1 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+            "phases": {"factor_ms": factor_ms,
+                       "factor_gflops": fl["factor"] / (factor_ms * 1e-3) / 1e9 if factor_ms else None,
+                       "form_q_ms": phase_ms.get("form_q", 0) / args.steps,
+                       "apply_qt_ms": phase_ms.get("apply_qt", 0) / args.steps,
+                       "small_ms": phase_ms.get("small", 0) / args.steps},
+            "roofline": {"kernel": "k_factor (leaf/flat-chain launch)", "bound": "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; no FP64 entry "
+                                      "in the measured peaks)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -131,6 +131,16 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
                        int32_t arity, int32_t prec, int32_t flags, int32_t max_refine,
                        void *stream, double *info);
 
+/*
+ * tsqr_solve_r — X = R^{-1} C[0:n] with F's R (diag(R) >= 0): the back substitution of
+ * least squares after tsqr_apply_qt (C = Q^T B, ldc >= n, 1 <= k; X n-by-k, ldx >= n).
+ *   status  device int32 or NULL: set to TSQR_ERR_SINGULAR when some r_jj == 0 (X then
+ *           holds non-finite values); never cleared by the call.
+ *   Errors: TSQR_ERR_ARG (null F/C/X, k < 1, ldc < n, ldx < n), TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, int32_t k,
+                         double *X, int64_t ldx, int32_t *status, void *stream);
+
 /* tsqr_free — releases F (stream-ordered on the stream F was created on). NULL is
  * accepted. */
 tsqr_status tsqr_free(tsqr_factors *F);
@@ -159,6 +169,27 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
                                int64_t smem_reserved, int64_t smem_optin, int64_t *out,
                                int64_t *tiles, int64_t max_tiles, int64_t *jobs,
                                int64_t max_jobs);
+
+/* launch classes reported by the profiler */
+enum {
+  TSQR_PROF_FACTOR_CHAINS = 0, /* leaf / flat-chain launch of the factorization */
+  TSQR_PROF_FACTOR_TREE = 1,   /* one tree level of the factorization */
+  TSQR_PROF_APPLY_QT = 2,
+  TSQR_PROF_APPLY_Q = 3,
+  TSQR_PROF_FORM_Q = 4,
+  TSQR_PROF_SMALL = 5          /* sign fix, scaling, triangular solve */
+};
+
+/*
+ * tsqr_profile_start / tsqr_profile_stop — opt-in launch timing. Between the two calls
+ * every kernel launch the library makes is bracketed by a pair of CUDA events recorded
+ * on the launching stream (the events add no synchronization). tsqr_profile_stop waits
+ * for the recorded events, writes up to max_records entries (launch class, elapsed ms)
+ * into the host arrays kind/ms (either may be NULL to discard), the total number of
+ * recorded launches into *count (host, may be NULL), and stops recording.
+ */
+tsqr_status tsqr_profile_start(void);
+tsqr_status tsqr_profile_stop(int64_t max_records, int32_t *kind, float *ms, int64_t *count);
 
 /* tsqr_strerror — static description of a status code. */
 const char *tsqr_strerror(tsqr_status s);

@@ -141,6 +141,17 @@ def apply_q(VR, tau, B):
     return Bv[:, 0] if vec else Bv
 
 
+def form_q(VR, tau):
+    """The thin Q = Q [I_n; 0] for the reflectors (VR, tau) (no sign normalisation)."""
+    lib = _load()
+    VR = _f64(VR)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    m, n = VR.shape
+    Q = np.zeros((m, n), order="F")
+    lib.oracle_form_q(m, n, _p(VR), m, _p(tau), _p(Q), m)
+    return Q
+
+
 def qr(A, normalise: bool = True):
     """Thin QR of A (m >= n): returns (Q m-by-n, R n-by-n, d). With ``normalise`` the
     signs are fixed so that diag(R) >= 0 (R <- D R, Q <- Q D, sign(0) = +1); d holds

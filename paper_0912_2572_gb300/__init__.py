@@ -17,7 +17,7 @@ import ctypes
 from . import _lib
 
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
-           "TSQRError"]
+           "TSQRError", "profile_collect", "plan_describe"]
 
 FP64 = 0
 MIXED = 1
@@ -96,6 +96,20 @@ class Factors:
         _lib.check(_lib.load().tsqr_form_q(self._h, Q.data_ptr(), ldq, _stream(stream)), "tsqr_form_q")
         return Q
 
+    def solve_r(self, C, X=None, status=None, stream=None):
+        """X = R^{-1} C[0:n] (C as returned by apply_qt); status: optional int32 CUDA
+        tensor set to 4 when R has a zero diagonal entry."""
+        import torch
+        ldc = _check_mat(C, "C")
+        k = C.shape[1]
+        if X is None:
+            X = torch.empty((k, self.n), dtype=torch.float64, device="cuda").t()
+        ldx = _check_mat(X, "X", rows=self.n, cols=k)
+        sp = status.data_ptr() if status is not None else None
+        _lib.check(_lib.load().tsqr_solve_r(self._h, C.data_ptr(), ldc, k, X.data_ptr(), ldx, sp,
+                                            _stream(stream)), "tsqr_solve_r")
+        return X
+
     def free(self):
         if self._h:
             _lib.load().tsqr_free(self._h)
@@ -129,6 +143,44 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
                          ctypes.byref(h), R.data_ptr(), ldr)
     _lib.check(st, "tsqr_factor")
     return Factors(h, m, n, R, A if inplace else None, stream)
+
+
+PROFILE_KINDS = {0: "factor_chains", 1: "factor_tree", 2: "apply_qt", 3: "apply_q", 4: "form_q",
+                 5: "small"}
+
+
+def profile_collect(fn):
+    """Runs fn() with launch profiling on and returns (fn's result, [(class, ms), ...])."""
+    lib = _lib.load()
+    _lib.check(lib.tsqr_profile_start(), "tsqr_profile_start")
+    try:
+        out = fn()
+    finally:
+        cap = 1 << 16
+        kinds = (ctypes.c_int32 * cap)()
+        ms = (ctypes.c_float * cap)()
+        cnt = ctypes.c_int64(0)
+        st = lib.tsqr_profile_stop(cap, kinds, ms, ctypes.byref(cnt))
+    _lib.check(st, "tsqr_profile_stop")
+    n = min(cnt.value, cap)
+    return out, [(PROFILE_KINDS.get(kinds[i], str(kinds[i])), ms[i]) for i in range(n)]
+
+
+def plan_describe(m, n, leaf_h, arity=2, two_level=True, nc=None, sms=None):
+    """Host-only plan summary for the current device (or a device with `sms` SMs and
+    GB300 shared-memory sizes)."""
+    import torch
+    lib = _lib.load()
+    if sms is None and torch.cuda.is_available():
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        sms = p.multi_processor_count
+    sms = sms or 152
+    out = (ctypes.c_int64 * 8)()
+    st = lib.tsqr_plan_describe(m, n, nc or n, leaf_h, arity, TWO_LEVEL if two_level else 0, sms, 233472,
+                                1024, 232448, out, None, 0, None, 0)
+    _lib.check(st, "tsqr_plan_describe")
+    keys = ["m", "n", "leaves", "tile_rows", "jobs", "tiles", "launches", "ctas_per_sm"]
+    return dict(zip(keys, list(out)))
 
 
 def lstsq(A, B, leaf_h: int = 256, arity: int = 2, two_level: bool = True, prec: int = FP64,

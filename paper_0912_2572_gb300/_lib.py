@@ -27,7 +27,11 @@ SIGNATURES = {
     "tsqr_form_q": (_i32, [_vp, _dp, _i64, _vp]),
     "tsqr_lstsq": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _i32, _i32, _i32, _i32,
                           _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "tsqr_solve_r": (_i32, [_vp, _dp, _i64, _i32, _dp, _i64, _dp, _vp]),
     "tsqr_free": (_i32, [_vp]),
+    "tsqr_profile_start": (_i32, []),
+    "tsqr_profile_stop": (_i32, [_i64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(_i64)]),
     "tsqr_factors_info": (_i32, [_vp, ctypes.POINTER(_i64)]),
     "tsqr_plan_describe": (_i32, [_i64, _i32, _i32, _i32, _i32, _i32, _i32, _i64, _i64, _i64,
                                   ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i64,

@@ -33,10 +33,11 @@ __global__ void k_formq_init(double *Q, int64_t ldq, int n, const double *__rest
 // X(:, c) = R^{-1} C(:, c) by back substitution, one CTA per right-hand side. R is the
 // upper triangle of an n-by-n block (n <= 1024). A zero pivot sets *status = 4.
 __global__ void k_trsv(const double *__restrict__ R, int64_t ldr, int n, const double *__restrict__ C,
-                       int64_t ldc, double *X, int64_t ldx, int32_t *status) {
+                       int64_t ldc, double *X, int64_t ldx, const double *__restrict__ d, int32_t *status) {
   extern __shared__ double xs[];
   const int c = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = C[i + (int64_t)c * ldc];
+  // with D = diag(d): (D R)^{-1} C = R^{-1} (D C), D = D^{-1}
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = d ? d[i] * C[i + (int64_t)c * ldc] : C[i + (int64_t)c * ldc];
   __syncthreads();
   __shared__ double xi_s;
   for (int i = n - 1; i >= 0; --i) {
@@ -78,9 +79,9 @@ cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cu
 }
 
 cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc, int k,
-                        double *X, int64_t ldx, int32_t *status, cudaStream_t s) {
+                        double *X, int64_t ldx, const double *d, int32_t *status, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  k_trsv<<<k, 128, sizeof(double) * (size_t)n, s>>>(R, ldr, n, C, ldc, X, ldx, status);
+  k_trsv<<<k, 128, sizeof(double) * (size_t)n, s>>>(R, ldr, n, C, ldc, X, ldx, d, status);
   return cudaGetLastError();
 }
 

@@ -1,10 +1,12 @@
 // C ABI of the TSQR library: argument checking, the planner (leaf partition, chains,
-// reduction tree) and the factor-set object. Every public entry point is declared and
-// documented in include/tsqr.h.
+// reduction tree), the device-resident plan cache, the factor-set object and the opt-in
+// launch profiler. Every public entry point is declared and documented in include/tsqr.h.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -63,19 +65,59 @@ DeviceInfo device_info(int dev) {
 // Stream-ordered allocations come from the device's default pool, kept cached so
 // that repeated factorizations do not return memory to the driver.
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t thr = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) == done.end()) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      done.push_back(dev);
     }
-  });
+  }
   if (bytes == 0) bytes = 16;
   return cudaMallocAsync(p, bytes, s);
 }
+
+// ------------------------------------------------------------------- profiler
+// Opt-in: a pair of CUDA events recorded on the launching stream around every kernel
+// launch the library makes, read back by tsqr_profile_stop.
+struct ProfRec {
+  int32_t kind;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+struct ProfScope {
+  bool on = false;
+  cudaStream_t s;
+  ProfRec r{};
+  ProfScope(int32_t kind, cudaStream_t st) : s(st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    r.kind = kind;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) {
+      cudaEventDestroy(r.a);
+      return;
+    }
+    cudaEventRecord(r.a, s);
+    on = true;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(r.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(r);
+  }
+};
 
 }  // namespace
 
@@ -160,38 +202,103 @@ static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &t
   return false;
 }
 
-struct tsqr_factors {
+static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
+                                int arity, int flags) {
+  pl.m = m;
+  pl.n = n;
+  pl.nc = nc;
+  pl.leaf_h = leaf_h;
+  pl.arity = arity;
+  pl.flags = flags & TSQR_TWO_LEVEL;
+  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm))
+    return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
+  const int64_t chains = (int64_t)di.sms * pl.ctas_per_sm * 4;
+  try {
+    plan_build(pl, chains);
+  } catch (const std::bad_alloc &) {
+    return fail(TSQR_ERR_OOM, "host allocation failed while planning");
+  }
+  return TSQR_OK;
+}
+
+// A plan together with its job and tile arrays resident on one device. Plans are
+// cached by shape so repeated factorizations of one shape upload nothing.
+struct DevPlan {
   Plan plan;
+  int device = -1;
+  JobDesc *jobs = nullptr;
+  TileDesc *tiles = nullptr;
+  ~DevPlan() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (device >= 0) cudaSetDevice(device);
+    if (jobs) cudaFree(jobs);
+    if (tiles) cudaFree(tiles);
+    cudaSetDevice(cur);
+  }
+};
+
+static std::mutex g_plan_mu;
+static std::list<std::shared_ptr<DevPlan>> g_plans;  // most recent first
+constexpr size_t kPlanCacheSize = 64;
+
+static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int flags,
+                            std::shared_ptr<DevPlan> &out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  flags &= TSQR_TWO_LEVEL;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+      const Plan &p = (*it)->plan;
+      if ((*it)->device == dev && p.m == m && p.n == n && p.nc == nc && p.leaf_h == leaf_h &&
+          p.arity == arity && p.flags == flags) {
+        out = *it;
+        g_plans.splice(g_plans.begin(), g_plans, it);
+        return TSQR_OK;
+      }
+    }
+  }
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  auto dp = std::make_shared<DevPlan>();
+  dp->device = dev;
+  tsqr_status st = make_plan_on(di, dp->plan, m, n, nc, leaf_h, arity, flags);
+  if (st != TSQR_OK) return st;
+  const Plan &pl = dp->plan;
+  CUDA_TRY(cudaMalloc(&dp->jobs, sizeof(JobDesc) * pl.jobs.size()));
+  CUDA_TRY(cudaMalloc(&dp->tiles, sizeof(TileDesc) * pl.tiles.size()));
+  CUDA_TRY(cudaMemcpy(dp->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(dp->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(), cudaMemcpyHostToDevice));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plans.push_front(dp);
+  while (g_plans.size() > kPlanCacheSize) g_plans.pop_back();
+  out = dp;
+  return TSQR_OK;
+}
+
+struct tsqr_factors {
+  std::shared_ptr<DevPlan> dp;
   int device = 0;
   cudaStream_t stream = nullptr;
   double *V = nullptr;  // reflector storage (== user A when in place)
   int64_t ldv = 0;
   bool owns_V = false;
   double *tau = nullptr, *scl = nullptr, *d = nullptr;
-  JobDesc *jobs = nullptr;
-  TileDesc *tiles = nullptr;
-  void *block = nullptr;  // one allocation for tau, scl, d, jobs, tiles
+  void *block = nullptr;  // one allocation for tau, scl, d
+  const Plan &plan() const { return dp->plan; }
 };
 
 static tsqr_status factors_alloc(tsqr_factors *F, cudaStream_t s) {
-  const Plan &pl = F->plan;
+  const Plan &pl = F->plan();
   const size_t nrefl = pl.tiles.size() * (size_t)pl.n;
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b_tau = up(sizeof(double) * nrefl), b_d = up(sizeof(double) * pl.n);
-  const size_t b_jobs = up(sizeof(JobDesc) * pl.jobs.size());
-  const size_t b_tiles = up(sizeof(TileDesc) * pl.tiles.size());
-  const size_t total = 2 * b_tau + b_d + b_jobs + b_tiles;
-  CUDA_TRY(pool_alloc(&F->block, total, s));
+  CUDA_TRY(pool_alloc(&F->block, 2 * b_tau + b_d, s));
   char *base = (char *)F->block;
   F->tau = (double *)base;
   F->scl = (double *)(base + b_tau);
   F->d = (double *)(base + 2 * b_tau);
-  F->jobs = (JobDesc *)(base + 2 * b_tau + b_d);
-  F->tiles = (TileDesc *)(base + 2 * b_tau + b_d + b_jobs);
-  CUDA_TRY(cudaMemcpyAsync(F->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(),
-                           cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(F->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(),
-                           cudaMemcpyHostToDevice, s));
   return TSQR_OK;
 }
 
@@ -205,7 +312,7 @@ static void factors_release(tsqr_factors *F) {
 // Runs the factorization launches of F on A (first touch) and optional extra columns B.
 static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, double *B, int64_t ldb,
                               cudaStream_t s) {
-  const Plan &pl = F->plan;
+  const Plan &pl = F->plan();
   FactorParams p{};
   p.A = A;
   p.lda = lda;
@@ -213,15 +320,17 @@ static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, dou
   p.ldv = F->ldv;
   p.B = B;
   p.ldb = ldb;
-  p.jobs = F->jobs;
-  p.tiles = F->tiles;
+  p.jobs = F->dp->jobs;
+  p.tiles = F->dp->tiles;
   p.tau = F->tau;
   p.scl = F->scl;
   p.n = pl.n;
-  p.nc = pl.nc;
+  p.nc = B ? pl.nc : pl.n;
   p.ldt = pl.tile_h;
-  for (const LaunchDesc &ld : pl.launches) {
+  for (size_t q = 0; q < pl.launches.size(); ++q) {
+    const LaunchDesc &ld = pl.launches[q];
     p.job0 = ld.job_begin;
+    ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
     CUDA_TRY(launch_factor(p, ld.job_count, s));
   }
   return TSQR_OK;
@@ -229,14 +338,14 @@ static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, dou
 
 static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
                              cudaStream_t s) {
-  const Plan &pl = F->plan;
+  const Plan &pl = F->plan();
   ApplyParams p{};
   p.V = F->V;
   p.ldv = F->ldv;
   p.B = B;
   p.ldb = ldb;
-  p.jobs = F->jobs;
-  p.tiles = F->tiles;
+  p.jobs = F->dp->jobs;
+  p.tiles = F->dp->tiles;
   p.tau = F->tau;
   p.scl = F->scl;
   p.n = pl.n;
@@ -252,37 +361,11 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
     for (int q = 0; q < nl; ++q) {
       const LaunchDesc &ld = pl.launches[trans ? q : nl - 1 - q];
       p.job0 = ld.job_begin;
+      ProfScope ps(formq ? TSQR_PROF_FORM_Q : (trans ? TSQR_PROF_APPLY_QT : TSQR_PROF_APPLY_Q), s);
       CUDA_TRY(launch_apply(p, ld.job_count, s));
     }
   }
   return TSQR_OK;
-}
-
-static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
-                                int arity, int flags) {
-  pl.m = m;
-  pl.n = n;
-  pl.nc = nc;
-  pl.leaf_h = leaf_h;
-  pl.arity = arity;
-  pl.flags = flags;
-  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm))
-    return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
-  const int64_t chains = (int64_t)di.sms * pl.ctas_per_sm * 4;
-  try {
-    plan_build(pl, chains);
-  } catch (const std::bad_alloc &) {
-    return fail(TSQR_ERR_OOM, "host allocation failed while planning");
-  }
-  return TSQR_OK;
-}
-
-static tsqr_status make_plan(Plan &pl, int64_t m, int n, int nc, int leaf_h, int arity, int flags) {
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  const DeviceInfo di = device_info(dev);
-  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
-  return make_plan_on(di, pl, m, n, nc, leaf_h, arity, flags);
 }
 
 static tsqr_status check_factor_args(const void *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h,
@@ -294,6 +377,17 @@ static tsqr_status check_factor_args(const void *A, int64_t m, int32_t n, int64_
   if (leaf_h < n) return fail(TSQR_ERR_ARG, "leaf_h=%d < n=%d", leaf_h, n);
   if (!(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "arity=%d not in {0, 2..16}", arity);
   return TSQR_OK;
+}
+
+static void plan_info(const Plan &pl, int64_t *out) {
+  out[0] = pl.m;
+  out[1] = pl.n;
+  out[2] = pl.leaves;
+  out[3] = pl.tile_h;
+  out[4] = (int64_t)pl.jobs.size();
+  out[5] = (int64_t)pl.tiles.size();
+  out[6] = (int64_t)pl.launches.size() + 1;
+  out[7] = pl.ctas_per_sm;
 }
 
 extern "C" {
@@ -329,7 +423,7 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
   if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
   f->stream = s;
   cudaGetDevice(&f->device);
-  st = make_plan(f->plan, m, n, n, leaf_h, arity, flags);
+  st = get_plan(m, n, n, leaf_h, arity, flags, f->dp);
   if (st == TSQR_OK) st = factors_alloc(f, s);
   if (st == TSQR_OK) {
     if (flags & TSQR_INPLACE) {
@@ -344,6 +438,7 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
   }
   if (st == TSQR_OK) st = run_factor(f, A, lda, nullptr, 0, s);
   if (st == TSQR_OK) {
+    ProfScope ps(TSQR_PROF_SMALL, s);
     cudaError_t e = launch_extract_r(f->V, f->ldv, n, R, ldr, f->d, s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "extract_r: %s", cudaGetErrorString(e));
   }
@@ -358,30 +453,49 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
 tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
   g_last_error.clear();
   if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
-  if (k < 1 || ldb < F->plan.m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  if (k < 1 || ldb < F->plan().m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
   cudaStream_t s = (cudaStream_t)stream;
   tsqr_status st = run_apply(F, B, ldb, k, 1, 0, s);
   if (st != TSQR_OK) return st;
-  CUDA_TRY(launch_scale_rows(B, ldb, F->plan.n, k, F->d, s));
+  ProfScope ps(TSQR_PROF_SMALL, s);
+  CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
   return TSQR_OK;
 }
 
 tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
   g_last_error.clear();
   if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
-  if (k < 1 || ldb < F->plan.m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  if (k < 1 || ldb < F->plan().m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
   cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_scale_rows(B, ldb, F->plan.n, k, F->d, s));
+  {
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
+  }
   return run_apply(F, B, ldb, k, 0, 0, s);
 }
 
 tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *stream) {
   g_last_error.clear();
   if (!F || !Q) return fail(TSQR_ERR_ARG, "NULL factor set or Q");
-  if (ldq < F->plan.m) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
+  if (ldq < F->plan().m) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
   cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_formq_init(Q, ldq, F->plan.n, F->d, s));
-  return run_apply(F, Q, ldq, F->plan.n, 0, 1, s);
+  {
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    CUDA_TRY(launch_formq_init(Q, ldq, F->plan().n, F->d, s));
+  }
+  return run_apply(F, Q, ldq, F->plan().n, 0, 1, s);
+}
+
+tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, int32_t k, double *X, int64_t ldx,
+                         int32_t *status, void *stream) {
+  g_last_error.clear();
+  if (!F || !C || !X) return fail(TSQR_ERR_ARG, "NULL factor set, C or X");
+  const int n = F->plan().n;
+  if (k < 1 || ldc < n || ldx < n) return fail(TSQR_ERR_ARG, "bad k=%d, ldc or ldx", k);
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(TSQR_PROF_SMALL, s);
+  CUDA_TRY(launch_trsv(F->V, F->ldv, n, C, ldc, k, X, ldx, F->d, status, s));
+  return TSQR_OK;
 }
 
 tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const double *B, int64_t ldb,
@@ -405,7 +519,7 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   double *W = nullptr;  // Q^T B workspace (m-by-k)
   int32_t *status = nullptr;
   const bool fused = (n + k) <= 128;
-  st = make_plan(f->plan, m, n, fused ? n + k : n, leaf_h, arity, flags);
+  st = get_plan(m, n, fused ? n + k : n, leaf_h, arity, flags, f->dp);
   if (st == TSQR_OK) st = factors_alloc(f, s);
   if (st == TSQR_OK) {
     cudaError_t e = pool_alloc((void **)&f->V, sizeof(double) * (size_t)m * n, s);
@@ -430,7 +544,8 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
     }
   }
   if (st == TSQR_OK) {
-    cudaError_t e = launch_trsv(f->V, f->ldv, n, W, m, k, X, ldx, status, s);
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    cudaError_t e = launch_trsv(f->V, f->ldv, n, W, m, k, X, ldx, nullptr, status, s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "trsv: %s", cudaGetErrorString(e));
   }
   int32_t hstatus = 0;
@@ -450,17 +565,6 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
 tsqr_status tsqr_free(tsqr_factors *F) {
   factors_release(F);
   return TSQR_OK;
-}
-
-static void plan_info(const Plan &pl, int64_t *out) {
-  out[0] = pl.m;
-  out[1] = pl.n;
-  out[2] = pl.leaves;
-  out[3] = pl.tile_h;
-  out[4] = (int64_t)pl.jobs.size();
-  out[5] = (int64_t)pl.tiles.size();
-  out[6] = (int64_t)pl.launches.size() + 1;
-  out[7] = pl.ctas_per_sm;
 }
 
 tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h, int32_t arity, int32_t flags,
@@ -513,8 +617,42 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
 
 tsqr_status tsqr_factors_info(const tsqr_factors *F, int64_t *out) {
   if (!F || !out) return fail(TSQR_ERR_ARG, "NULL argument");
-  plan_info(F->plan, out);
+  plan_info(F->plan(), out);
   return TSQR_OK;
+}
+
+tsqr_status tsqr_profile_start(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (ProfRec &r : g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = true;
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_profile_stop(int64_t max_records, int32_t *kind, float *ms, int64_t *count) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = false;
+  tsqr_status st = TSQR_OK;
+  const int64_t nrec = (int64_t)g_prof.size();
+  if (count) *count = nrec;
+  for (int64_t i = 0; i < nrec; ++i) {
+    ProfRec &r = g_prof[i];
+    if (i < max_records && kind && ms) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(r.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "profile readback: %s", cudaGetErrorString(e));
+      kind[i] = r.kind;
+      ms[i] = t;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  return st;
 }
 
 }  // extern "C"

@@ -103,7 +103,10 @@ cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int
 cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double *d,
                               cudaStream_t s);
 cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s);
+// X = R^{-1} (D C[0:n]) for the raw upper triangle R (leading dimension ldr) and the
+// optional sign vector d (NULL = no scaling); a zero pivot sets *status = 4.
 cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc,
-                        int k, double *X, int64_t ldx, int32_t *status, cudaStream_t s);
+                        int k, double *X, int64_t ldx, const double *d, int32_t *status,
+                        cudaStream_t s);
 
 }  // namespace tsqr
