@@ -141,6 +141,32 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
 tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, int32_t k,
                          double *X, int64_t ldx, int32_t *status, void *stream);
 
+/*
+ * tsqr_lstsq_static — FP64 least squares X = argmin ||A X - B||_F that allocates
+ * nothing. The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory at the point of the call (code in host callbacks, plugins whose
+ * framework owns all allocations, applications that reserve the whole device up front
+ * and forbid later cudaMalloc/cudaMallocAsync). It computes what tsqr_lstsq computes
+ * with prec = TSQR_FP64, leaf_h = the on-chip tile height, arity = 2, TSQR_TWO_LEVEL,
+ * but keeps every scratch buffer in one 64 MiB static device array that the library
+ * reserves on every GPU that loads it, for the life of the process.
+ *   A  device m-by-n (lda >= m), B device m-by-k (ldb >= m), X device n-by-k (ldx >= n);
+ *      n >= 1, k >= 1, n + k <= 128. A and B are not modified.
+ *   The scratch needed is about 8 * m * (n + k) bytes plus the plan: for n = 64, k = 1
+ *   at most about 129,000 rows.
+ *   The first call on a device looks up the array's address with that device current;
+ *   make that first call before any stream capture. All calls share the array and it
+ *   keeps the previous call's contents: calls that may overlap on the GPU (several
+ *   streams or host threads) race and must be serialized by the caller. The call waits
+ *   for its stream to finish (it reads back the singularity flag).
+ *   Errors: TSQR_ERR_ARG (null pointers, bad sizes or leading dimensions),
+ *           TSQR_ERR_UNSUPPORTED (the problem needs more scratch than the static array
+ *           holds; nothing is enqueued), TSQR_ERR_SINGULAR, TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, int64_t lda,
+                              const double *B, int64_t ldb, int32_t k, double *X,
+                              int64_t ldx, void *stream);
+
 /* tsqr_free — releases F (stream-ordered on the stream F was created on). NULL is
  * accepted. */
 tsqr_status tsqr_free(tsqr_factors *F);

@@ -28,6 +28,7 @@ SIGNATURES = {
     "tsqr_lstsq": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _i32, _i32, _i32, _i32,
                           _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tsqr_solve_r": (_i32, [_vp, _dp, _i64, _i32, _dp, _i64, _dp, _vp]),
+    "tsqr_lstsq_static": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _vp]),
     "tsqr_free": (_i32, [_vp]),
     "tsqr_profile_start": (_i32, []),
     "tsqr_profile_stop": (_i32, [_i64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
