@@ -16,7 +16,10 @@
 //     value instead of four;
 //   * reflectors are stored unscaled with (tau, scale) beside them, so the update of a
 //     trailing element is exactly one DFMA: b_ik -= (tau*scale*w_k) * b_ij;
-//   * the scalar work of a step (sqrt, division) runs on one lane of warp 0 while the
+//   * every warp issues exactly as many column slots as it owns at each step: a
+//     predicated-off DFMA still occupies the FP64 pipe, so the column guards are
+//     warp-uniform branches, not predicates;
+//   * the scalar work of a step (one rsqrt, one division) runs on warp 0 while the
 //     other CTA resident on the SM keeps the FP64 pipe busy (2 CTAs/SM by design).
 #include "tsqr_internal.h"
 
@@ -56,13 +59,17 @@ __device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
   return v[0];
 }
 
-// Gram row of step j: Pg[c] = sum_{i in [lo,hi)} T[j][i] * T[c][i] for c in [j, nc).
-template <int C>
-__device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, int j, int nc,
-                                         int lo, int hi, int hw, int hl, int warp,
-                                         double *__restrict__ Pg) {
+__host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
+
+// Gram row of step j: Pg[c] = sum_{i in [lo,hi)} T[j][i] T[c][i] for c in [j, nc) (c = j
+// is the squared norm of the pivot column's tail). Half-warp hw owns columns
+// j + hw + 16 t; this warp has exactly NS slots (t < NS), so no predicated-off DFMA is
+// issued; only half-warp 1 of the last slot can fall past nc.
+template <int NS>
+__device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, int j, int nc, int lo,
+                                         int hi, int hw, int hl, double *__restrict__ Pg) {
+  constexpr int C = pow2ceil(NS);
   const int cb = j + hw;
-  if (j + 2 * warp >= nc) return;  // warp-uniform: no column for this warp
   double acc[C];
 #pragma unroll
   for (int t = 0; t < C; ++t) acc[t] = 0.0;
@@ -70,27 +77,26 @@ __device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, 
   for (int i = lo + hl; i < hi; i += 16) {
     const double x = Tj[i];
 #pragma unroll
-    for (int t = 0; t < C; ++t) {
+    for (int t = 0; t < NS; ++t) {
       const int c = cb + 16 * t;
-      if (c < nc) acc[t] = fma(x, T[(size_t)c * ldt + i], acc[t]);
+      if (t < NS - 1 || c < nc) acc[t] = fma(x, T[(size_t)c * ldt + i], acc[t]);
     }
   }
   int idx;
   const double s = treduce16<C>(acc, hl, idx);
   const int c = cb + 16 * idx;
-  if ((hl & (16 / C - 1)) == 0 && c < nc) Pg[c] = s;
+  if ((hl & (16 / C - 1)) == 0 && idx < NS && c < nc) Pg[c] = s;
 }
 
-// Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c in (j, nc), i in [lo, hi).
-template <int C>
-__device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt, int j, int nc,
-                                                int lo, int hi, int hw, int hl, int warp,
-                                                const double *__restrict__ CF) {
+// Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c in (j, nc), i in [lo, hi);
+// half-warp hw owns columns j + 1 + hw + 16 t, this warp has exactly NS slots.
+template <int NS>
+__device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt, int j, int nc, int lo,
+                                                int hi, int hw, int hl, const double *__restrict__ CF) {
   const int cb = j + 1 + hw;
-  if (j + 1 + 2 * warp >= nc) return;
-  double cf[C];
+  double cf[NS];
 #pragma unroll
-  for (int t = 0; t < C; ++t) {
+  for (int t = 0; t < NS; ++t) {
     const int c = cb + 16 * t;
     cf[t] = (c < nc) ? CF[c] : 0.0;
   }
@@ -98,9 +104,9 @@ __device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt,
   for (int i = lo + hl; i < hi; i += 16) {
     const double x = Tj[i];
 #pragma unroll
-    for (int t = 0; t < C; ++t) {
+    for (int t = 0; t < NS; ++t) {
       const int c = cb + 16 * t;
-      if (c < nc) {
+      if (t < NS - 1 || c < nc) {
         double *q = T + (size_t)c * ldt + i;
         *q = fma(-cf[t], x, *q);
       }
@@ -108,36 +114,84 @@ __device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt,
   }
 }
 
-template <int CMAX>
-__device__ __forceinline__ void gram_row_dispatch(const double *T, int ldt, int j, int nc, int lo,
-                                                  int hi, int hw, int hl, int warp, double *Pg) {
-  const int slots = (nc - j + 15) >> 4;
-  if (slots <= 1 || CMAX == 1) gram_row<1>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
-  else if (slots <= 2 || CMAX == 2) gram_row<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
-  else if (slots <= 4 || CMAX == 4) gram_row<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
-  else gram_row<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+// The warp's slot count: the first column of half-warp 0 is cs + 2*warp.
+__device__ __forceinline__ int warp_slots(int cs, int nc, int warp) {
+  const int r = nc - cs - 2 * warp;
+  return r <= 0 ? 0 : (r + 15) >> 4;
 }
 
 template <int CMAX>
-__device__ __forceinline__ void update_dispatch(double *T, int ldt, int j, int nc, int lo, int hi,
-                                                int hw, int hl, int warp, const double *CF) {
-  const int slots = (nc - j - 1 + 15) >> 4;
-  if (slots <= 0) return;
-  if (slots <= 1 || CMAX == 1) trailing_update<1>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
-  else if (slots <= 2 || CMAX == 2) trailing_update<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
-  else if (slots <= 4 || CMAX == 4) trailing_update<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
-  else trailing_update<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+__device__ __forceinline__ void gram_row_dispatch(const double *T, int ldt, int j, int nc, int lo, int hi,
+                                                  int hw, int hl, int warp, double *Pg) {
+  switch (warp_slots(j, nc, warp)) {
+    case 0: return;
+    case 1: gram_row<1>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 2: if (CMAX >= 2) gram_row<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 3: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 3 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 4: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 5: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 5 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 6: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 6 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 7: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 7 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    default: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+  }
 }
 
 template <int CMAX>
-__global__ void __launch_bounds__(kThreads) k_factor(const FactorParams p) {
+__device__ __forceinline__ void update_dispatch(double *T, int ldt, int j, int nc, int lo, int hi, int hw,
+                                                int hl, int warp, const double *CF) {
+  switch (warp_slots(j + 1, nc, warp)) {
+    case 0: return;
+    case 1: trailing_update<1>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 2: if (CMAX >= 2) trailing_update<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 3: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 3 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 4: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 5: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 5 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 6: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 6 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 7: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 7 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    default: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+  }
+}
+
+// Scalars of the reflector that maps x = [alpha; tail], ||tail||^2 = s2, onto beta e_1
+// (Golub & Van Loan's sign choice, beta = -sign(alpha) ||x||, sign(0) = +1), in the form
+// the kernel stores: v = [1; scale * tail], H = I - tau v v^T. With nrm = ||x||:
+//   scale = sign(alpha) / (|alpha| + nrm),  tau = 1 + |alpha| / nrm,
+//   tau * scale = sign(alpha) / nrm,
+// which needs one reciprocal square root and one division. s2 == 0 gives H = I.
+struct Refl {
+  double tau, scale, beta, ts;
+};
+
+__device__ __forceinline__ Refl reflector(double alpha, double s2) {
+  Refl r;
+  if (s2 == 0.0) {
+    r.tau = 0.0;
+    r.scale = 0.0;
+    r.beta = alpha;
+    r.ts = 0.0;
+    return r;
+  }
+  const double s = fma(alpha, alpha, s2);
+  const double rn = rsqrt(s);
+  const double nrm = s * rn;
+  const double sg = (alpha < 0.0) ? -1.0 : 1.0;
+  const double aa = fabs(alpha);
+  r.beta = -sg * nrm;
+  r.scale = sg / (aa + nrm);
+  r.tau = fma(aa, rn, 1.0);
+  r.ts = sg * rn;
+  return r;
+}
+
+template <int CMAX>
+__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
   extern __shared__ __align__(16) double sm[];
   const int n = p.n, nc = p.nc, ldt = p.ldt;
   const int ncp = (nc + 7) & ~7;
   double *T = sm;                       // tile, column-major, nc columns of ldt rows
-  double *Pg = T + (size_t)nc * ldt;    // Gram row of the current step
-  double *CF = Pg + ncp;                // update coefficients tau*scale*w_k
-  double *PV = CF + ncp;                // staged pivot row (TSQRT / TTQRT)
+  double *PC = T + (size_t)nc * ldt;    // Gram row of the step, then (in place) the
+                                        // update coefficients tau*scale*w_k
+  double *PV = PC + ncp;                // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
   const JobDesc job = p.jobs[p.job0 + blockIdx.x];
@@ -181,31 +235,18 @@ __global__ void __launch_bounds__(kThreads) k_factor(const FactorParams p) {
         }
       }
 
-      gram_row_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, Pg);
+      gram_row_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
       __syncthreads();
 
       if (warp == 0) {
-        double tau = 0.0, scale = 0.0, beta = 0.0;
-        if (lane == 0) {
-          const double alpha = ge ? T[(size_t)j * ldt + j] : PV[j];
-          const double s2 = Pg[j];
-          beta = alpha;
-          if (s2 != 0.0) {
-            const double nrm = sqrt(fma(alpha, alpha, s2));
-            beta = (alpha < 0.0) ? nrm : -nrm;  // -sign(alpha)*||x||, sign(0) = +1
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
-          }
-        }
-        tau = __shfl_sync(kFull, tau, 0);
-        scale = __shfl_sync(kFull, scale, 0);
-        beta = __shfl_sync(kFull, beta, 0);
-        const double ts = tau * scale;
+        // every lane computes the (warp-uniform) scalars: a warp instruction costs the
+        // same with one active lane or 32
+        const Refl rf = reflector(ge ? T[(size_t)j * ldt + j] : PV[j], PC[j]);
         for (int c = j + 1 + lane; c < nc; c += 32) {
           const double pk = ge ? T[(size_t)c * ldt + j] : PV[c];
-          const double w = fma(scale, Pg[c], pk);  // v^T x over pivot row + tail
-          const double npk = fma(-tau, w, pk);
-          CF[c] = ts * w;
+          const double w = fma(rf.scale, PC[c], pk);  // v^T x over pivot row + tail
+          const double npk = fma(-rf.tau, w, pk);
+          PC[c] = rf.ts * w;
           if (ge)
             T[(size_t)c * ldt + j] = npk;
           else
@@ -213,16 +254,16 @@ __global__ void __launch_bounds__(kThreads) k_factor(const FactorParams p) {
         }
         if (lane == 0) {
           if (ge)
-            T[(size_t)j * ldt + j] = beta;
+            T[(size_t)j * ldt + j] = rf.beta;
           else
-            *piv_ptr(j, j) = beta;
-          p.tau[td.refl + j] = tau;
-          p.scl[td.refl + j] = scale;
+            *piv_ptr(j, j) = rf.beta;
+          p.tau[td.refl + j] = rf.tau;
+          p.scl[td.refl + j] = rf.scale;
         }
       }
       __syncthreads();
 
-      update_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, CF);
+      update_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
       if (do_pf) {
 #pragma unroll
         for (int q = 0; q < PFN; ++q) {
@@ -260,7 +301,7 @@ cudaError_t launch_factor_t(const FactorParams &p, int njobs, cudaStream_t s) {
 
 size_t factor_smem_bytes(int nc, int ldt) {
   const size_t ncp = (size_t)((nc + 7) & ~7);
-  return sizeof(double) * ((size_t)nc * (size_t)ldt + 3 * ncp);
+  return sizeof(double) * ((size_t)nc * (size_t)ldt + 2 * ncp);
 }
 
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
@@ -273,7 +314,7 @@ int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved
   const size_t extra = factor_smem_bytes(nc, 0);
   if (per_cta <= extra) return 0;
   int rows = (int)((per_cta - extra) / (sizeof(double) * (size_t)nc));
-  return rows & ~7;
+  return rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
 }
 
 cudaError_t launch_factor(const FactorParams &p, int njobs, cudaStream_t s) {

@@ -1,5 +1,5 @@
 """Parity at the benchmark's full size and launch configuration: 4,194,304 x 64 FP64,
-A = G diag(sigma) V^T with sigma from 1 to 1e-6, two-level tree, 216-row tiles.
+A = G diag(sigma) V^T with sigma from 1 to 1e-6, two-level tree, 224-row tiles.
 
 R is compared with the oracle's R of the whole matrix (relative Frobenius <= 1e-12);
 backward error ||A - QR||/||A|| and orthogonality ||Q^T Q - I|| are checked on rows the
@@ -23,7 +23,7 @@ def full_case(cuda_lib):
     A = inputs.graded(M, N, 6.0, seed_g=0, seed_v=1)
     b = inputs.gaussian(M, 1, seed=2)
     Ad = to_dev(A)
-    F = ts.factor(Ad, leaf_h=216, arity=2, two_level=True)
+    F = ts.factor(Ad, leaf_h=224, arity=2, two_level=True)
     Q = F.form_q()
     bd = to_dev(b)
     F.apply_qt(bd)
