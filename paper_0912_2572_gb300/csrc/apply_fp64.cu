@@ -10,12 +10,12 @@
 //   * k_apply_warp: one warp per job, for B with at most 8 columns. Each reflector is a
 //     dot product over the tile rows, one warp-level transpose-reduce, and an update; no
 //     block barrier is needed, so many jobs run per SM and hide the reduction latency.
-//   * k_apply_wide: one CTA per job and per pass of 32 columns, the same half-warp
-//     column mapping as the factor kernel. Used for many right-hand sides and for
-//     forming Q. When forming Q every pivot-row block stays upper triangular (the
-//     root starts from diag(sign(r_jj)) and each node's Q blocks are triangular), so
-//     reflector j only touches columns >= j and forming Q costs as many flops as the
-//     factorization, not twice as many.
+//   * k_apply_tile: one CTA per job and per pass of up to 64 columns, the structure of
+//     the factor kernel. Used for many right-hand sides and for forming Q. When forming
+//     Q every pivot-row block stays upper triangular (the root starts from
+//     diag(sign(r_jj)) and each node's Q blocks are triangular), so reflector j only
+//     touches columns >= j and forming Q costs as many flops as the factorization, not
+//     twice as many.
 #include "tsqr_internal.h"
 
 namespace tsqr {
@@ -89,23 +89,66 @@ __device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
   return v[0];
 }
 
-constexpr int kWarpRows = 16;  // rows per lane in k_apply_warp: tiles of at most 512 rows
+__host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
+
+// Runs BODY(r) for r = ra-1 down to 0 (ra <= 32, warp-uniform) through a fall-through
+// switch: only the row slots the reflector needs are issued (a predicated-off FP64
+// instruction still occupies the FP64 pipe), while r stays a compile-time register index.
+#define TSQR_ROW_SLOTS(ra, RM, BODY)                                                        \
+  switch ((ra) > (RM) ? (RM) : (ra)) {                                                      \
+    case 32: if (RM >= 32) BODY(31)                                                         \
+    case 31: if (RM >= 31) BODY(30)                                                         \
+    case 30: if (RM >= 30) BODY(29)                                                         \
+    case 29: if (RM >= 29) BODY(28)                                                         \
+    case 28: if (RM >= 28) BODY(27)                                                         \
+    case 27: if (RM >= 27) BODY(26)                                                         \
+    case 26: if (RM >= 26) BODY(25)                                                         \
+    case 25: if (RM >= 25) BODY(24)                                                         \
+    case 24: if (RM >= 24) BODY(23)                                                         \
+    case 23: if (RM >= 23) BODY(22)                                                         \
+    case 22: if (RM >= 22) BODY(21)                                                         \
+    case 21: if (RM >= 21) BODY(20)                                                         \
+    case 20: if (RM >= 20) BODY(19)                                                         \
+    case 19: if (RM >= 19) BODY(18)                                                         \
+    case 18: if (RM >= 18) BODY(17)                                                         \
+    case 17: if (RM >= 17) BODY(16)                                                         \
+    case 16: if (RM >= 16) BODY(15)                                                         \
+    case 15: if (RM >= 15) BODY(14)                                                         \
+    case 14: if (RM >= 14) BODY(13)                                                         \
+    case 13: if (RM >= 13) BODY(12)                                                         \
+    case 12: if (RM >= 12) BODY(11)                                                         \
+    case 11: if (RM >= 11) BODY(10)                                                         \
+    case 10: if (RM >= 10) BODY(9)                                                          \
+    case 9: if (RM >= 9) BODY(8)                                                            \
+    case 8: if (RM >= 8) BODY(7)                                                            \
+    case 7: if (RM >= 7) BODY(6)                                                            \
+    case 6: if (RM >= 6) BODY(5)                                                            \
+    case 5: if (RM >= 5) BODY(4)                                                            \
+    case 4: if (RM >= 4) BODY(3)                                                            \
+    case 3: if (RM >= 3) BODY(2)                                                            \
+    case 2: if (RM >= 2) BODY(1)                                                            \
+    case 1: BODY(0)                                                                         \
+    default: break;                                                                         \
+  }
 
 // ------------------------------------------------------------- one warp per job
-template <int KM>
-__global__ void __launch_bounds__(128) k_apply_warp(const ApplyParams p, int njobs) {
+// Lane l handles rows lo + l + 32 r of each reflector's tail (RW slots at most, entered
+// through TSQR_ROW_SLOTS so only the needed slots issue); the K columns of B are exact.
+template <int K, int RW>
+__global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int njobs) {
   extern __shared__ __align__(16) double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jid = blockIdx.x * 4 + warp;
   if (jid >= njobs) return;  // warp-uniform; this kernel uses no block barrier
-  const int n = p.n, k = p.k, ldt = p.ldt;
-  double *Bt = sm + (size_t)warp * ((size_t)ldt + n) * KM;  // tile rows, column-major
-  double *PR = Bt + (size_t)ldt * KM;                        // pivot rows, PR[c*n + j]
+  const int n = p.n, ldt = p.ldt;
+  double *Bt = sm + (size_t)warp * ((size_t)ldt + n) * K;  // tile rows, column-major
+  double *PR = Bt + (size_t)ldt * K;                        // pivot rows, PR[c*n + j]
   const JobDesc job = p.jobs[p.job0 + jid];
   const int64_t pr = job.piv_row;
   auto bcol = [&](int c) -> double * { return p.B + (int64_t)(p.col0 + c) * p.ldb; };
 
-  for (int c = 0; c < k; ++c)
+#pragma unroll
+  for (int c = 0; c < K; ++c)
     for (int j = lane; j < n; j += 32) PR[c * n + j] = bcol(c)[pr + j];
   __syncwarp();
 
@@ -116,7 +159,8 @@ __global__ void __launch_bounds__(128) k_apply_warp(const ApplyParams p, int njo
     const int ht = td.nrows, kind = td.kind;
     const bool ge = (kind == GEQRT);
     const int64_t r0 = td.row0;
-    for (int c = 0; c < k; ++c) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
       const double *src = bcol(c) + r0;
       for (int i = lane; i < ht; i += 32)
         Bt[c * ldt + i] = (ge && i < n) ? PR[c * n + i] : (p.formq ? 0.0 : src[i]);
@@ -124,15 +168,15 @@ __global__ void __launch_bounds__(128) k_apply_warp(const ApplyParams p, int njo
     __syncwarp();
 
     const double *Vt = p.V + r0;
-    double xv[kWarpRows], xn[kWarpRows];
+    double xv[RW], xn[RW];
     {
       const int j0 = p.trans ? 0 : n - 1;
       int lo, hi;
       refl_rows(kind, j0, ht, lo, hi);
 #pragma unroll
-      for (int r = 0; r < kWarpRows; ++r) {
-        const int i = lane + 32 * r;
-        xv[r] = (i >= lo && i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : 0.0;
+      for (int r = 0; r < RW; ++r) {
+        const int i = lo + lane + 32 * r;
+        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : 0.0;
       }
     }
     for (int s = 0; s < n; ++s) {
@@ -144,53 +188,56 @@ __global__ void __launch_bounds__(128) k_apply_warp(const ApplyParams p, int njo
         int lo2, hi2;
         refl_rows(kind, jn, ht, lo2, hi2);
 #pragma unroll
-        for (int r = 0; r < kWarpRows; ++r) {
-          const int i = lane + 32 * r;
-          xn[r] = (i >= lo2 && i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : 0.0;
+        for (int r = 0; r < RW; ++r) {
+          const int i = lo2 + lane + 32 * r;
+          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : 0.0;
         }
       }
       const double tau = __ldg(p.tau + td.refl + j);
       const double sc = __ldg(p.scl + td.refl + j);
-      double part[KM];
+      constexpr int KP = pow2ceil(K);
+      double part[KP];
 #pragma unroll
-      for (int c = 0; c < KM; ++c) part[c] = 0.0;
-#pragma unroll
-      for (int r = 0; r < kWarpRows; ++r) {
-        const int i = lane + 32 * r;
-        if (i >= lo && i < hi) {
-#pragma unroll
-          for (int c = 0; c < KM; ++c)
-            if (c < k) part[c] = fma(xv[r], Bt[c * ldt + i], part[c]);
-        }
-      }
+      for (int c = 0; c < KP; ++c) part[c] = 0.0;
+      const int ra = (hi - lo + 31) >> 5;
+#define TSQR_WDOT(r)                                                                        \
+  {                                                                                         \
+    const int i = lo + lane + 32 * (r);                                                     \
+    if (i < hi) {                                                                           \
+      _Pragma("unroll") for (int c = 0; c < K; ++c) part[c] = fma(xv[r], Bt[c * ldt + i], part[c]); \
+    }                                                                                       \
+  }
+      TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
+#undef TSQR_WDOT
       int idx;
-      const double tot = treduce32<KM>(part, lane, idx);
+      const double tot = treduce32<KP>(part, lane, idx);
       double cfv = 0.0;
-      if ((lane & (32 / KM - 1)) == 0 && idx < k) {
+      if ((lane & (32 / KP - 1)) == 0 && idx < K) {
         double *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
         const double piv = *pp;
         const double w = fma(sc, tot, piv);
         *pp = fma(-tau, w, piv);
         cfv = tau * sc * w;
       }
-      double cf[KM];
+      double cf[K];
 #pragma unroll
-      for (int c = 0; c < KM; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KM>(c));
+      for (int c = 0; c < K; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(c));
+      __syncwarp();
+#define TSQR_WUPD(r)                                                                        \
+  {                                                                                         \
+    const int i = lo + lane + 32 * (r);                                                     \
+    if (i < hi) {                                                                           \
+      _Pragma("unroll") for (int c = 0; c < K; ++c) Bt[c * ldt + i] = fma(-cf[c], xv[r], Bt[c * ldt + i]); \
+    }                                                                                       \
+  }
+      TSQR_ROW_SLOTS(ra, RW, TSQR_WUPD)
+#undef TSQR_WUPD
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < kWarpRows; ++r) {
-        const int i = lane + 32 * r;
-        if (i >= lo && i < hi) {
-#pragma unroll
-          for (int c = 0; c < KM; ++c)
-            if (c < k) Bt[c * ldt + i] = fma(-cf[c], xv[r], Bt[c * ldt + i]);
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < kWarpRows; ++r) xv[r] = xn[r];
+      for (int r = 0; r < RW; ++r) xv[r] = xn[r];
     }
-    for (int c = 0; c < k; ++c) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
       double *dst = bcol(c) + r0;
       for (int i = lane; i < ht; i += 32) {
         if (ge && i < n)
@@ -201,35 +248,123 @@ __global__ void __launch_bounds__(128) k_apply_warp(const ApplyParams p, int njo
     }
     __syncwarp();
   }
-  for (int c = 0; c < k; ++c)
+#pragma unroll
+  for (int c = 0; c < K; ++c)
     for (int j = lane; j < n; j += 32) bcol(c)[pr + j] = PR[c * n + j];
 }
 
 // ------------------------------------------------------------ one CTA per job
-constexpr int kWideThreads = 256;
-constexpr int kWideCM = 2;                 // column slots per half-warp
-constexpr int kWideCols = 16 * kWideCM;    // columns per pass
+// The structure of the factor kernel: the job's tile of B (up to 16*CMAX columns of this
+// pass) is staged in shared memory, the pivot row of each reflector is staged from
+// global memory (prefetched one reflector ahead), and the reflector tail is prefetched
+// into registers (every half-warp reads the same rows, so the loads hit L1). Half-warp hw
+// owns columns cs + hw + 16 t; each warp issues exactly its own slots.
+constexpr int kTileThreads = 256;
 
-__global__ void __launch_bounds__(kWideThreads) k_apply_wide(const ApplyParams p) {
+
+__device__ __forceinline__ int warp_slots(int cs, int nc, int warp) {
+  const int r = nc - cs - 2 * warp;
+  return r <= 0 ? 0 : (r + 15) >> 4;
+}
+
+// dots: PC[c] = sum_r xv[r] * Bt[c][lo + hl + 16 r] over rows < hi, c = cs + hw + 16 t
+template <int NS, int RM>
+__device__ __forceinline__ void tile_dots(const double *__restrict__ Bt, int ldt, int cs, int kc, int lo,
+                                          int hi, int hw, int hl, const double (&xv)[RM],
+                                          double *__restrict__ PC) {
+  constexpr int C = pow2ceil(NS);
+  const int cb = cs + hw;
+  double acc[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) acc[t] = 0.0;
+  const int ra = (hi - lo + 15) >> 4;
+#define TSQR_DOT_ROW(r)                                                                    \
+  {                                                                                          \
+    const int i = lo + hl + 16 * (r);                                                        \
+    if (i < hi) {                                                                            \
+      _Pragma("unroll") for (int t = 0; t < NS; ++t) {                                       \
+        const int c = cb + 16 * t;                                                           \
+        if (t < NS - 1 || c < kc) acc[t] = fma(xv[r], Bt[(size_t)c * ldt + i], acc[t]);     \
+      }                                                                                      \
+    }                                                                                        \
+  }
+  TSQR_ROW_SLOTS(ra, RM, TSQR_DOT_ROW)
+#undef TSQR_DOT_ROW
+  int idx;
+  const double sres = treduce16<C>(acc, hl, idx);
+  const int c = cb + 16 * idx;
+  if ((hl & (16 / C - 1)) == 0 && idx < NS && c < kc) PC[c] = sres;
+}
+
+template <int NS, int RM>
+__device__ __forceinline__ void tile_update(double *__restrict__ Bt, int ldt, int cs, int kc, int lo, int hi,
+                                           int hw, int hl, const double (&xv)[RM],
+                                           const double *__restrict__ CF) {
+  const int cb = cs + hw;
+  double cf[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int c = cb + 16 * t;
+    cf[t] = (c < kc) ? CF[c] : 0.0;
+  }
+  const int ra = (hi - lo + 15) >> 4;
+#define TSQR_UPD_ROW(r)                                                                    \
+  {                                                                                          \
+    const int i = lo + hl + 16 * (r);                                                        \
+    if (i < hi) {                                                                            \
+      _Pragma("unroll") for (int t = 0; t < NS; ++t) {                                       \
+        const int c = cb + 16 * t;                                                           \
+        if (t < NS - 1 || c < kc) {                                                          \
+          double *b = Bt + (size_t)c * ldt + i;                                              \
+          *b = fma(-cf[t], xv[r], *b);                                                       \
+        }                                                                                    \
+      }                                                                                      \
+    }                                                                                        \
+  }
+  TSQR_ROW_SLOTS(ra, RM, TSQR_UPD_ROW)
+#undef TSQR_UPD_ROW
+}
+
+template <int CMAX, int RM>
+__device__ __forceinline__ void dots_dispatch(const double *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
+                                              int hl, int warp, const double (&xv)[RM], double *PC) {
+  switch (warp_slots(cs, kc, warp)) {
+    case 0: return;
+    case 1: tile_dots<1, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
+    case 2: if (CMAX >= 2) tile_dots<(CMAX >= 2 ? 2 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
+    case 3: if (CMAX >= 4) tile_dots<(CMAX >= 4 ? 3 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
+    default: if (CMAX >= 4) tile_dots<(CMAX >= 4 ? 4 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
+  }
+}
+
+template <int CMAX, int RM>
+__device__ __forceinline__ void update_dispatch(double *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
+                                                int hl, int warp, const double (&xv)[RM], const double *CF) {
+  switch (warp_slots(cs, kc, warp)) {
+    case 0: return;
+    case 1: tile_update<1, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
+    case 2: if (CMAX >= 2) tile_update<(CMAX >= 2 ? 2 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
+    case 3: if (CMAX >= 4) tile_update<(CMAX >= 4 ? 3 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
+    default: if (CMAX >= 4) tile_update<(CMAX >= 4 ? 4 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
+  }
+}
+
+template <int CMAX, int RM>
+__global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile(const ApplyParams p) {
   extern __shared__ __align__(16) double sm[];
+  constexpr int KC = 16 * CMAX;
   const int n = p.n, ldt = p.ldt;
-  const int pass_col = blockIdx.y * kWideCols;
-  const int col0 = p.col0 + pass_col;
-  const int kc = min(kWideCols, p.k - pass_col);
-  double *Bt = sm;                               // ldt x kWideCols
-  double *PR = Bt + (size_t)ldt * kWideCols;     // n x kWideCols
-  double *Vc = PR + (size_t)n * kWideCols;       // 2 x ldt
-  double *Pg = Vc + 2 * (size_t)ldt;             // kWideCols
-  double *CF = Pg + kWideCols;                   // kWideCols
+  const int col0 = p.col0 + blockIdx.y * KC;
+  const int kc = min(KC, p.k - (int)blockIdx.y * KC);
+  double *Bt = sm;                        // KC columns of ldt rows
+  double *PC = Bt + (size_t)KC * ldt;     // dot products, then update coefficients
+  double *PV = PC + KC;                   // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
   const JobDesc job = p.jobs[p.job0 + blockIdx.x];
   const int64_t pr = job.piv_row;
-  auto bcol = [&](int c) -> double * { return p.B + (int64_t)(col0 + c) * p.ldb; };
-
-  for (int c = warp; c < kc; c += kWideThreads / 32)
-    for (int j = lane; j < n; j += 32) PR[c * n + j] = bcol(c)[pr + j];
-  __syncthreads();
+  auto bp = [&](int64_t row, int c) -> double * { return p.B + row + (int64_t)(col0 + c) * p.ldb; };
+  constexpr int PFN = (KC + 31) / 32;
 
   const int nt = job.tile_count;
   for (int q = 0; q < nt; ++q) {
@@ -239,140 +374,151 @@ __global__ void __launch_bounds__(kWideThreads) k_apply_wide(const ApplyParams p
     const bool ge = (kind == GEQRT);
     const int64_t r0 = td.row0;
     const double *Vt = p.V + r0;
-    for (int c = warp; c < kc; c += kWideThreads / 32) {
-      const double *src = bcol(c) + r0;
-      for (int i = lane; i < ht; i += 32)
-        Bt[(size_t)c * ldt + i] = (ge && i < n) ? PR[c * n + i] : (p.formq ? 0.0 : src[i]);
+    // stage the tile: when forming Q every row below the pivot block starts at zero
+    for (int c = warp; c < kc; c += kTileThreads / 32) {
+      const double *src = bp(r0, c);
+      double *dst = Bt + (size_t)c * ldt;
+      for (int i = lane; i < ht; i += 32) dst[i] = (p.formq && !(ge && i < n)) ? 0.0 : src[i];
     }
+    const int j0 = p.trans ? 0 : n - 1;
+    if (!ge)
+      for (int c = tid; c < kc; c += kTileThreads) PV[c] = __ldcg(bp(pr + j0, c));
+    double xv[RM], xn[RM];
     {
-      const int j0 = p.trans ? 0 : n - 1;
       int lo, hi;
       refl_rows(kind, j0, ht, lo, hi);
-      for (int i = lo + tid; i < hi; i += kWideThreads) Vc[i] = __ldg(Vt + i + (int64_t)j0 * p.ldv);
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        const int i = lo + hl + 16 * r;
+        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : 0.0;
+      }
     }
     __syncthreads();
 
     for (int s = 0; s < n; ++s) {
       const int j = p.trans ? s : n - 1 - s;
-      const int buf = s & 1;
-      const double *vc = Vc + (size_t)buf * ldt;
+      const bool more = (s + 1 < n);
+      const int jn = p.trans ? s + 1 : n - 2 - s;
       int lo, hi;
       refl_rows(kind, j, ht, lo, hi);
-      // prefetch the next reflector's tail into registers (at most 2 rows per thread)
-      double pf0 = 0.0, pf1 = 0.0;
-      int lo2 = 0, hi2 = 0;
-      if (s + 1 < n) {
-        const int jn = p.trans ? s + 1 : n - 2 - s;
-        refl_rows(kind, jn, ht, lo2, hi2);
-        const int i0 = lo2 + tid, i1 = lo2 + tid + kWideThreads;
-        if (i0 < hi2) pf0 = __ldg(Vt + i0 + (int64_t)jn * p.ldv);
-        if (i1 < hi2) pf1 = __ldg(Vt + i1 + (int64_t)jn * p.ldv);
-      }
       const int cs = p.formq ? max(0, j - col0) : 0;  // first column this reflector touches
-      if (cs < kc) {
-        // dot products of the reflector tail with the tile columns
-        const int cb = cs + hw;
-        if (cs + 2 * warp < kc) {
-          double acc[kWideCM];
+      // prefetch the next reflector's tail (registers) and pivot row (warp 1)
+      if (more) {
+        int lo2, hi2;
+        refl_rows(kind, jn, ht, lo2, hi2);
 #pragma unroll
-          for (int t = 0; t < kWideCM; ++t) acc[t] = 0.0;
-          for (int i = lo + hl; i < hi; i += 16) {
-            const double x = vc[i];
-#pragma unroll
-            for (int t = 0; t < kWideCM; ++t) {
-              const int c = cb + 16 * t;
-              if (c < kc) acc[t] = fma(x, Bt[(size_t)c * ldt + i], acc[t]);
-            }
-          }
-          int idx;
-          const double sres = treduce16<kWideCM>(acc, hl, idx);
-          const int c = cb + 16 * idx;
-          if ((hl & (16 / kWideCM - 1)) == 0 && c < kc) Pg[c] = sres;
+        for (int r = 0; r < RM; ++r) {
+          const int i = lo2 + hl + 16 * r;
+          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : 0.0;
         }
+      }
+      double pf[PFN];
+      const bool do_pf = (!ge) && warp == 1 && more;
+      if (do_pf) {
+#pragma unroll
+        for (int u = 0; u < PFN; ++u) {
+          const int c = lane + 32 * u;
+          pf[u] = (c < kc) ? __ldcg(bp(pr + jn, c)) : 0.0;
+        }
+      }
+      if (cs < kc) {
+        dots_dispatch<CMAX, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
         __syncthreads();
-        if (tid >= cs && tid < kc) {
+        if (warp == 0) {
           const double tau = __ldg(p.tau + td.refl + j);
           const double sc = __ldg(p.scl + td.refl + j);
-          const int c = tid;
-          double *pp = ge ? &Bt[(size_t)c * ldt + j] : &PR[c * n + j];
-          const double piv = *pp;
-          const double w = fma(sc, Pg[c], piv);
-          *pp = fma(-tau, w, piv);
-          CF[c] = tau * sc * w;
+          const double ts = tau * sc;
+          for (int c = cs + lane; c < kc; c += 32) {
+            const double piv = ge ? Bt[(size_t)c * ldt + j] : PV[c];
+            const double w = fma(sc, PC[c], piv);
+            const double np = fma(-tau, w, piv);
+            PC[c] = ts * w;
+            if (ge)
+              Bt[(size_t)c * ldt + j] = np;
+            else
+              *bp(pr + j, c) = np;
+          }
         }
         __syncthreads();
-        if (cs + 1 + 2 * warp - 1 < kc) {
-          double cf[kWideCM];
+        update_dispatch<CMAX, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
+      }
+      if (do_pf) {
 #pragma unroll
-          for (int t = 0; t < kWideCM; ++t) {
-            const int c = cb + 16 * t;
-            cf[t] = (c < kc) ? CF[c] : 0.0;
-          }
-          for (int i = lo + hl; i < hi; i += 16) {
-            const double x = vc[i];
-#pragma unroll
-            for (int t = 0; t < kWideCM; ++t) {
-              const int c = cb + 16 * t;
-              if (c < kc) {
-                double *b = Bt + (size_t)c * ldt + i;
-                *b = fma(-cf[t], x, *b);
-              }
-            }
-          }
+        for (int u = 0; u < PFN; ++u) {
+          const int c = lane + 32 * u;
+          if (c < kc) PV[c] = pf[u];
         }
       }
-      if (s + 1 < n) {
-        double *vn = Vc + (size_t)(buf ^ 1) * ldt;
-        const int i0 = lo2 + tid, i1 = lo2 + tid + kWideThreads;
-        if (i0 < hi2) vn[i0] = pf0;
-        if (i1 < hi2) vn[i1] = pf1;
-      }
+#pragma unroll
+      for (int r = 0; r < RM; ++r) xv[r] = xn[r];
       __syncthreads();
     }
-    for (int c = warp; c < kc; c += kWideThreads / 32) {
-      double *dst = bcol(c) + r0;
-      for (int i = lane; i < ht; i += 32) {
-        if (ge && i < n)
-          PR[c * n + i] = Bt[(size_t)c * ldt + i];
-        else
-          dst[i] = Bt[(size_t)c * ldt + i];
-      }
+    for (int c = warp; c < kc; c += kTileThreads / 32) {
+      double *dst = bp(r0, c);
+      const double *src = Bt + (size_t)c * ldt;
+      for (int i = lane; i < ht; i += 32) dst[i] = src[i];
     }
     __syncthreads();
   }
-  for (int c = warp; c < kc; c += kWideThreads / 32)
-    for (int j = lane; j < n; j += 32) bcol(c)[pr + j] = PR[c * n + j];
 }
 
-template <int KM>
-cudaError_t launch_warp_t(const ApplyParams &p, int njobs, cudaStream_t s) {
-  const size_t bytes = sizeof(double) * 4 * ((size_t)p.ldt + p.n) * KM;
-  cudaError_t e = cudaFuncSetAttribute(k_apply_warp<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int CMAX, int RM>
+cudaError_t launch_tile_t(const ApplyParams &p, int njobs, cudaStream_t s) {
+  constexpr int KC = 16 * CMAX;
+  const size_t bytes = sizeof(double) * ((size_t)KC * p.ldt + 2 * KC);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_tile<CMAX, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  k_apply_warp<KM><<<(njobs + 3) / 4, 128, bytes, s>>>(p, njobs);
+  dim3 grid(njobs, (p.k + KC - 1) / KC);
+  k_apply_tile<CMAX, RM><<<grid, kTileThreads, bytes, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int CMAX>
+cudaError_t launch_tile_rm(const ApplyParams &p, int njobs, cudaStream_t s) {
+  const int rows_per_lane = (p.ldt + 15) / 16;
+  if (rows_per_lane <= 8) return launch_tile_t<CMAX, 8>(p, njobs, s);
+  if (rows_per_lane <= 16) return launch_tile_t<CMAX, 16>(p, njobs, s);
+  return launch_tile_t<CMAX, 32>(p, njobs, s);
+}
+
+template <int K, int RW>
+cudaError_t launch_warp_t(const ApplyParams &p, int njobs, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * 4 * ((size_t)p.ldt + p.n) * K;
+  cudaError_t e = cudaFuncSetAttribute(k_apply_warp<K, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_apply_warp<K, RW><<<(njobs + 3) / 4, 128, bytes, s>>>(p, njobs);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_warp_k(const ApplyParams &p, int njobs, cudaStream_t s) {
+  if (p.ldt <= 256) return launch_warp_t<K, 8>(p, njobs, s);
+  return launch_warp_t<K, 16>(p, njobs, s);
 }
 
 }  // namespace
 
 cudaError_t launch_apply(const ApplyParams &p, int njobs, cudaStream_t s) {
   if (njobs <= 0 || p.k <= 0) return cudaSuccess;
-  if (p.k <= 8 && p.ldt <= 32 * kWarpRows) {
-    if (p.k == 1) return launch_warp_t<1>(p, njobs, s);
-    if (p.k == 2) return launch_warp_t<2>(p, njobs, s);
-    if (p.k <= 4) return launch_warp_t<4>(p, njobs, s);
-    return launch_warp_t<8>(p, njobs, s);
+  if (p.ldt > 512) return cudaErrorInvalidValue;
+  if (p.k <= 8 && !p.formq) {
+    switch (p.k) {
+      case 1: return launch_warp_k<1>(p, njobs, s);
+      case 2: return launch_warp_k<2>(p, njobs, s);
+      case 3: return launch_warp_k<3>(p, njobs, s);
+      case 4: return launch_warp_k<4>(p, njobs, s);
+      case 5: return launch_warp_k<5>(p, njobs, s);
+      case 6: return launch_warp_k<6>(p, njobs, s);
+      case 7: return launch_warp_k<7>(p, njobs, s);
+      default: return launch_warp_k<8>(p, njobs, s);
+    }
   }
-  if (p.ldt > 2 * kWideThreads) return cudaErrorInvalidValue;
-  const size_t bytes = sizeof(double) * ((size_t)p.ldt * kWideCols + (size_t)p.n * kWideCols +
-                                         2 * (size_t)p.ldt + 2 * kWideCols);
-  cudaError_t e = cudaFuncSetAttribute(k_apply_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
-  if (e != cudaSuccess) return e;
-  dim3 grid(njobs, (p.k + kWideCols - 1) / kWideCols);
-  k_apply_wide<<<grid, kWideThreads, bytes, s>>>(p);
-  return cudaGetLastError();
+  // up to 64 columns per pass; fewer columns use a narrower tile
+  if (p.k <= 16) return launch_tile_rm<1>(p, njobs, s);
+  if (p.k <= 32) return launch_tile_rm<2>(p, njobs, s);
+  return launch_tile_rm<4>(p, njobs, s);
 }
 
 }  // namespace tsqr
