@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TSQR Gflop/s & %roofline (4M×64 fp64); served LSQ solves/s, p99 vs plain path"
 FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20 TFLOP/s at 2.0 GHz)
+# DRAM bytes (read + write) per row of the factorization's chain launch, from the ncu
+# capture in profiles/k_factor_tsqr_fp64_4194304x64.md (m = 1,048,576, n = 64: 1.043 GB);
+# traffic grows with the rows, so it is scaled by m. Valid for n = 64 and that kernel build.
+CHAIN_DRAM_BYTES_PER_ROW_N64 = 1.043e9 / 1048576
 
 
 def flops_step(m, n, k=1):
@@ -376,7 +380,8 @@ def bench_ours(args):
                        "apply_qt_ms": phase_ms.get("apply_qt", 0) / args.steps,
                        "small_ms": phase_ms.get("small", 0) / args.steps},
             "roofline": {"kernel": "k_factor (leaf/flat-chain launch)", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (CHAIN_DRAM_BYTES_PER_ROW_N64 * m if n == 64 else None),
                          "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; no FP64 entry "
                                       "in the measured peaks)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
