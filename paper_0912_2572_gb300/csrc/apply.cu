@@ -25,8 +25,8 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Transpose-reduce over a full warp (C a power of two <= 32); see treduce16 in the
 // factor kernel. The lane ends with the warp total of value idx.
-template <int C>
-__device__ __forceinline__ double treduce32(double (&v)[C], int lane, int &idx) {
+template <int C, typename R>
+__device__ __forceinline__ R treduce32(R (&v)[C], int lane, int &idx) {
   idx = 0;
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
@@ -38,8 +38,8 @@ __device__ __forceinline__ double treduce32(double (&v)[C], int lane, int &idx) 
 #pragma unroll
       for (int i = 0; i < C / 2; ++i) {
         if (i < half) {
-          const double send = up ? v[i] : v[i + half];
-          const double keep = up ? v[i + half] : v[i];
+          const R send = up ? v[i] : v[i + half];
+          const R keep = up ? v[i + half] : v[i];
           v[i] = keep + __shfl_xor_sync(kFull, send, m);
         }
       }
@@ -63,8 +63,8 @@ __device__ __forceinline__ int treduce32_lane(int c) {
   return lane;
 }
 
-template <int C>
-__device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
+template <int C, typename R>
+__device__ __forceinline__ R treduce16(R (&v)[C], int hl, int &idx) {
   idx = 0;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -76,8 +76,8 @@ __device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
 #pragma unroll
       for (int i = 0; i < C / 2; ++i) {
         if (i < half) {
-          const double send = up ? v[i] : v[i + half];
-          const double keep = up ? v[i + half] : v[i];
+          const R send = up ? v[i] : v[i + half];
+          const R keep = up ? v[i + half] : v[i];
           v[i] = keep + __shfl_xor_sync(kFull, send, m);
         }
       }
@@ -134,18 +134,20 @@ __host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2
 // ------------------------------------------------------------- one warp per job
 // Lane l handles rows lo + l + 32 r of each reflector's tail (RW slots at most, entered
 // through TSQR_ROW_SLOTS so only the needed slots issue); the K columns of B are exact.
-template <int K, int RW>
-__global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int njobs) {
-  extern __shared__ __align__(16) double sm[];
+template <int K, int RW, typename R>
+__global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, int njobs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R *sm = reinterpret_cast<R *>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jid = blockIdx.x * 4 + warp;
   if (jid >= njobs) return;  // warp-uniform; this kernel uses no block barrier
+  if (p.done && *p.done) return;
   const int n = p.n, ldt = p.ldt;
-  double *Bt = sm + (size_t)warp * ((size_t)ldt + n) * K;  // tile rows, column-major
-  double *PR = Bt + (size_t)ldt * K;                        // pivot rows, PR[c*n + j]
+  R *Bt = sm + (size_t)warp * ((size_t)ldt + n) * K;  // tile rows, column-major
+  R *PR = Bt + (size_t)ldt * K;                        // pivot rows, PR[c*n + j]
   const JobDesc job = p.jobs[p.job0 + jid];
   const int64_t pr = job.piv_row;
-  auto bcol = [&](int c) -> double * { return p.B + (int64_t)(p.col0 + c) * p.ldb; };
+  auto bcol = [&](int c) -> R * { return p.B + (int64_t)(p.col0 + c) * p.ldb; };
 
 #pragma unroll
   for (int c = 0; c < K; ++c)
@@ -161,14 +163,14 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int 
     const int64_t r0 = td.row0;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      const double *src = bcol(c) + r0;
+      const R *src = bcol(c) + r0;
       for (int i = lane; i < ht; i += 32)
-        Bt[c * ldt + i] = (ge && i < n) ? PR[c * n + i] : (p.formq ? 0.0 : src[i]);
+        Bt[c * ldt + i] = (ge && i < n) ? PR[c * n + i] : (p.formq ? R(0) : src[i]);
     }
     __syncwarp();
 
-    const double *Vt = p.V + r0;
-    double xv[RW], xn[RW];
+    const R *Vt = p.V + r0;
+    R xv[RW], xn[RW];
     {
       const int j0 = p.trans ? 0 : n - 1;
       int lo, hi;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int 
 #pragma unroll
       for (int r = 0; r < RW; ++r) {
         const int i = lo + lane + 32 * r;
-        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : 0.0;
+        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : R(0);
       }
     }
     for (int s = 0; s < n; ++s) {
@@ -190,15 +192,15 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int 
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
           const int i = lo2 + lane + 32 * r;
-          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : 0.0;
+          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : R(0);
         }
       }
-      const double tau = __ldg(p.tau + td.refl + j);
-      const double sc = __ldg(p.scl + td.refl + j);
+      const R tau = __ldg(p.tau + td.refl + j);
+      const R sc = __ldg(p.scl + td.refl + j);
       constexpr int KP = pow2ceil(K);
-      double part[KP];
+      R part[KP];
 #pragma unroll
-      for (int c = 0; c < KP; ++c) part[c] = 0.0;
+      for (int c = 0; c < KP; ++c) part[c] = R(0);
       const int ra = (hi - lo + 31) >> 5;
 #define TSQR_WDOT(r)                                                                        \
   {                                                                                         \
@@ -210,16 +212,16 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int 
       TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
 #undef TSQR_WDOT
       int idx;
-      const double tot = treduce32<KP>(part, lane, idx);
-      double cfv = 0.0;
+      const R tot = treduce32<KP, R>(part, lane, idx);
+      R cfv = R(0);
       if ((lane & (32 / KP - 1)) == 0 && idx < K) {
-        double *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
-        const double piv = *pp;
-        const double w = fma(sc, tot, piv);
+        R *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
+        const R piv = *pp;
+        const R w = fma(sc, tot, piv);
         *pp = fma(-tau, w, piv);
         cfv = tau * sc * w;
       }
-      double cf[K];
+      R cf[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(c));
       __syncwarp();
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParams p, int 
     }
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      double *dst = bcol(c) + r0;
+      R *dst = bcol(c) + r0;
       for (int i = lane; i < ht; i += 32) {
         if (ge && i < n)
           PR[c * n + i] = Bt[c * ldt + i];
@@ -268,15 +270,15 @@ __device__ __forceinline__ int warp_slots(int cs, int nc, int warp) {
 }
 
 // dots: PC[c] = sum_r xv[r] * Bt[c][lo + hl + 16 r] over rows < hi, c = cs + hw + 16 t
-template <int NS, int RM>
-__device__ __forceinline__ void tile_dots(const double *__restrict__ Bt, int ldt, int cs, int kc, int lo,
-                                          int hi, int hw, int hl, const double (&xv)[RM],
-                                          double *__restrict__ PC) {
+template <int NS, int RM, typename R>
+__device__ __forceinline__ void tile_dots(const R *__restrict__ Bt, int ldt, int cs, int kc, int lo,
+                                          int hi, int hw, int hl, const R (&xv)[RM],
+                                          R *__restrict__ PC) {
   constexpr int C = pow2ceil(NS);
   const int cb = cs + hw;
-  double acc[C];
+  R acc[C];
 #pragma unroll
-  for (int t = 0; t < C; ++t) acc[t] = 0.0;
+  for (int t = 0; t < C; ++t) acc[t] = R(0);
   const int ra = (hi - lo + 15) >> 4;
 #define TSQR_DOT_ROW(r)                                                                    \
   {                                                                                          \
@@ -291,21 +293,21 @@ __device__ __forceinline__ void tile_dots(const double *__restrict__ Bt, int ldt
   TSQR_ROW_SLOTS(ra, RM, TSQR_DOT_ROW)
 #undef TSQR_DOT_ROW
   int idx;
-  const double sres = treduce16<C>(acc, hl, idx);
+  const R sres = treduce16<C, R>(acc, hl, idx);
   const int c = cb + 16 * idx;
   if ((hl & (16 / C - 1)) == 0 && idx < NS && c < kc) PC[c] = sres;
 }
 
-template <int NS, int RM>
-__device__ __forceinline__ void tile_update(double *__restrict__ Bt, int ldt, int cs, int kc, int lo, int hi,
-                                           int hw, int hl, const double (&xv)[RM],
-                                           const double *__restrict__ CF) {
+template <int NS, int RM, typename R>
+__device__ __forceinline__ void tile_update(R *__restrict__ Bt, int ldt, int cs, int kc, int lo, int hi,
+                                           int hw, int hl, const R (&xv)[RM],
+                                           const R *__restrict__ CF) {
   const int cb = cs + hw;
-  double cf[NS];
+  R cf[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
     const int c = cb + 16 * t;
-    cf[t] = (c < kc) ? CF[c] : 0.0;
+    cf[t] = (c < kc) ? CF[c] : R(0);
   }
   const int ra = (hi - lo + 15) >> 4;
 #define TSQR_UPD_ROW(r)                                                                    \
@@ -315,7 +317,7 @@ __device__ __forceinline__ void tile_update(double *__restrict__ Bt, int ldt, in
       _Pragma("unroll") for (int t = 0; t < NS; ++t) {                                       \
         const int c = cb + 16 * t;                                                           \
         if (t < NS - 1 || c < kc) {                                                          \
-          double *b = Bt + (size_t)c * ldt + i;                                              \
+          R *b = Bt + (size_t)c * ldt + i;                                                   \
           *b = fma(-cf[t], xv[r], *b);                                                       \
         }                                                                                    \
       }                                                                                      \
@@ -325,45 +327,47 @@ __device__ __forceinline__ void tile_update(double *__restrict__ Bt, int ldt, in
 #undef TSQR_UPD_ROW
 }
 
-template <int CMAX, int RM>
-__device__ __forceinline__ void dots_dispatch(const double *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
-                                              int hl, int warp, const double (&xv)[RM], double *PC) {
+template <int CMAX, int RM, typename R>
+__device__ __forceinline__ void dots_dispatch(const R *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
+                                              int hl, int warp, const R (&xv)[RM], R *PC) {
   switch (warp_slots(cs, kc, warp)) {
     case 0: return;
-    case 1: tile_dots<1, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
+    case 1: tile_dots<1, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
     case 2: if (CMAX >= 2) tile_dots<(CMAX >= 2 ? 2 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
     case 3: if (CMAX >= 4) tile_dots<(CMAX >= 4 ? 3 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
     default: if (CMAX >= 4) tile_dots<(CMAX >= 4 ? 4 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, PC); return;
   }
 }
 
-template <int CMAX, int RM>
-__device__ __forceinline__ void update_dispatch(double *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
-                                                int hl, int warp, const double (&xv)[RM], const double *CF) {
+template <int CMAX, int RM, typename R>
+__device__ __forceinline__ void update_dispatch(R *Bt, int ldt, int cs, int kc, int lo, int hi, int hw,
+                                                int hl, int warp, const R (&xv)[RM], const R *CF) {
   switch (warp_slots(cs, kc, warp)) {
     case 0: return;
-    case 1: tile_update<1, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
+    case 1: tile_update<1, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
     case 2: if (CMAX >= 2) tile_update<(CMAX >= 2 ? 2 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
     case 3: if (CMAX >= 4) tile_update<(CMAX >= 4 ? 3 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
     default: if (CMAX >= 4) tile_update<(CMAX >= 4 ? 4 : 1), RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, xv, CF); return;
   }
 }
 
-template <int CMAX, int RM>
-__global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile(const ApplyParams p) {
-  extern __shared__ __align__(16) double sm[];
+template <int CMAX, int RM, typename R>
+__global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile(const ApplyParamsT<R> p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R *sm = reinterpret_cast<R *>(smraw);
   constexpr int KC = 16 * CMAX;
+  if (p.done && *p.done) return;  // uniform over the grid
   const int n = p.n, ldt = p.ldt;
   const int col0 = p.col0 + blockIdx.y * KC;
   const int kc = min(KC, p.k - (int)blockIdx.y * KC);
-  double *Bt = sm;                        // KC columns of ldt rows
-  double *PC = Bt + (size_t)KC * ldt;     // dot products, then update coefficients
-  double *PV = PC + KC;                   // staged pivot row (TSQRT / TTQRT)
+  R *Bt = sm;                        // KC columns of ldt rows
+  R *PC = Bt + (size_t)KC * ldt;     // dot products, then update coefficients
+  R *PV = PC + KC;                   // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
   const JobDesc job = p.jobs[p.job0 + blockIdx.x];
   const int64_t pr = job.piv_row;
-  auto bp = [&](int64_t row, int c) -> double * { return p.B + row + (int64_t)(col0 + c) * p.ldb; };
+  auto bp = [&](int64_t row, int c) -> R * { return p.B + row + (int64_t)(col0 + c) * p.ldb; };
   constexpr int PFN = (KC + 31) / 32;
 
   const int nt = job.tile_count;
@@ -373,24 +377,24 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
     const int ht = td.nrows, kind = td.kind;
     const bool ge = (kind == GEQRT);
     const int64_t r0 = td.row0;
-    const double *Vt = p.V + r0;
+    const R *Vt = p.V + r0;
     // stage the tile: when forming Q every row below the pivot block starts at zero
     for (int c = warp; c < kc; c += kTileThreads / 32) {
-      const double *src = bp(r0, c);
-      double *dst = Bt + (size_t)c * ldt;
-      for (int i = lane; i < ht; i += 32) dst[i] = (p.formq && !(ge && i < n)) ? 0.0 : src[i];
+      const R *src = bp(r0, c);
+      R *dst = Bt + (size_t)c * ldt;
+      for (int i = lane; i < ht; i += 32) dst[i] = (p.formq && !(ge && i < n)) ? R(0) : src[i];
     }
     const int j0 = p.trans ? 0 : n - 1;
     if (!ge)
       for (int c = tid; c < kc; c += kTileThreads) PV[c] = __ldcg(bp(pr + j0, c));
-    double xv[RM], xn[RM];
+    R xv[RM], xn[RM];
     {
       int lo, hi;
       refl_rows(kind, j0, ht, lo, hi);
 #pragma unroll
       for (int r = 0; r < RM; ++r) {
         const int i = lo + hl + 16 * r;
-        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : 0.0;
+        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : R(0);
       }
     }
     __syncthreads();
@@ -409,29 +413,29 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
           const int i = lo2 + hl + 16 * r;
-          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : 0.0;
+          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : R(0);
         }
       }
-      double pf[PFN];
+      R pf[PFN];
       const bool do_pf = (!ge) && warp == 1 && more;
       if (do_pf) {
 #pragma unroll
         for (int u = 0; u < PFN; ++u) {
           const int c = lane + 32 * u;
-          pf[u] = (c < kc) ? __ldcg(bp(pr + jn, c)) : 0.0;
+          pf[u] = (c < kc) ? __ldcg(bp(pr + jn, c)) : R(0);
         }
       }
       if (cs < kc) {
-        dots_dispatch<CMAX, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
+        dots_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
         __syncthreads();
         if (warp == 0) {
-          const double tau = __ldg(p.tau + td.refl + j);
-          const double sc = __ldg(p.scl + td.refl + j);
-          const double ts = tau * sc;
+          const R tau = __ldg(p.tau + td.refl + j);
+          const R sc = __ldg(p.scl + td.refl + j);
+          const R ts = tau * sc;
           for (int c = cs + lane; c < kc; c += 32) {
-            const double piv = ge ? Bt[(size_t)c * ldt + j] : PV[c];
-            const double w = fma(sc, PC[c], piv);
-            const double np = fma(-tau, w, piv);
+            const R piv = ge ? Bt[(size_t)c * ldt + j] : PV[c];
+            const R w = fma(sc, PC[c], piv);
+            const R np = fma(-tau, w, piv);
             PC[c] = ts * w;
             if (ge)
               Bt[(size_t)c * ldt + j] = np;
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
           }
         }
         __syncthreads();
-        update_dispatch<CMAX, RM>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
+        update_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
       }
       if (do_pf) {
 #pragma unroll
@@ -454,71 +458,80 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
       __syncthreads();
     }
     for (int c = warp; c < kc; c += kTileThreads / 32) {
-      double *dst = bp(r0, c);
-      const double *src = Bt + (size_t)c * ldt;
+      R *dst = bp(r0, c);
+      const R *src = Bt + (size_t)c * ldt;
       for (int i = lane; i < ht; i += 32) dst[i] = src[i];
     }
     __syncthreads();
   }
 }
 
-template <int CMAX, int RM>
-cudaError_t launch_tile_t(const ApplyParams &p, int njobs, cudaStream_t s) {
+template <int CMAX, int RM, typename R>
+cudaError_t launch_tile_t(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   constexpr int KC = 16 * CMAX;
-  const size_t bytes = sizeof(double) * ((size_t)KC * p.ldt + 2 * KC);
-  cudaError_t e = cudaFuncSetAttribute(k_apply_tile<CMAX, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t bytes = sizeof(R) * ((size_t)KC * p.ldt + 2 * KC);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_tile<CMAX, RM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
   dim3 grid(njobs, (p.k + KC - 1) / KC);
-  k_apply_tile<CMAX, RM><<<grid, kTileThreads, bytes, s>>>(p);
+  k_apply_tile<CMAX, RM, R><<<grid, kTileThreads, bytes, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int CMAX>
-cudaError_t launch_tile_rm(const ApplyParams &p, int njobs, cudaStream_t s) {
+template <int CMAX, typename R>
+cudaError_t launch_tile_rm(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   const int rows_per_lane = (p.ldt + 15) / 16;
-  if (rows_per_lane <= 8) return launch_tile_t<CMAX, 8>(p, njobs, s);
-  if (rows_per_lane <= 16) return launch_tile_t<CMAX, 16>(p, njobs, s);
-  return launch_tile_t<CMAX, 32>(p, njobs, s);
+  if (rows_per_lane <= 8) return launch_tile_t<CMAX, 8, R>(p, njobs, s);
+  if (rows_per_lane <= 16) return launch_tile_t<CMAX, 16, R>(p, njobs, s);
+  return launch_tile_t<CMAX, 32, R>(p, njobs, s);
 }
 
-template <int K, int RW>
-cudaError_t launch_warp_t(const ApplyParams &p, int njobs, cudaStream_t s) {
-  const size_t bytes = sizeof(double) * 4 * ((size_t)p.ldt + p.n) * K;
-  cudaError_t e = cudaFuncSetAttribute(k_apply_warp<K, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int K, int RW, typename R>
+cudaError_t launch_warp_t(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
+  const size_t bytes = sizeof(R) * 4 * ((size_t)p.ldt + p.n) * K;
+  cudaError_t e = cudaFuncSetAttribute(k_apply_warp<K, RW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  k_apply_warp<K, RW><<<(njobs + 3) / 4, 128, bytes, s>>>(p, njobs);
+  k_apply_warp<K, RW, R><<<(njobs + 3) / 4, 128, bytes, s>>>(p, njobs);
   return cudaGetLastError();
 }
 
-template <int K>
-cudaError_t launch_warp_k(const ApplyParams &p, int njobs, cudaStream_t s) {
-  if (p.ldt <= 256) return launch_warp_t<K, 8>(p, njobs, s);
-  return launch_warp_t<K, 16>(p, njobs, s);
+template <int K, typename R>
+cudaError_t launch_warp_k(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
+  if (p.ldt <= 256) return launch_warp_t<K, 8, R>(p, njobs, s);
+  return launch_warp_t<K, 16, R>(p, njobs, s);
 }
 
-}  // namespace
-
-cudaError_t launch_apply(const ApplyParams &p, int njobs, cudaStream_t s) {
+template <typename R>
+cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   if (njobs <= 0 || p.k <= 0) return cudaSuccess;
   if (p.ldt > 512) return cudaErrorInvalidValue;
   if (p.k <= 8 && !p.formq) {
     switch (p.k) {
-      case 1: return launch_warp_k<1>(p, njobs, s);
-      case 2: return launch_warp_k<2>(p, njobs, s);
-      case 3: return launch_warp_k<3>(p, njobs, s);
-      case 4: return launch_warp_k<4>(p, njobs, s);
-      case 5: return launch_warp_k<5>(p, njobs, s);
-      case 6: return launch_warp_k<6>(p, njobs, s);
-      case 7: return launch_warp_k<7>(p, njobs, s);
-      default: return launch_warp_k<8>(p, njobs, s);
+      case 1: return launch_warp_k<1, R>(p, njobs, s);
+      case 2: return launch_warp_k<2, R>(p, njobs, s);
+      case 3: return launch_warp_k<3, R>(p, njobs, s);
+      case 4: return launch_warp_k<4, R>(p, njobs, s);
+      case 5: return launch_warp_k<5, R>(p, njobs, s);
+      case 6: return launch_warp_k<6, R>(p, njobs, s);
+      case 7: return launch_warp_k<7, R>(p, njobs, s);
+      default: return launch_warp_k<8, R>(p, njobs, s);
     }
   }
   // up to 64 columns per pass; fewer columns use a narrower tile
-  if (p.k <= 16) return launch_tile_rm<1>(p, njobs, s);
-  if (p.k <= 32) return launch_tile_rm<2>(p, njobs, s);
-  return launch_tile_rm<4>(p, njobs, s);
+  if (p.k <= 16) return launch_tile_rm<1, R>(p, njobs, s);
+  if (p.k <= 32) return launch_tile_rm<2, R>(p, njobs, s);
+  return launch_tile_rm<4, R>(p, njobs, s);
+}
+
+}  // namespace
+
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s) {
+  return launch_apply_any(p, njobs, s);
+}
+
+cudaError_t launch_apply(const ApplyParamsT<float> &p, int njobs, cudaStream_t s) {
+  return launch_apply_any(p, njobs, s);
 }
 
 }  // namespace tsqr

@@ -1,4 +1,4 @@
-// FP64 TSQR factorization kernel (sm_103a).
+// TSQR factorization kernel (sm_103a), FP64 and FP32 instantiations.
 //
 // One CTA runs one job (a chain of tiles sharing n pivot rows, see tsqr_internal.h).
 // Each tile is staged in shared memory and factored column by column with Householder
@@ -33,8 +33,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // (C a power of two <= 16). Stage s exchanges half of the values with the lane whose
 // bit (8 >> s) differs and adds, until one value is left, then plain butterflies
 // finish the sum. The lane ends with the half-warp total of value `idx`.
-template <int C>
-__device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
+template <int C, typename R>
+__device__ __forceinline__ R treduce16(R (&v)[C], int hl, int &idx) {
   idx = 0;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -46,8 +46,8 @@ __device__ __forceinline__ double treduce16(double (&v)[C], int hl, int &idx) {
 #pragma unroll
       for (int i = 0; i < C / 2; ++i) {
         if (i < half) {
-          const double send = up ? v[i] : v[i + half];
-          const double keep = up ? v[i + half] : v[i];
+          const R send = up ? v[i] : v[i + half];
+          const R keep = up ? v[i + half] : v[i];
           v[i] = keep + __shfl_xor_sync(kFull, send, m);
         }
       }
@@ -65,17 +65,17 @@ __host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2
 // is the squared norm of the pivot column's tail). Half-warp hw owns columns
 // j + hw + 16 t; this warp has exactly NS slots (t < NS), so no predicated-off DFMA is
 // issued; only half-warp 1 of the last slot can fall past nc.
-template <int NS>
-__device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, int j, int nc, int lo,
-                                         int hi, int hw, int hl, double *__restrict__ Pg) {
+template <int NS, typename R>
+__device__ __forceinline__ void gram_row(const R *__restrict__ T, int ldt, int j, int nc, int lo,
+                                         int hi, int hw, int hl, R *__restrict__ Pg) {
   constexpr int C = pow2ceil(NS);
   const int cb = j + hw;
-  double acc[C];
+  R acc[C];
 #pragma unroll
-  for (int t = 0; t < C; ++t) acc[t] = 0.0;
-  const double *Tj = T + (size_t)j * ldt;
+  for (int t = 0; t < C; ++t) acc[t] = R(0);
+  const R *Tj = T + (size_t)j * ldt;
   for (int i = lo + hl; i < hi; i += 16) {
-    const double x = Tj[i];
+    const R x = Tj[i];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       const int c = cb + 16 * t;
@@ -83,31 +83,31 @@ __device__ __forceinline__ void gram_row(const double *__restrict__ T, int ldt, 
     }
   }
   int idx;
-  const double s = treduce16<C>(acc, hl, idx);
+  const R s = treduce16<C, R>(acc, hl, idx);
   const int c = cb + 16 * idx;
   if ((hl & (16 / C - 1)) == 0 && idx < NS && c < nc) Pg[c] = s;
 }
 
 // Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c in (j, nc), i in [lo, hi);
 // half-warp hw owns columns j + 1 + hw + 16 t, this warp has exactly NS slots.
-template <int NS>
-__device__ __forceinline__ void trailing_update(double *__restrict__ T, int ldt, int j, int nc, int lo,
-                                                int hi, int hw, int hl, const double *__restrict__ CF) {
+template <int NS, typename R>
+__device__ __forceinline__ void trailing_update(R *__restrict__ T, int ldt, int j, int nc, int lo,
+                                                int hi, int hw, int hl, const R *__restrict__ CF) {
   const int cb = j + 1 + hw;
-  double cf[NS];
+  R cf[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
     const int c = cb + 16 * t;
-    cf[t] = (c < nc) ? CF[c] : 0.0;
+    cf[t] = (c < nc) ? CF[c] : R(0);
   }
-  const double *Tj = T + (size_t)j * ldt;
+  const R *Tj = T + (size_t)j * ldt;
   for (int i = lo + hl; i < hi; i += 16) {
-    const double x = Tj[i];
+    const R x = Tj[i];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       const int c = cb + 16 * t;
       if (t < NS - 1 || c < nc) {
-        double *q = T + (size_t)c * ldt + i;
+        R *q = T + (size_t)c * ldt + i;
         *q = fma(-cf[t], x, *q);
       }
     }
@@ -120,35 +120,35 @@ __device__ __forceinline__ int warp_slots(int cs, int nc, int warp) {
   return r <= 0 ? 0 : (r + 15) >> 4;
 }
 
-template <int CMAX>
-__device__ __forceinline__ void gram_row_dispatch(const double *T, int ldt, int j, int nc, int lo, int hi,
-                                                  int hw, int hl, int warp, double *Pg) {
+template <int CMAX, typename R>
+__device__ __forceinline__ void gram_row_dispatch(const R *T, int ldt, int j, int nc, int lo, int hi,
+                                                  int hw, int hl, int warp, R *Pg) {
   switch (warp_slots(j, nc, warp)) {
     case 0: return;
-    case 1: gram_row<1>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 2: if (CMAX >= 2) gram_row<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 3: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 3 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 4: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 5: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 5 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 6: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 6 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 7: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 7 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    default: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 1: gram_row<1, R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 2: if (CMAX >= 2) gram_row<(CMAX >= 2 ? 2 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 3: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 3 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 4: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 4 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 5: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 6: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 7: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    default: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
   }
 }
 
-template <int CMAX>
-__device__ __forceinline__ void update_dispatch(double *T, int ldt, int j, int nc, int lo, int hi, int hw,
-                                                int hl, int warp, const double *CF) {
+template <int CMAX, typename R>
+__device__ __forceinline__ void update_dispatch(R *T, int ldt, int j, int nc, int lo, int hi, int hw,
+                                                int hl, int warp, const R *CF) {
   switch (warp_slots(j + 1, nc, warp)) {
     case 0: return;
-    case 1: trailing_update<1>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 2: if (CMAX >= 2) trailing_update<(CMAX >= 2 ? 2 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 3: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 3 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 4: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 4 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 5: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 5 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 6: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 6 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 7: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 7 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    default: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1)>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 1: trailing_update<1, R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 2: if (CMAX >= 2) trailing_update<(CMAX >= 2 ? 2 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 3: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 3 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 4: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 4 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 5: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 6: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 7: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    default: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
   }
 }
 
@@ -158,47 +158,53 @@ __device__ __forceinline__ void update_dispatch(double *T, int ldt, int j, int n
 //   scale = sign(alpha) / (|alpha| + nrm),  tau = 1 + |alpha| / nrm,
 //   tau * scale = sign(alpha) / nrm,
 // which needs one reciprocal square root and one division. s2 == 0 gives H = I.
+template <typename R>
 struct Refl {
-  double tau, scale, beta, ts;
+  R tau, scale, beta, ts;
 };
 
-__device__ __forceinline__ Refl reflector(double alpha, double s2) {
-  Refl r;
-  if (s2 == 0.0) {
-    r.tau = 0.0;
-    r.scale = 0.0;
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+template <typename R>
+__device__ __forceinline__ Refl<R> reflector(R alpha, R s2) {
+  Refl<R> r;
+  if (s2 == R(0)) {
+    r.tau = R(0);
+    r.scale = R(0);
     r.beta = alpha;
-    r.ts = 0.0;
+    r.ts = R(0);
     return r;
   }
-  const double s = fma(alpha, alpha, s2);
-  const double rn = rsqrt(s);
-  const double nrm = s * rn;
-  const double sg = (alpha < 0.0) ? -1.0 : 1.0;
-  const double aa = fabs(alpha);
+  const R s = fma(alpha, alpha, s2);
+  const R rn = rsqrt_t(s);
+  const R nrm = s * rn;
+  const R sg = (alpha < R(0)) ? R(-1) : R(1);
+  const R aa = fabs(alpha);
   r.beta = -sg * nrm;
   r.scale = sg / (aa + nrm);
-  r.tau = fma(aa, rn, 1.0);
+  r.tau = fma(aa, rn, R(1));
   r.ts = sg * rn;
   return r;
 }
 
-template <int CMAX>
-__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
-  extern __shared__ __align__(16) double sm[];
+template <int CMAX, typename R>
+__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R *sm = reinterpret_cast<R *>(smraw);
   const int n = p.n, nc = p.nc, ldt = p.ldt;
   const int ncp = (nc + 7) & ~7;
-  double *T = sm;                       // tile, column-major, nc columns of ldt rows
-  double *PC = T + (size_t)nc * ldt;    // Gram row of the step, then (in place) the
+  R *T = sm;                            // tile, column-major, nc columns of ldt rows
+  R *PC = T + (size_t)nc * ldt;         // Gram row of the step, then (in place) the
                                         // update coefficients tau*scale*w_k
-  double *PV = PC + ncp;                // staged pivot row (TSQRT / TTQRT)
+  R *PV = PC + ncp;                     // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
   const JobDesc job = p.jobs[p.job0 + blockIdx.x];
   const int64_t pr = job.piv_row;
 
   // pivot-row element (row pr + j, column c) in global memory
-  auto piv_ptr = [&](int j, int c) -> double * {
+  auto piv_ptr = [&](int j, int c) -> R * {
     return (c < n) ? p.V + pr + j + (int64_t)c * p.ldv : p.B + pr + j + (int64_t)(c - n) * p.ldb;
   };
   constexpr int PFN = (CMAX * 16 + 31) / 32;
@@ -211,11 +217,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
 
     // stage the tile: GEQRT/TSQRT tiles come from A (first touch), TTQRT from V
     for (int c = warp; c < nc; c += kThreads / 32) {
-      const double *src = (c < n) ? ((kind == TTQRT) ? p.V + r0 + (int64_t)c * p.ldv
-                                                     : p.A + r0 + (int64_t)c * p.lda)
-                                  : p.B + r0 + (int64_t)(c - n) * p.ldb;
-      double *dst = T + (size_t)c * ldt;
-      for (int i = lane; i < ht; i += 32) dst[i] = src[i];
+      R *dst = T + (size_t)c * ldt;
+      if (c < n && kind != TTQRT) {  // input A is FP64; the FP32 path rounds on load
+        const double *src = p.A + r0 + (int64_t)c * p.lda;
+        for (int i = lane; i < ht; i += 32) dst[i] = R(src[i]);
+      } else {
+        const R *src = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
+        for (int i = lane; i < ht; i += 32) dst[i] = src[i];
+      }
     }
     if (!ge)
       for (int c = tid; c < nc; c += kThreads) PV[c] = __ldcg(piv_ptr(0, c));
@@ -225,27 +234,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
       int lo, hi;
       refl_rows(kind, j, ht, lo, hi);
       // warp 1 prefetches pivot row j+1 (not written before step j+1)
-      double pf[PFN];
+      R pf[PFN];
       const bool do_pf = (!ge) && warp == 1 && (j + 1 < n);
       if (do_pf) {
 #pragma unroll
         for (int q = 0; q < PFN; ++q) {
           const int c = j + 1 + lane + 32 * q;
-          pf[q] = (c < nc) ? __ldcg(piv_ptr(j + 1, c)) : 0.0;
+          pf[q] = (c < nc) ? __ldcg(piv_ptr(j + 1, c)) : R(0);
         }
       }
 
-      gram_row_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
+      gram_row_dispatch<CMAX, R>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
       __syncthreads();
 
       if (warp == 0) {
         // every lane computes the (warp-uniform) scalars: a warp instruction costs the
         // same with one active lane or 32
-        const Refl rf = reflector(ge ? T[(size_t)j * ldt + j] : PV[j], PC[j]);
+        const Refl<R> rf = reflector<R>(ge ? T[(size_t)j * ldt + j] : PV[j], PC[j]);
         for (int c = j + 1 + lane; c < nc; c += 32) {
-          const double pk = ge ? T[(size_t)c * ldt + j] : PV[c];
-          const double w = fma(rf.scale, PC[c], pk);  // v^T x over pivot row + tail
-          const double npk = fma(-rf.tau, w, pk);
+          const R pk = ge ? T[(size_t)c * ldt + j] : PV[c];
+          const R w = fma(rf.scale, PC[c], pk);  // v^T x over pivot row + tail
+          const R npk = fma(-rf.tau, w, pk);
           PC[c] = rf.ts * w;
           if (ge)
             T[(size_t)c * ldt + j] = npk;
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
       }
       __syncthreads();
 
-      update_dispatch<CMAX>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
+      update_dispatch<CMAX, R>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
       if (do_pf) {
 #pragma unroll
         for (int q = 0; q < PFN; ++q) {
@@ -278,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
     // reflector tails, TTQRT -> the upper triangle only (the child's own leaf
     // reflectors live below its diagonal)
     for (int c = warp; c < nc; c += kThreads / 32) {
-      double *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
-      const double *src = T + (size_t)c * ldt;
+      R *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
+      const R *src = T + (size_t)c * ldt;
       const int lim = (kind == TTQRT && c < n) ? min(ht, c + 1) : ht;
       for (int i = lane; i < lim; i += 32) dst[i] = src[i];
     }
@@ -287,42 +296,51 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParams p) {
   }
 }
 
-template <int CMAX>
-cudaError_t launch_factor_t(const FactorParams &p, int njobs, cudaStream_t s) {
-  const size_t bytes = factor_smem_bytes(p.nc, p.ldt);
-  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int CMAX, typename R>
+cudaError_t launch_factor_t(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
+  const size_t bytes = factor_smem_bytes(p.nc, p.ldt, sizeof(R));
+  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  k_factor<CMAX><<<njobs, kThreads, bytes, s>>>(p);
+  k_factor<CMAX, R><<<njobs, kThreads, bytes, s>>>(p);
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_factor_any(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  if (p.nc <= 16) return launch_factor_t<1, R>(p, njobs, s);
+  if (p.nc <= 32) return launch_factor_t<2, R>(p, njobs, s);
+  if (p.nc <= 64) return launch_factor_t<4, R>(p, njobs, s);
+  return launch_factor_t<8, R>(p, njobs, s);
 }
 
 }  // namespace
 
-size_t factor_smem_bytes(int nc, int ldt) {
+size_t factor_smem_bytes(int nc, int ldt, size_t elem) {
   const size_t ncp = (size_t)((nc + 7) & ~7);
-  return sizeof(double) * ((size_t)nc * (size_t)ldt + 2 * ncp);
+  return elem * ((size_t)nc * (size_t)ldt + 2 * ncp);
 }
 
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
-                    size_t optin_per_block) {
+                    size_t optin_per_block, size_t elem) {
   if (ctas_per_sm < 1) return 0;
   size_t per_cta = smem_per_sm / (size_t)ctas_per_sm;
   if (per_cta <= reserved_per_block) return 0;
   per_cta -= reserved_per_block;
   if (per_cta > optin_per_block) per_cta = optin_per_block;
-  const size_t extra = factor_smem_bytes(nc, 0);
+  const size_t extra = factor_smem_bytes(nc, 0, elem);
   if (per_cta <= extra) return 0;
-  int rows = (int)((per_cta - extra) / (sizeof(double) * (size_t)nc));
+  int rows = (int)((per_cta - extra) / (elem * (size_t)nc));
   return rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
 }
 
-cudaError_t launch_factor(const FactorParams &p, int njobs, cudaStream_t s) {
-  if (njobs <= 0) return cudaSuccess;
-  if (p.nc <= 16) return launch_factor_t<1>(p, njobs, s);
-  if (p.nc <= 32) return launch_factor_t<2>(p, njobs, s);
-  if (p.nc <= 64) return launch_factor_t<4>(p, njobs, s);
-  return launch_factor_t<8>(p, njobs, s);
+cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {
+  return launch_factor_any(p, njobs, s);
+}
+
+cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s) {
+  return launch_factor_any(p, njobs, s);
 }
 
 }  // namespace tsqr

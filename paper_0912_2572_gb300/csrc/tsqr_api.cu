@@ -125,6 +125,7 @@ struct ProfScope {
 struct Plan {
   int64_t m = 0;
   int n = 0, nc = 0, leaf_h = 0, arity = 0, flags = 0, tile_h = 0, ctas_per_sm = 0;
+  bool mixed = false;  // FP32 chains on global rows, FP64 tree on compact pivot blocks
   int64_t leaves = 0;
   std::vector<TileDesc> tiles;
   std::vector<JobDesc> jobs;
@@ -189,9 +190,10 @@ static void plan_build(Plan &pl, int64_t chains_target) {
 // Chooses the tile height and CTAs per SM of the factor kernel for nc columns: two
 // resident CTAs when the tile still holds at least n rows (one CTA's scalar phase is
 // then hidden behind the other's updates), otherwise one.
-static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &tile_h, int &cps) {
+static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &tile_h, int &cps,
+                         size_t elem = sizeof(double)) {
   for (int c = 2; c >= 1; --c) {
-    int rows = factor_max_rows(nc, c, di.smem_sm, di.reserved, di.optin);
+    int rows = factor_max_rows(nc, c, di.smem_sm, di.reserved, di.optin, elem);
     rows = std::min(rows, 512);  // the apply kernels stage at most 512 rows per tile
     if (rows >= n && rows >= 8) {
       tile_h = std::min(rows, std::max(leaf_h, n));
@@ -203,18 +205,39 @@ static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &t
 }
 
 static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
-                                int arity, int flags) {
+                                int arity, int flags, bool mixed = false) {
   pl.m = m;
   pl.n = n;
   pl.nc = nc;
   pl.leaf_h = leaf_h;
   pl.arity = arity;
   pl.flags = flags & TSQR_TWO_LEVEL;
-  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm))
+  pl.mixed = mixed;
+  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double)))
     return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
   const int64_t chains = (int64_t)di.sms * pl.ctas_per_sm * 4;
   try {
     plan_build(pl, chains);
+    if (mixed) {
+      // the tree works on a compact FP64 array: chain c's pivot block at rows c*n..c*n+n-1
+      std::vector<std::pair<int64_t, int64_t>> idx;  // (global pivot row, chain)
+      const int32_t G = pl.launches[0].job_count;
+      for (int32_t c = 0; c < G; ++c) idx.push_back({pl.jobs[c].piv_row, c});
+      std::sort(idx.begin(), idx.end());
+      auto compact = [&](int64_t row) {
+        auto it = std::lower_bound(idx.begin(), idx.end(), std::make_pair(row, (int64_t)-1));
+        return it->second * (int64_t)n;
+      };
+      for (size_t q = 1; q < pl.launches.size(); ++q) {
+        const LaunchDesc &ld = pl.launches[q];
+        for (int32_t jb = ld.job_begin; jb < ld.job_begin + ld.job_count; ++jb) {
+          JobDesc &jd = pl.jobs[jb];
+          for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t)
+            pl.tiles[t].row0 = compact(pl.tiles[t].row0);
+          jd.piv_row = compact(jd.piv_row);
+        }
+      }
+    }
   } catch (const std::bad_alloc &) {
     return fail(TSQR_ERR_OOM, "host allocation failed while planning");
   }
@@ -228,12 +251,14 @@ struct DevPlan {
   int device = -1;
   JobDesc *jobs = nullptr;
   TileDesc *tiles = nullptr;
+  int64_t *piv = nullptr;  // pivot row of every chain (launch-0 job), for the mixed path
   ~DevPlan() {
     int cur = 0;
     cudaGetDevice(&cur);
     if (device >= 0) cudaSetDevice(device);
     if (jobs) cudaFree(jobs);
     if (tiles) cudaFree(tiles);
+    if (piv) cudaFree(piv);
     cudaSetDevice(cur);
   }
 };
@@ -243,7 +268,7 @@ static std::list<std::shared_ptr<DevPlan>> g_plans;  // most recent first
 constexpr size_t kPlanCacheSize = 64;
 
 static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int flags,
-                            std::shared_ptr<DevPlan> &out) {
+                            std::shared_ptr<DevPlan> &out, bool mixed = false) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   flags &= TSQR_TWO_LEVEL;
@@ -252,7 +277,7 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
     for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
       const Plan &p = (*it)->plan;
       if ((*it)->device == dev && p.m == m && p.n == n && p.nc == nc && p.leaf_h == leaf_h &&
-          p.arity == arity && p.flags == flags) {
+          p.arity == arity && p.flags == flags && p.mixed == mixed) {
         out = *it;
         g_plans.splice(g_plans.begin(), g_plans, it);
         return TSQR_OK;
@@ -263,13 +288,20 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
   if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
   auto dp = std::make_shared<DevPlan>();
   dp->device = dev;
-  tsqr_status st = make_plan_on(di, dp->plan, m, n, nc, leaf_h, arity, flags);
+  tsqr_status st = make_plan_on(di, dp->plan, m, n, nc, leaf_h, arity, flags, mixed);
   if (st != TSQR_OK) return st;
   const Plan &pl = dp->plan;
   CUDA_TRY(cudaMalloc(&dp->jobs, sizeof(JobDesc) * pl.jobs.size()));
   CUDA_TRY(cudaMalloc(&dp->tiles, sizeof(TileDesc) * pl.tiles.size()));
   CUDA_TRY(cudaMemcpy(dp->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(dp->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(), cudaMemcpyHostToDevice));
+  if (mixed) {
+    const int32_t G = pl.launches[0].job_count;
+    std::vector<int64_t> piv(G);
+    for (int32_t c = 0; c < G; ++c) piv[c] = pl.jobs[c].piv_row;
+    CUDA_TRY(cudaMalloc(&dp->piv, sizeof(int64_t) * G));
+    CUDA_TRY(cudaMemcpy(dp->piv, piv.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice));
+  }
   std::lock_guard<std::mutex> lk(g_plan_mu);
   g_plans.push_front(dp);
   while (g_plans.size() > kPlanCacheSize) g_plans.pop_back();
@@ -388,6 +420,184 @@ static void plan_info(const Plan &pl, int64_t *out) {
   out[5] = (int64_t)pl.tiles.size();
   out[6] = (int64_t)pl.launches.size() + 1;
   out[7] = pl.ctas_per_sm;
+}
+
+// Mixed-precision least squares: FP32 chains (leaves and flat chains), FP64 tree on the
+// compact pivot blocks, then Bjorck augmented-system refinement with FP64 residuals
+// (mixed.cu). Right-hand sides are refined in groups of at most 8 columns.
+static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t lda, const double *B, int64_t ldb,
+                                   int k, double *X, int64_t ldx, int leaf_h, int arity, int flags, int max_refine,
+                                   cudaStream_t s, double *info) {
+  std::shared_ptr<DevPlan> dp;
+  tsqr_status st = get_plan(m, n, n, leaf_h, arity, flags, dp, true);
+  if (st != TSQR_OK) return st;
+  const Plan &pl = dp->plan;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  const int G = pl.launches[0].job_count;
+  const int64_t Gn = (int64_t)G * n;
+  const size_t nrefl = pl.tiles.size() * (size_t)n;
+  const int kk = std::min(k, 8);
+  const int steps = max_refine + 1;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  // one pool block for everything
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += up(bytes);
+    return o;
+  };
+  const size_t o_V32 = take(sizeof(float) * (size_t)m * n);
+  const size_t o_t32 = take(sizeof(float) * nrefl), o_s32 = take(sizeof(float) * nrefl);
+  const size_t o_V64 = take(sizeof(double) * (size_t)Gn * n);
+  const size_t o_t64 = take(sizeof(double) * nrefl), o_s64 = take(sizeof(double) * nrefl);
+  const size_t o_B32 = take(sizeof(float) * (size_t)m * kk);
+  const size_t o_B64 = take(sizeof(double) * (size_t)Gn * kk);
+  const size_t o_r = take(sizeof(double) * (size_t)m * kk);
+  const size_t o_x = take(sizeof(double) * (size_t)n * kk);
+  const size_t o_g = take(sizeof(double) * (size_t)n * kk);
+  const size_t o_h = take(sizeof(double) * (size_t)steps);
+  const size_t o_f = take(sizeof(int32_t) * 2);
+  void *blk = nullptr;
+  CUDA_TRY(pool_alloc(&blk, off, s));
+  char *base = (char *)blk;
+  float *V32 = (float *)(base + o_V32), *tau32 = (float *)(base + o_t32), *scl32 = (float *)(base + o_s32);
+  double *V64 = (double *)(base + o_V64), *tau64 = (double *)(base + o_t64), *scl64 = (double *)(base + o_s64);
+  float *B32 = (float *)(base + o_B32);
+  double *B64 = (double *)(base + o_B64), *r = (double *)(base + o_r), *x = (double *)(base + o_x);
+  double *g = (double *)(base + o_g), *hist = (double *)(base + o_h);
+  int32_t *done = (int32_t *)(base + o_f), *status = done + 1;
+  std::vector<double> hinfo;
+  int32_t hstatus = 0;
+
+  auto body = [&]() -> tsqr_status {
+    // factorization: FP32 chains, pivot blocks to FP64, FP64 tree
+    FactorParamsT<float> f32{};
+    f32.A = A;
+    f32.lda = lda;
+    f32.V = V32;
+    f32.ldv = m;
+    f32.jobs = dp->jobs;
+    f32.tiles = dp->tiles;
+    f32.tau = tau32;
+    f32.scl = scl32;
+    f32.n = n;
+    f32.nc = n;
+    f32.ldt = pl.tile_h;
+    f32.job0 = 0;
+    {
+      ProfScope ps(TSQR_PROF_FACTOR_CHAINS, s);
+      CUDA_TRY(launch_factor(f32, G, s));
+    }
+    {
+      ProfScope ps(TSQR_PROF_SMALL, s);
+      CUDA_TRY(launch_gather_r(V32, m, dp->piv, G, n, V64, Gn, s));
+    }
+    FactorParamsT<double> f64{};
+    f64.V = V64;
+    f64.ldv = Gn;
+    f64.jobs = dp->jobs;
+    f64.tiles = dp->tiles;
+    f64.tau = tau64;
+    f64.scl = scl64;
+    f64.n = n;
+    f64.nc = n;
+    f64.ldt = n;
+    for (size_t q = 1; q < pl.launches.size(); ++q) {
+      f64.job0 = pl.launches[q].job_begin;
+      ProfScope ps(TSQR_PROF_FACTOR_TREE, s);
+      CUDA_TRY(launch_factor(f64, pl.launches[q].job_count, s));
+    }
+    ApplyParamsT<float> a32{};
+    a32.V = V32;
+    a32.ldv = m;
+    a32.B = B32;
+    a32.ldb = m;
+    a32.jobs = dp->jobs;
+    a32.tiles = dp->tiles;
+    a32.tau = tau32;
+    a32.scl = scl32;
+    a32.n = n;
+    a32.ldt = pl.tile_h;
+    a32.job0 = 0;
+    a32.done = done;
+    ApplyParamsT<double> a64{};
+    a64.V = V64;
+    a64.ldv = Gn;
+    a64.B = B64;
+    a64.ldb = Gn;
+    a64.jobs = dp->jobs;
+    a64.tiles = dp->tiles;
+    a64.tau = tau64;
+    a64.scl = scl64;
+    a64.n = n;
+    a64.ldt = n;
+    a64.done = done;
+    const int nl = (int)pl.launches.size();
+    for (int c0 = 0; c0 < k; c0 += 8) {
+      const int kc = std::min(8, k - c0);
+      a32.k = a64.k = kc;
+      CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * kk, s));
+      CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)n * kk, s));
+      CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * (size_t)steps, s));
+      CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(int32_t) * 2, s));
+      for (int step = 0; step < steps; ++step) {
+        {
+          ProfScope ps(TSQR_PROF_SMALL, s);
+          CUDA_TRY(launch_resid(A, lda, m, n, kc, B + (int64_t)c0 * ldb, ldb, r, x, B32, g, step == 0, done,
+                                di.sms, s));
+        }
+        a32.trans = 1;
+        {
+          ProfScope ps(TSQR_PROF_APPLY_QT, s);
+          CUDA_TRY(launch_apply(a32, G, s));
+        }
+        CUDA_TRY(launch_gather_b(B32, m, dp->piv, G, n, kc, B64, Gn, done, s));
+        a64.trans = 1;
+        for (int q = 1; q < nl; ++q) {
+          a64.job0 = pl.launches[q].job_begin;
+          ProfScope ps(TSQR_PROF_APPLY_QT, s);
+          CUDA_TRY(launch_apply(a64, pl.launches[q].job_count, s));
+        }
+        {
+          ProfScope ps(TSQR_PROF_SMALL, s);
+          CUDA_TRY(launch_refine_step(V64, Gn, n, kc, B64, Gn, g, x, hist, step, 1e-14, done, status, s));
+        }
+        if (step + 1 == steps) break;  // the last correction of x needs no new residual
+        a64.trans = 0;
+        for (int q = nl - 1; q >= 1; --q) {
+          a64.job0 = pl.launches[q].job_begin;
+          ProfScope ps(TSQR_PROF_APPLY_Q, s);
+          CUDA_TRY(launch_apply(a64, pl.launches[q].job_count, s));
+        }
+        CUDA_TRY(launch_scatter_b(B32, m, dp->piv, G, n, kc, B64, Gn, done, s));
+        a32.trans = 0;
+        {
+          ProfScope ps(TSQR_PROF_APPLY_Q, s);
+          CUDA_TRY(launch_apply(a32, G, s));
+        }
+      }
+      CUDA_TRY(cudaMemcpy2DAsync(X + (int64_t)c0 * ldx, sizeof(double) * ldx, x, sizeof(double) * n,
+                                 sizeof(double) * n, kc, cudaMemcpyDeviceToDevice, s));
+      if (info && c0 == 0) {
+        hinfo.resize(steps);
+        CUDA_TRY(cudaMemcpyAsync(hinfo.data(), hist, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+      }
+      int32_t st_c = 0;
+      CUDA_TRY(cudaMemcpyAsync(&st_c, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (st_c) hstatus = st_c;
+    }
+    return TSQR_OK;
+  };
+  st = body();
+  cudaFreeAsync(blk, s);
+  if (st != TSQR_OK) return st;
+  if (info)
+    for (int i = 0; i < steps; ++i) info[i] = i < (int)hinfo.size() ? hinfo[i] : 0.0;
+  if (hstatus == 4) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
+  return TSQR_OK;
 }
 
 extern "C" {
@@ -509,9 +719,11 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   if (ldb < m || ldx < n) return fail(TSQR_ERR_ARG, "bad ldb/ldx");
   if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   if (max_refine < 0) return fail(TSQR_ERR_ARG, "max_refine < 0");
-  if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_MIXED is not built yet");
-  if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
+  if (prec != TSQR_FP64 && prec != TSQR_MIXED) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   flags &= ~TSQR_INPLACE;
+  if (prec == TSQR_MIXED)
+    return run_lstsq_mixed(A, m, n, lda, B, ldb, k, X, ldx, leaf_h, arity, flags, max_refine, (cudaStream_t)stream,
+                           info);
   cudaStream_t s = (cudaStream_t)stream;
   tsqr_factors *f = new (std::nothrow) tsqr_factors();
   if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");

@@ -54,38 +54,44 @@ __host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int 
 }
 
 // ----------------------------------------------------------------- factor kernel
-struct FactorParams {
+// R is the element type of the factorization (double; float for the leaves of the
+// mixed-precision path). The input A is always FP64 and is rounded on load.
+template <typename R>
+struct FactorParamsT {
   const double *A;  // first-touch input for GEQRT/TSQRT tiles
   int64_t lda;
-  double *V;        // reflector and R storage, m-by-n
+  R *V;             // reflector and R storage, m-by-n
   int64_t ldv;
-  double *B;        // optional extra columns (Q^T B fused), m-by-(nc-n), in place
+  R *B;             // optional extra columns (Q^T B fused), m-by-(nc-n), in place
   int64_t ldb;
   const JobDesc *jobs;
   const TileDesc *tiles;
-  double *tau;
-  double *scl;
+  R *tau;
+  R *scl;
   int32_t n;
   int32_t nc;   // n + extra columns
   int32_t ldt;  // tile capacity in rows (shared-memory leading dimension)
   int32_t job0; // first job of this launch
 };
+using FactorParams = FactorParamsT<double>;
 
-size_t factor_smem_bytes(int nc, int ldt);
-cudaError_t launch_factor(const FactorParams &p, int njobs, cudaStream_t s);
+size_t factor_smem_bytes(int nc, int ldt, size_t elem = sizeof(double));
+cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s);
+cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s);
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
-                    size_t optin_per_block);
+                    size_t optin_per_block, size_t elem = sizeof(double));
 
 // ------------------------------------------------------------------ apply kernels
-struct ApplyParams {
-  const double *V;
+template <typename R>
+struct ApplyParamsT {
+  const R *V;
   int64_t ldv;
-  double *B;  // m-by-k target
+  R *B;  // m-by-k target
   int64_t ldb;
   const JobDesc *jobs;
   const TileDesc *tiles;
-  const double *tau;
-  const double *scl;
+  const R *tau;
+  const R *scl;
   int32_t n;
   int32_t k;         // columns of B handled by this launch
   int32_t col0;      // first column of B (wide kernel passes)
@@ -93,9 +99,13 @@ struct ApplyParams {
   int32_t job0;
   int32_t trans;     // 1: Q^T (forward order), 0: Q (reverse order)
   int32_t formq;     // 1: forming the thin Q (tiles start at zero, column j >= ref j only)
+  const int32_t *done;  // optional device flag: the launch does nothing when *done != 0
 };
 
-cudaError_t launch_apply(const ApplyParams &p, int njobs, cudaStream_t s);
+using ApplyParams = ApplyParamsT<double>;
+
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s);
+cudaError_t launch_apply(const ApplyParamsT<float> &p, int njobs, cudaStream_t s);
 
 // ------------------------------------------------------------------- small kernels
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,
@@ -103,6 +113,20 @@ cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int
 cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double *d,
                               cudaStream_t s);
 cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s);
+// mixed-precision least squares (mixed.cu)
+cudaError_t launch_gather_r(const float *V32, int64_t ldv32, const int64_t *piv, int G, int n, double *V64,
+                            int64_t ldv64, cudaStream_t s);
+cudaError_t launch_gather_b(const float *B32, int64_t ldb32, const int64_t *piv, int G, int n, int k, double *B64,
+                            int64_t ldb64, const int32_t *done, cudaStream_t s);
+cudaError_t launch_scatter_b(float *B32, int64_t ldb32, const int64_t *piv, int G, int n, int k, const double *B64,
+                             int64_t ldb64, const int32_t *done, cudaStream_t s);
+cudaError_t launch_resid(const double *A, int64_t lda, int64_t m, int n, int k, const double *b, int64_t ldb,
+                         double *r, const double *x, float *B32, double *g, int first, const int32_t *done,
+                         int sms, cudaStream_t s);
+cudaError_t launch_refine_step(const double *R, int64_t ldr, int n, int k, double *B64, int64_t ldb64, double *g,
+                               double *x, double *hist, int step, double tol, int32_t *done, int32_t *status,
+                               cudaStream_t s);
+
 // X = R^{-1} (D C[0:n]) for the raw upper triangle R (leading dimension ldr) and the
 // optional sign vector d (NULL = no scaling); a zero pivot sets *status = 4.
 cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc,
