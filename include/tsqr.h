@@ -196,6 +196,41 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
                                int64_t *tiles, int64_t max_tiles, int64_t *jobs,
                                int64_t max_jobs);
 
+/*
+ * Batched factorization / least squares: many independent problems in ONE persistent
+ * kernel launch. Every CTA takes chain jobs (runs of leaves) of any problem from a device
+ * queue; when a job finishes, the last child to arrive at a tree node performs that
+ * node's combine (the reduce operator of paper §2.3), so tree levels of different
+ * problems overlap and no CTA ever waits.
+ */
+typedef struct tsqr_batch_item {
+  const double *A;  /* device, m-by-n column-major, lda >= m; not modified */
+  int64_t m;
+  int32_t n;        /* 1 <= n <= 128, m >= n */
+  int64_t lda;
+  const double *B;  /* device, m-by-k (ldb >= m) right-hand sides, or NULL with k = 0 */
+  int64_t ldb;
+  int32_t k;        /* 0 <= k, n + k <= 128 */
+  double *R;        /* device, n-by-n (ldr >= n) output with diag(R) >= 0, or NULL */
+  int64_t ldr;
+  double *X;        /* device, n-by-k (ldx >= n) least-squares solution, or NULL */
+  int64_t ldx;
+  int32_t prec;     /* TSQR_FP64, or TSQR_MIXED: FP32 leaf chains + FP64 tree (R only, k = 0) */
+} tsqr_batch_item;
+
+/*
+ * tsqr_batch_solve — factor every item (and solve for its right-hand sides) in one launch.
+ *   items        host array of count items (device pointers inside).
+ *   chain_tiles  tiles per chain (leaves per flat chain inside a CTA); 0 = automatic.
+ *   arity        tree arity 2..16 over each item's chains; 0 = automatic (binary).
+ *   status       host array of count int32 or NULL: 0, or TSQR_ERR_SINGULAR when the
+ *                item's R has an exactly zero diagonal entry (its X is then undefined).
+ *                Filling it synchronizes the stream.
+ *   Errors: TSQR_ERR_ARG (invalid item; nothing is enqueued), TSQR_ERR_OOM, TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                             int32_t arity, void *stream, int32_t *status);
+
 /* launch classes reported by the profiler */
 enum {
   TSQR_PROF_FACTOR_CHAINS = 0, /* leaf / flat-chain launch of the factorization */
@@ -203,7 +238,8 @@ enum {
   TSQR_PROF_APPLY_QT = 2,
   TSQR_PROF_APPLY_Q = 3,
   TSQR_PROF_FORM_Q = 4,
-  TSQR_PROF_SMALL = 5          /* sign fix, scaling, triangular solve */
+  TSQR_PROF_SMALL = 5,         /* sign fix, scaling, triangular solve */
+  TSQR_PROF_BATCH = 6          /* the persistent batched kernel */
 };
 
 /*

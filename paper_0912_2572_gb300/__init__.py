@@ -17,7 +17,7 @@ import ctypes
 from . import _lib
 
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
-           "TSQRError", "profile_collect", "plan_describe"]
+           "TSQRError", "profile_collect", "plan_describe", "batch_solve"]
 
 FP64 = 0
 MIXED = 1
@@ -146,7 +146,55 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
 
 
 PROFILE_KINDS = {0: "factor_chains", 1: "factor_tree", 2: "apply_qt", 3: "apply_q", 4: "form_q",
-                 5: "small"}
+                 5: "small", 6: "batch"}
+
+
+def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status: bool = False):
+    """Factor (and solve) many independent problems in one persistent launch.
+
+    items: list of dicts with "A" (m-by-n column-major float64 CUDA tensor) and optional
+    "B" (m-by-k), "R" and "X" output tensors (allocated here when missing and "want_r" /
+    B are given) and "prec" (FP64 or MIXED; MIXED takes no B). Returns the list of
+    (R, X) per item (None where not requested); with ``status`` also the per-item status
+    codes (this synchronizes the stream).
+    """
+    import torch
+    lib = _lib.load()
+    arr = (_lib.BatchItem * max(1, len(items)))()
+    keep = []
+    outs = []
+    for q, it in enumerate(items):
+        A = it["A"]
+        lda = _check_mat(A, "A")
+        m, n = A.shape
+        B = it.get("B")
+        k = 0
+        ldb = m
+        X = it.get("X")
+        if B is not None:
+            ldb = _check_mat(B, "B", rows=m)
+            k = B.shape[1]
+            if X is None:
+                X = torch.empty((k, n), dtype=torch.float64, device=A.device).t()
+        R = it.get("R")
+        if R is None and it.get("want_r", True):
+            R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+        arr[q].A = A.data_ptr()
+        arr[q].m, arr[q].n, arr[q].lda = m, n, lda
+        arr[q].B = B.data_ptr() if B is not None else None
+        arr[q].ldb, arr[q].k = ldb, k
+        arr[q].R = R.data_ptr() if R is not None else None
+        arr[q].ldr = _check_mat(R, "R", rows=n, cols=n) if R is not None else n
+        arr[q].X = X.data_ptr() if X is not None else None
+        arr[q].ldx = _check_mat(X, "X", rows=n, cols=k) if X is not None else n
+        arr[q].prec = it.get("prec", FP64)
+        keep += [A, B, R, X]
+        outs.append((R, X if k else None))
+    st = (ctypes.c_int32 * max(1, len(items)))() if status else None
+    _lib.check(lib.tsqr_batch_solve(arr, len(items), chain_tiles, arity, _stream(stream), st), "tsqr_batch_solve")
+    if status:
+        return outs, [st[q] for q in range(len(items))]
+    return outs
 
 
 def profile_collect(fn):

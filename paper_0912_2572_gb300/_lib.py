@@ -19,6 +19,14 @@ _i32 = ctypes.c_int32
 _vp = ctypes.c_void_p
 _dp = ctypes.c_void_p  # device pointers travel as plain addresses
 
+class BatchItem(ctypes.Structure):
+    """Mirror of tsqr_batch_item (include/tsqr.h)."""
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int32), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("R", ctypes.c_void_p), ("ldr", ctypes.c_int64), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64),
+                ("prec", ctypes.c_int32)]
+
+
 SIGNATURES = {
     "tsqr_factor": (_i32, [_dp, _i64, _i32, _i64, _i32, _i32, _i32, _i32, _vp,
                            ctypes.POINTER(_vp), _dp, _i64]),
@@ -29,6 +37,7 @@ SIGNATURES = {
                           _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tsqr_solve_r": (_i32, [_vp, _dp, _i64, _i32, _dp, _i64, _dp, _vp]),
     "tsqr_lstsq_static": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _vp]),
+    "tsqr_batch_solve": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _vp, ctypes.POINTER(_i32)]),
     "tsqr_free": (_i32, [_vp]),
     "tsqr_profile_start": (_i32, []),
     "tsqr_profile_stop": (_i32, [_i64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),

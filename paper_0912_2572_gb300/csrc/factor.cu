@@ -188,9 +188,11 @@ __device__ __forceinline__ Refl<R> reflector(R alpha, R s2) {
   return r;
 }
 
+// One job: the tiles of a chain or a tree node, run by the whole CTA (256 threads) in the
+// shared-memory buffer smraw. Reads of V and B go through L2 (ld.global.cg): in the
+// persistent batched kernel they may have been written by another CTA of the same launch.
 template <int CMAX, typename R>
-__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc job, unsigned char *smraw) {
   R *sm = reinterpret_cast<R *>(smraw);
   const int n = p.n, nc = p.nc, ldt = p.ldt;
   const int ncp = (nc + 7) & ~7;
@@ -200,7 +202,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p
   R *PV = PC + ncp;                     // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
-  const JobDesc job = p.jobs[p.job0 + blockIdx.x];
   const int64_t pr = job.piv_row;
 
   // pivot-row element (row pr + j, column c) in global memory
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p
         for (int i = lane; i < ht; i += 32) dst[i] = R(src[i]);
       } else {
         const R *src = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
-        for (int i = lane; i < ht; i += 32) dst[i] = src[i];
+        for (int i = lane; i < ht; i += 32) dst[i] = __ldcg(src + i);
       }
     }
     if (!ge)
@@ -297,6 +298,129 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p
 }
 
 template <int CMAX, typename R>
+__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  run_job<CMAX, R>(p, p.jobs[p.job0 + blockIdx.x], smraw);
+}
+
+
+// ----------------------------------------------------------- batched persistent kernel
+// Finishing an instance: R out with diag >= 0, and X = R^{-1} (Q^T B)[0:n] when the
+// right-hand sides were factored along (back substitution in shared memory).
+__device__ __forceinline__ void finish_instance(const BatchInst &in, int64_t row64, unsigned char *smraw) {
+  const int n = in.n, k = in.k;
+  const double *Rr = in.V64 + row64;  // R(i, j) = Rr[i + j * ldv64]
+  if (in.R) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e % n, j = e / n;
+      const double di = (__ldcg(Rr + i + (int64_t)i * in.ldv64) < 0.0) ? -1.0 : 1.0;
+      in.R[i + (int64_t)j * in.ldr] = (i <= j) ? di * __ldcg(Rr + i + (int64_t)j * in.ldv64) : 0.0;
+    }
+  }
+  if (k > 0 && in.X) {
+    double *xs = reinterpret_cast<double *>(smraw);  // n * k
+    const double *C = in.B + row64;                   // (Q^T B)[0:n] in the pivot rows
+    for (int e = threadIdx.x; e < n * k; e += blockDim.x) {
+      const int i = e % n, c = e / n;
+      xs[e] = __ldcg(C + i + (int64_t)c * in.ldb);
+    }
+    __syncthreads();
+    for (int i = n - 1; i >= 0; --i) {
+      const double rii = __ldcg(Rr + i + (int64_t)i * in.ldv64);
+      for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (rii == 0.0) {
+          if (in.status) atomicExch(in.status, 4);
+          xs[i + c * n] = 0.0;
+        } else {
+          xs[i + c * n] /= rii;
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < i * k; e += blockDim.x) {
+        const int l = e % i, c = e / i;
+        xs[l + c * n] = fma(-__ldcg(Rr + l + (int64_t)i * in.ldv64), xs[i + c * n], xs[l + c * n]);
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * k; e += blockDim.x) {
+      const int i = e % n, c = e / n;
+      in.X[i + (int64_t)c * in.ldx] = xs[e];
+    }
+  }
+  __syncthreads();
+}
+
+template <int CMAX>
+__global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams bp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_job, s_go;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(bp.queue, 1);
+    __syncthreads();
+    int jb = s_job;
+    __syncthreads();
+    if (jb >= bp.nchains) return;
+    for (;;) {
+      const BatchJob bj = bp.jobs[jb];
+      const BatchInst in = bp.inst[bj.inst];
+      const JobDesc jd{bj.piv_row, bj.tile_begin, bj.tile_count};
+      const bool chain = jb < bp.nchains;
+      if (chain && in.mixed) {
+        FactorParamsT<float> fp{};
+        fp.A = in.A;
+        fp.lda = in.lda;
+        fp.V = static_cast<float *>(in.V);
+        fp.ldv = in.ldv;
+        fp.tiles = bp.tiles;
+        fp.tau = static_cast<float *>(in.tau);
+        fp.scl = static_cast<float *>(in.scl);
+        fp.n = in.n;
+        fp.nc = in.n;
+        fp.ldt = in.ldt;
+        run_job<CMAX, float>(fp, jd, smraw);
+        // hand the chain's triangle to the FP64 tree storage
+        const float *Vs = static_cast<const float *>(in.V) + bj.piv_row;
+        for (int e = threadIdx.x; e < in.n * in.n; e += blockDim.x) {
+          const int i = e % in.n, j = e / in.n;
+          if (i <= j) in.V64[bj.row64 + i + (int64_t)j * in.ldv64] = (double)__ldcg(Vs + i + (int64_t)j * in.ldv);
+        }
+        __syncthreads();
+      } else {
+        FactorParamsT<double> fp{};
+        fp.A = in.A;
+        fp.lda = in.lda;
+        fp.V = chain ? static_cast<double *>(in.V) : in.V64;
+        fp.ldv = chain ? in.ldv : in.ldv64;
+        fp.B = in.B;
+        fp.ldb = in.ldb;
+        fp.tiles = bp.tiles;
+        fp.tau = chain ? static_cast<double *>(in.tau) : in.tau64;
+        fp.scl = chain ? static_cast<double *>(in.scl) : in.scl64;
+        fp.n = in.n;
+        fp.nc = in.n + in.k;
+        fp.ldt = chain ? in.ldt : in.n;
+        run_job<CMAX, double>(fp, jd, smraw);
+      }
+      if (bj.parent < 0) {
+        __threadfence();
+        finish_instance(in, bj.row64, smraw);
+        break;
+      }
+      // publish this job's triangle, then arrive at the parent; the last child combines
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_go = (atomicAdd(bp.counters + bj.parent, 1) == bp.jobs[bj.parent].nchild - 1);
+      __syncthreads();
+      const int go = s_go;
+      __syncthreads();
+      if (!go) break;
+      __threadfence();
+      jb = bj.parent;
+    }
+  }
+}
+
+template <int CMAX, typename R>
 cudaError_t launch_factor_t(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
   const size_t bytes = factor_smem_bytes(p.nc, p.ldt, sizeof(R));
   cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -341,6 +465,19 @@ cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_
 
 cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s) {
   return launch_factor_any(p, njobs, s);
+}
+
+cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s) {
+  auto go = [&](auto kernel) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, kThreads, smem_bytes, s>>>(p);
+    return cudaGetLastError();
+  };
+  if (cmax <= 1) return go(k_factor_batch<1>);
+  if (cmax <= 2) return go(k_factor_batch<2>);
+  if (cmax <= 4) return go(k_factor_batch<4>);
+  return go(k_factor_batch<8>);
 }
 
 }  // namespace tsqr

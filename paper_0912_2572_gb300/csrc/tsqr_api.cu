@@ -205,7 +205,7 @@ static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &t
 }
 
 static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
-                                int arity, int flags, bool mixed = false) {
+                                int arity, int flags, bool mixed = false, int64_t chains_override = 0) {
   pl.m = m;
   pl.n = n;
   pl.nc = nc;
@@ -215,7 +215,7 @@ static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n
   pl.mixed = mixed;
   if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double)))
     return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
-  const int64_t chains = (int64_t)di.sms * pl.ctas_per_sm * 4;
+  const int64_t chains = chains_override > 0 ? chains_override : (int64_t)di.sms * pl.ctas_per_sm * 4;
   try {
     plan_build(pl, chains);
     if (mixed) {
@@ -600,6 +600,211 @@ static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t ld
   return TSQR_OK;
 }
 
+// ---------------------------------------------------------------- batched solve
+static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                               cudaStream_t s, int32_t *status) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  if (arity == 0) arity = 2;
+  const int L = chain_tiles > 0 ? chain_tiles : 8;
+  std::vector<Plan> plans(count);
+  size_t smem = 0;
+  int cmax = 1, cps_min = 2;
+  for (int32_t q = 0; q < count; ++q) {
+    const tsqr_batch_item &it = items[q];
+    const bool mixed = it.prec == TSQR_MIXED;
+    const int nc = it.n + it.k;
+    const size_t elem = mixed ? sizeof(float) : sizeof(double);
+    int th = 0, cps = 0;
+    if (!choose_tiles(di, it.n, nc, 1 << 20, th, cps, elem))
+      return fail(TSQR_ERR_UNSUPPORTED, "item %d: no tile fits shared memory", q);
+    const int64_t tiles = (it.m + th - 1) / th;
+    const int64_t G = std::max<int64_t>(1, (tiles + L / 2) / L);
+    tsqr_status st = make_plan_on(di, plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
+    if (st != TSQR_OK) return st;
+    smem = std::max(smem, factor_smem_bytes(nc, plans[q].tile_h, elem));
+    smem = std::max(smem, factor_smem_bytes(nc, it.n, sizeof(double)));  // tree nodes
+    smem = std::max(smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
+    while (16 * cmax < nc) cmax *= 2;
+    cps_min = std::min(cps_min, plans[q].ctas_per_sm);
+  }
+  // device-side job arrays: chains of every item (largest first), then tree nodes
+  struct Chain {
+    double cost;
+    int32_t item, job;
+  };
+  std::vector<Chain> chains;
+  std::vector<int64_t> tile_base(count), job_base(count);
+  int64_t ntiles = 0;
+  for (int32_t q = 0; q < count; ++q) {
+    const Plan &pl = plans[q];
+    tile_base[q] = ntiles;
+    ntiles += (int64_t)pl.tiles.size();
+    for (int32_t c = 0; c < pl.launches[0].job_count; ++c) {
+      const JobDesc &jd = pl.jobs[c];
+      double rows = 0;
+      for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t) rows += pl.tiles[t].nrows;
+      const double w = (double)(pl.nc) * pl.nc * (pl.mixed ? 0.1 : 1.0);
+      chains.push_back({rows * w, q, c});
+    }
+  }
+  std::sort(chains.begin(), chains.end(), [](const Chain &a, const Chain &b) { return a.cost > b.cost; });
+  const int32_t nchains = (int32_t)chains.size();
+  std::vector<std::vector<int32_t>> gidx(count);  // global job index of each plan job
+  for (int32_t q = 0; q < count; ++q) gidx[q].assign(plans[q].jobs.size(), -1);
+  for (int32_t c = 0; c < nchains; ++c) gidx[chains[c].item][chains[c].job] = c;
+  int32_t next = nchains;
+  for (int32_t q = 0; q < count; ++q)
+    for (size_t j = plans[q].launches[0].job_count; j < plans[q].jobs.size(); ++j) gidx[q][j] = next++;
+  const int32_t njobs = next;
+  std::vector<BatchJob> jobs(njobs);
+  std::vector<TileDesc> tiles((size_t)ntiles);
+  for (int32_t q = 0; q < count; ++q) {
+    const Plan &pl = plans[q];
+    for (size_t t = 0; t < pl.tiles.size(); ++t) tiles[tile_base[q] + t] = pl.tiles[t];
+    const int32_t G = pl.launches[0].job_count;
+    // parents: follow which job currently holds each pivot block, level by level
+    std::vector<int32_t> holder(G);  // by chain index
+    std::vector<std::pair<int64_t, int32_t>> rowkey;  // (tree-storage row, chain index)
+    for (int32_t c = 0; c < G; ++c) {
+      holder[c] = c;
+      rowkey.push_back({pl.mixed ? (int64_t)c * pl.n : pl.jobs[c].piv_row, c});
+    }
+    std::sort(rowkey.begin(), rowkey.end());
+    auto chain_of = [&](int64_t row) {
+      auto it2 = std::lower_bound(rowkey.begin(), rowkey.end(), std::make_pair(row, (int32_t)-1));
+      return it2->second;
+    };
+    for (int32_t c = 0; c < G; ++c) {
+      BatchJob &bj = jobs[gidx[q][c]];
+      const JobDesc &jd = pl.jobs[c];
+      bj.piv_row = jd.piv_row;
+      bj.row64 = pl.mixed ? (int64_t)c * pl.n : jd.piv_row;
+      bj.tile_begin = (int32_t)(tile_base[q] + jd.tile_begin);
+      bj.tile_count = jd.tile_count;
+      bj.inst = q;
+      bj.parent = -1;
+      bj.nchild = 0;
+    }
+    for (size_t j = G; j < pl.jobs.size(); ++j) {
+      const JobDesc &jd = pl.jobs[j];
+      BatchJob &bj = jobs[gidx[q][j]];
+      bj.piv_row = jd.piv_row;
+      bj.row64 = jd.piv_row;
+      bj.tile_begin = (int32_t)(tile_base[q] + jd.tile_begin);
+      bj.tile_count = jd.tile_count;
+      bj.inst = q;
+      bj.parent = -1;
+      bj.nchild = jd.tile_count + 1;
+      const int32_t first = chain_of(jd.piv_row);
+      jobs[gidx[q][holder[first]]].parent = gidx[q][j];
+      for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t)
+        jobs[gidx[q][holder[chain_of(pl.tiles[t].row0)]]].parent = gidx[q][j];
+      holder[first] = (int32_t)j;
+    }
+  }
+  // one pool block: per-item workspaces, then the device copies of the arrays
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += up(b);
+    return o;
+  };
+  struct Off {
+    size_t V, B, tau, scl, V64, tau64, scl64;
+  };
+  std::vector<Off> offs(count);
+  for (int32_t q = 0; q < count; ++q) {
+    const tsqr_batch_item &it = items[q];
+    const Plan &pl = plans[q];
+    const size_t elem = pl.mixed ? sizeof(float) : sizeof(double);
+    const size_t nrefl = pl.tiles.size() * (size_t)it.n;
+    offs[q].V = take(elem * (size_t)it.m * it.n);
+    offs[q].B = it.k > 0 ? take(sizeof(double) * (size_t)it.m * it.k) : 0;
+    offs[q].tau = take(elem * nrefl);
+    offs[q].scl = take(elem * nrefl);
+    if (pl.mixed) {
+      const int64_t Gn = (int64_t)pl.launches[0].job_count * it.n;
+      offs[q].V64 = take(sizeof(double) * (size_t)Gn * it.n);
+      offs[q].tau64 = take(sizeof(double) * nrefl);
+      offs[q].scl64 = take(sizeof(double) * nrefl);
+    }
+  }
+  const size_t o_inst = take(sizeof(BatchInst) * count);
+  const size_t o_jobs = take(sizeof(BatchJob) * njobs);
+  const size_t o_tiles = take(sizeof(TileDesc) * (size_t)ntiles);
+  const size_t o_cnt = take(sizeof(int32_t) * ((size_t)njobs + 1));
+  const size_t o_st = take(sizeof(int32_t) * count);
+  void *blk = nullptr;
+  CUDA_TRY(pool_alloc(&blk, off, s));
+  char *base = (char *)blk;
+  std::vector<BatchInst> inst(count);
+  for (int32_t q = 0; q < count; ++q) {
+    const tsqr_batch_item &it = items[q];
+    const Plan &pl = plans[q];
+    BatchInst &bi = inst[q];
+    bi.A = it.A;
+    bi.lda = it.lda;
+    bi.V = base + offs[q].V;
+    bi.ldv = it.m;
+    bi.B = it.k > 0 ? (double *)(base + offs[q].B) : nullptr;
+    bi.ldb = it.m;
+    bi.tau = base + offs[q].tau;
+    bi.scl = base + offs[q].scl;
+    if (pl.mixed) {
+      bi.V64 = (double *)(base + offs[q].V64);
+      bi.ldv64 = (int64_t)pl.launches[0].job_count * it.n;
+      bi.tau64 = (double *)(base + offs[q].tau64);
+      bi.scl64 = (double *)(base + offs[q].scl64);
+    } else {
+      bi.V64 = (double *)bi.V;
+      bi.ldv64 = it.m;
+      bi.tau64 = (double *)bi.tau;
+      bi.scl64 = (double *)bi.scl;
+    }
+    bi.R = it.R;
+    bi.ldr = it.ldr;
+    bi.X = it.X;
+    bi.ldx = it.ldx;
+    bi.status = (int32_t *)(base + o_st) + q;
+    bi.n = it.n;
+    bi.k = it.k;
+    bi.ldt = pl.tile_h;
+    bi.mixed = pl.mixed ? 1 : 0;
+    if (it.k > 0)
+      CUDA_TRY(cudaMemcpy2DAsync(bi.B, sizeof(double) * it.m, it.B, sizeof(double) * it.ldb, sizeof(double) * it.m,
+                                 it.k, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(BatchJob) * njobs, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(base + o_tiles, tiles.data(), sizeof(TileDesc) * (size_t)ntiles, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(base + o_cnt, 0, sizeof(int32_t) * ((size_t)njobs + 1), s));
+  CUDA_TRY(cudaMemsetAsync(base + o_st, 0, sizeof(int32_t) * count, s));
+  BatchParams bp{};
+  bp.inst = (const BatchInst *)(base + o_inst);
+  bp.jobs = (const BatchJob *)(base + o_jobs);
+  bp.tiles = (const TileDesc *)(base + o_tiles);
+  bp.counters = (int32_t *)(base + o_cnt);
+  bp.queue = bp.counters + njobs;
+  bp.nchains = nchains;
+  const int grid = di.sms * cps_min;
+  {
+    ProfScope ps(TSQR_PROF_BATCH, s);
+    CUDA_TRY(launch_factor_batch(bp, cmax, grid, smem, s));
+  }
+  tsqr_status st = TSQR_OK;
+  if (status) {
+    cudaError_t e = cudaMemcpyAsync(status, base + o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
+  }
+  cudaFreeAsync(blk, s);
+  return st;
+}
+
 extern "C" {
 
 const char *tsqr_strerror(tsqr_status s) {
@@ -772,6 +977,30 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   factors_release(f);
   if (st == TSQR_OK && hstatus == 4) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
   return st;
+}
+
+tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                             void *stream, int32_t *status) {
+  g_last_error.clear();
+  if (count < 0 || (count > 0 && !items)) return fail(TSQR_ERR_ARG, "bad items/count");
+  if (chain_tiles < 0 || !(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "bad chain_tiles/arity");
+  for (int32_t q = 0; q < count; ++q) {
+    const tsqr_batch_item &it = items[q];
+    tsqr_status st = check_factor_args(it.A, it.m, it.n, it.lda, it.n, 2);
+    if (st != TSQR_OK) return fail(st, "item %d: %s", q, g_last_error.c_str());
+    if (it.k < 0 || it.n + it.k > 128) return fail(TSQR_ERR_ARG, "item %d: k=%d with n=%d", q, it.k, it.n);
+    if (it.k > 0 && (!it.B || it.ldb < it.m || (it.X && it.ldx < it.n)))
+      return fail(TSQR_ERR_ARG, "item %d: bad B/X", q);
+    if (it.R && it.ldr < it.n) return fail(TSQR_ERR_ARG, "item %d: ldr < n", q);
+    if (it.prec != TSQR_FP64 && it.prec != TSQR_MIXED) return fail(TSQR_ERR_ARG, "item %d: unknown prec", q);
+    if (it.prec == TSQR_MIXED && it.k > 0) return fail(TSQR_ERR_ARG, "item %d: MIXED items take k = 0", q);
+  }
+  if (count == 0) return TSQR_OK;
+  try {
+    return batch_solve(items, count, chain_tiles, arity, (cudaStream_t)stream, status);
+  } catch (const std::bad_alloc &) {
+    return fail(TSQR_ERR_OOM, "host allocation failed");
+  }
 }
 
 tsqr_status tsqr_free(tsqr_factors *F) {

@@ -81,6 +81,50 @@ cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
                     size_t optin_per_block, size_t elem = sizeof(double));
 
+// ---------------------------------------------------------- batched persistent kernel
+// One launch factors every instance of a batch: CTAs take chain jobs from an atomic queue;
+// when a job finishes, its CTA arrives at the parent tree node (an atomic counter) and
+// the last child to arrive runs the node's combine, then climbs on. No CTA ever waits.
+// The CTA that completes an instance's root writes R (diag >= 0) and, with right-hand
+// sides fused into the factorization, solves R X = (Q^T B)[0:n].
+struct BatchInst {
+  const double *A;  // input, m-by-n, leading dimension lda
+  int64_t lda;
+  void *V;          // chain storage: double (FP64) or float (mixed), m-by-n, ld = ldv
+  int64_t ldv;
+  double *B;        // fused right-hand sides (library copy, m-by-k) or null
+  int64_t ldb;
+  void *tau, *scl;  // chain reflector scalars (same element type as V)
+  double *V64;      // tree storage: V itself (FP64) or the compact pivot blocks (mixed)
+  int64_t ldv64;
+  double *tau64, *scl64;
+  double *R;        // optional output, n-by-n
+  int64_t ldr;
+  double *X;        // optional output, n-by-k
+  int64_t ldx;
+  int32_t *status;  // device flag set to 4 when R is singular (solve only)
+  int32_t n, k, ldt, mixed;
+};
+
+struct BatchJob {   // chain jobs first (queue order), then tree nodes
+  int64_t piv_row;  // pivot rows in the job's storage (V for chains, V64 for nodes)
+  int64_t row64;    // where the job's triangle lives in the tree storage
+  int32_t tile_begin, tile_count;
+  int32_t inst, parent;  // parent node (job index) or -1 at the root
+  int32_t nchild, pad;   // arrivals a node waits for (its children)
+};
+
+struct BatchParams {
+  const BatchInst *inst;
+  const BatchJob *jobs;
+  const TileDesc *tiles;
+  int32_t *counters;  // one per job, zero at launch
+  int32_t *queue;     // next chain job, zero at launch
+  int32_t nchains;
+};
+
+cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s);
+
 // ------------------------------------------------------------------ apply kernels
 template <typename R>
 struct ApplyParamsT {

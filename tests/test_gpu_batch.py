@@ -1,0 +1,83 @@
+"""The persistent batched engine: many uneven problems in one launch (chain jobs from a
+device queue; the last child to arrive at a tree node runs its combine, paper §2.3).
+Each item must match the oracle, and be bitwise identical alone and inside a batch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_2572_gb300 import inputs
+from conftest import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def make_items(count, seed, mlo=256, mhi=20000, ns=(8, 16, 32, 64), mixed_share=0.5, k=0):
+    g = inputs.rng(seed)
+    out = []
+    for q in range(count):
+        m = int(np.exp(g.uniform(np.log(mlo), np.log(mhi))))
+        n = int(g.choice(ns))
+        m = max(m, n)
+        A = inputs.gaussian(m, n, seed * 1000 + q)
+        prec = 1 if (k == 0 and g.uniform() < mixed_share) else 0
+        B = inputs.gaussian(m, k, seed * 1000 + q + 500) if k else None
+        out.append((A, B, prec))
+    return out
+
+
+def run(items, **kw):
+    import paper_0912_2572_gb300 as ts
+    dev = [{"A": to_dev(A), "prec": p, **({"B": to_dev(B)} if B is not None else {})} for A, B, p in items]
+    outs, st = ts.batch_solve(dev, status=True, **kw)
+    return [(to_host(R), to_host(X) if X is not None else None) for R, X in outs], st
+
+
+def test_batch_factor_matches_oracle(cuda_lib):
+    items = make_items(60, 1)
+    res, st = run(items)
+    assert st == [0] * len(items)
+    for (A, _, prec), (R, _) in zip(items, res):
+        Ro = oracle.r_factor(A)
+        assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+        # FP64 items to 1e-12; FP32-mixed items carry single-precision leaf rounding
+        assert rel(R, Ro) <= (1e-12 if prec == 0 else 1e-5)
+
+
+def test_batch_alone_equals_in_mix(cuda_lib):
+    items = make_items(40, 2)
+    res_mix, _ = run(items)
+    for q in (0, 7, 23, 39):
+        res_alone, _ = run([items[q]])
+        assert np.array_equal(res_alone[0][0], res_mix[q][0])
+
+
+def test_batch_least_squares(cuda_lib):
+    items = make_items(30, 3, k=3, ns=(16, 32, 64, 100))
+    res, st = run(items)
+    assert st == [0] * len(items)
+    for (A, B, _), (R, X) in zip(items, res):
+        assert rel(X, oracle.lstsq(A, B)) <= 1e-12
+        assert rel(R, oracle.r_factor(A)) <= 1e-12
+
+
+def test_batch_tree_shapes_and_chain_lengths(cuda_lib):
+    items = make_items(12, 4, mlo=5000, mhi=60000)
+    ref, _ = run(items, chain_tiles=8, arity=2)
+    for ct, ar in ((1, 2), (3, 4), (64, 16)):
+        res, _ = run(items, chain_tiles=ct, arity=ar)
+        for (A, _, prec), (R, _), (R0, _) in zip(items, res, ref):
+            assert rel(R, R0) <= (1e-12 if prec == 0 else 1e-5)
+
+
+def test_batch_singular_item(cuda_lib):
+    A = inputs.gaussian(3000, 8, 9)
+    A[:, 5] = 0.0
+    B = inputs.gaussian(3000, 1, 10)
+    good = make_items(3, 5, k=1)
+    res, st = run([good[0], (A, B, 0), good[1]])
+    assert st == [0, 4, 0]
+    assert rel(res[0][1], oracle.lstsq(good[0][0], good[0][1])) <= 1e-12
