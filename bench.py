@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--sweep", default="", help="write a leaf-height x tree sweep (factor only) to this file")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
+    p.add_argument("--batch-count", type=int, default=10000)
     return p.parse_args()
 
 
@@ -178,6 +181,119 @@ def cpu_baseline(m, n, decades, budget_s=12.0):
             "sample": f"{ms_} x {n} rows of the same generator (factor + thin Q + Q^T b + solve), "
                       f"{t:.2f} s"}
 
+
+
+# ------------------------------------------------------------ extra workloads
+def bench_mixed_lsq(ts):
+    """Mixed-precision least squares: A 16,777,216 x 32, sigma 1..1e-4, k = 4 right-hand
+    sides b = A x_true + 1e-6 N(0,1); FP32 leaves, FP64 tree, FP64 refinement. Reports the
+    time of the mixed and of the FP64 solve and the error against the FP64 oracle after
+    each refinement step (solving again with max_refine = 0, 1, 2, ...)."""
+    import torch
+    import oracle
+    from paper_0912_2572_gb300 import inputs
+    m, n, k = 16_777_216, 32, 4
+    A = inputs.graded(m, n, 4.0, seed_g=0, seed_v=1)
+    B, _ = inputs.lstsq_rhs(A, k, 1e-6, 2)
+    Ad, Bd = dev_colmajor(A), dev_colmajor(B)
+    leaf32 = ts.plan_describe(m, n, 1 << 20, 2, True)["tile_rows"]
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    t_mix, (X, hist) = timed(lambda: ts.lstsq(Ad, Bd, leaf_h=512, arity=2, two_level=True, prec=ts.MIXED,
+                                               max_refine=10, info=True))
+    t_64, X64 = timed(lambda: ts.lstsq(Ad, Bd, leaf_h=leaf32, arity=2, two_level=True, prec=ts.FP64))
+    Xo = oracle.lstsq(A, B)
+    nrm = np.linalg.norm(Xo)
+    steps = [h for h in hist if h > 0]
+    per_step = []
+    for s in range(len(steps)):
+        Xs = ts.lstsq(Ad, Bd, leaf_h=512, arity=2, two_level=True, prec=ts.MIXED, max_refine=s)
+        per_step.append(float(np.linalg.norm(Xs.cpu().numpy() - Xo) / nrm))
+    fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + 4.0 * m * n * k
+    return {"workload": f"lstsq {m}x{n}, k={k}, sigma 1..1e-4 (kappa 1e4), b = A x + 1e-6 N(0,1)",
+            "mixed_ms": t_mix, "fp64_ms": t_64, "speedup_vs_fp64": t_64 / t_mix,
+            "mixed_err_vs_oracle": float(np.linalg.norm(X.cpu().numpy() - Xo) / nrm),
+            "fp64_err_vs_oracle": float(np.linalg.norm(X64.cpu().numpy() - Xo) / nrm),
+            "err_vs_oracle_per_step": per_step, "dx_over_x_per_step": steps,
+            "fp64_gflops": fl / (t_64 * 1e-3) / 1e9}
+
+
+def bench_batched(ts, count):
+    """Batched uneven TSQR: `count` instances, m log-uniform in [256, 65536], n uniform in
+    {8, 16, 32, 64}, iid N(0,1) entries (device generator, seeded), alternately FP64 and
+    FP32-mixed; R of every instance. One persistent launch for the whole batch, with the
+    chain length and tree arity picked by timing candidates on a 1000-instance sample;
+    compared with one launch per instance (the same kernel, batches of one) and with the
+    plain multi-launch tsqr_factor, both timed on a sample and reported per instance."""
+    import torch
+    from paper_0912_2572_gb300 import inputs
+    g = inputs.rng(7)
+    ms = np.exp(g.uniform(np.log(256), np.log(65536), size=count)).astype(np.int64)
+    ns = g.choice([8, 16, 32, 64], size=count)
+    ms = np.maximum(ms, ns)
+    total = int(np.sum(ms * ns))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    buf = torch.randn(total, dtype=torch.float64, device="cuda", generator=gen)
+    items = []
+    off = 0
+    for q in range(count):
+        m, n = int(ms[q]), int(ns[q])
+        A = buf[off:off + m * n].view(n, m).t()
+        off += m * n
+        items.append({"A": A, "prec": q & 1})
+    flops = float(np.sum(2.0 * ms * ns * ns - 2.0 * ns ** 3 / 3.0))
+
+    def run(its, L, ar, reps=1):
+        ts.batch_solve(its, chain_tiles=L, arity=ar)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ts.batch_solve(its, chain_tiles=L, arity=ar)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    sample = items[:min(1000, count)]
+    cands = [(L, ar) for L in (2, 4, 8, 16, 32) for ar in (2, 4)]
+    tune = {f"L{L}_a{ar}": run(sample, L, ar) for L, ar in cands}
+    L_best, ar_best = min(cands, key=lambda c: tune[f"L{c[0]}_a{c[1]}"])
+    t_batch = run(items, L_best, ar_best, reps=2)
+    # one launch per instance and the plain API, on the first 500 instances
+    few = items[:min(500, count)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in few:
+        ts.batch_solve([it], chain_tiles=L_best, arity=ar_best)
+    torch.cuda.synchronize()
+    t_one = (time.perf_counter() - t0) / len(few)
+    t0 = time.perf_counter()
+    for it in few:
+        A = it["A"]
+        h = max(A.shape[1], 256)
+        ts.factor(A, leaf_h=h, arity=2, two_level=True).free()
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / len(few)
+    return {"workload": f"{count} instances, m log-uniform [256, 65536], n in {{8,16,32,64}}, half FP64 / half "
+                        "FP32-mixed, R of each",
+            "autotune_ms_on_1000": tune, "chain_tiles": L_best, "arity": ar_best,
+            "batched_ms": t_batch, "batched_instances_per_s": count / (t_batch * 1e-3),
+            "batched_gflops": flops / (t_batch * 1e-3) / 1e9,
+            "one_launch_per_instance_instances_per_s": 1.0 / t_one,
+            "plain_tsqr_factor_instances_per_s": 1.0 / t_plain,
+            "speedup_vs_one_launch_per_instance": t_one * count / (t_batch * 1e-3),
+            "speedup_vs_plain": t_plain * count / (t_batch * 1e-3)}
 
 # ------------------------------------------------------------------ reference
 def bench_reference(args):
@@ -363,6 +479,10 @@ def bench_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(m, n, args.decades)
+    del Q
+    mixed = None if args.no_mixed or rank != 0 else bench_mixed_lsq(ts)
+    torch.cuda.empty_cache()
+    batched = None if args.no_batch or rank != 0 else bench_batched(ts, args.batch_count)
 
     if rank == 0:
         line = {
@@ -385,6 +505,7 @@ def bench_ours(args):
                          "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; no FP64 entry "
                                       "in the measured peaks)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
+            "mixed_lsq": mixed, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -118,7 +118,9 @@ tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *str
  *   prec       TSQR_FP64: FP64 TSQR of [A | B] (Q^T B fused into the factorization),
  *              then back substitution.
  *              TSQR_MIXED: FP32 leaf factorizations, FP64 tree, and FP64 augmented-
- *              system iterative refinement (at most max_refine corrections).
+ *              system iterative refinement (Bjorck) starting from x = r = 0, so at most
+ *              max_refine + 1 correction steps; it stops once ||dX||_F/||X||_F <= 1e-13.
+ *              k <= 64; the right-hand sides are refined in groups of 8.
  *   info       host array of length max_refine + 1 or NULL: info[s] = ||dX||_F/||X||_F
  *              after correction s (TSQR_MIXED), info[0] = 0 for TSQR_FP64. Filling it
  *              synchronizes the stream.

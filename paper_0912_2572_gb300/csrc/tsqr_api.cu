@@ -422,6 +422,10 @@ static void plan_info(const Plan &pl, int64_t *out) {
   out[7] = pl.ctas_per_sm;
 }
 
+// Refinement stops once ||dx||/||x|| <= kRefineTol: x is then at the FP64 floor of the
+// problem (about kappa * u), so further corrections change nothing measurable.
+constexpr double kRefineTol = 1e-13;
+
 // Mixed-precision least squares: FP32 chains (leaves and flat chains), FP64 tree on the
 // compact pivot blocks, then Bjorck augmented-system refinement with FP64 residuals
 // (mixed.cu). Right-hand sides are refined in groups of at most 8 columns.
@@ -562,7 +566,7 @@ static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t ld
         }
         {
           ProfScope ps(TSQR_PROF_SMALL, s);
-          CUDA_TRY(launch_refine_step(V64, Gn, n, kc, B64, Gn, g, x, hist, step, 1e-14, done, status, s));
+          CUDA_TRY(launch_refine_step(V64, Gn, n, kc, B64, Gn, g, x, hist, step, kRefineTol, done, status, s));
         }
         if (step + 1 == steps) break;  // the last correction of x needs no new residual
         a64.trans = 0;
