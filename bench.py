@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
     p.add_argument("--batch-count", type=int, default=10000)
+    p.add_argument("--no-serve", action="store_true", help="skip the served least-squares workload")
+    p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
     return p.parse_args()
 
 
@@ -295,6 +297,154 @@ def bench_batched(ts, count):
             "speedup_vs_one_launch_per_instance": t_one * count / (t_batch * 1e-3),
             "speedup_vs_plain": t_plain * count / (t_batch * 1e-3)}
 
+def ts_plan_rows(m, n, nc):
+    import paper_0912_2572_gb300 as ts
+    return ts.plan_describe(m, n, 1 << 20, 2, True, nc=nc)["tile_rows"]
+
+
+def make_served_pool(count, seed=11):
+    """Least-squares requests shaped like the served workload: m log-uniform in [1e3, 1e6],
+    n uniform over {16, 32, 64, 128}, k uniform in 1..8, A = G diag(sigma) V^T with G iid
+    N(0,1) (device generator), sigma log-spaced from 1 to 1/kappa with kappa log-uniform in
+    [1, 1e4], V Haar-orthogonal, and b = A x_true + 1e-6 N(0,1). Built on the device."""
+    import torch
+    from paper_0912_2572_gb300 import inputs
+    g = inputs.rng(seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    pool = []
+    for q in range(count):
+        m = int(np.exp(g.uniform(np.log(1e3), np.log(1e6))))
+        n = int(g.choice([16, 32, 64, 128]))
+        k = int(g.integers(1, 9))
+        dec = float(g.uniform(0.0, 4.0))
+        sig = torch.tensor(inputs.log_spectrum(n, dec), device="cuda")
+        V = torch.tensor(inputs.haar_orthogonal(n, seed * 100003 + q), device="cuda")
+        G = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=gen).t()
+        A = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+        A.copy_(G * sig @ V.t())
+        del G
+        xt = torch.randn((n, k), dtype=torch.float64, device="cuda", generator=gen)
+        B = torch.empty((k, m), dtype=torch.float64, device="cuda").t()
+        B.copy_(A @ xt + 1e-6 * torch.randn((m, k), dtype=torch.float64, device="cuda", generator=gen))
+        nc = n + k if n + k <= 128 else n  # the plain path fuses Q^T B when it fits
+        leaf_h = ts_plan_rows(m, n, nc)
+        pool.append({"A": A, "B": B, "m": m, "n": n, "k": k, "kappa": 10.0 ** dec, "leaf_h": leaf_h})
+    return pool
+
+
+def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plain_sample=96, streams=2,
+                 max_batch=128, seed=11):
+    """Served least squares: a continuous-batching server fed (a) open-loop by a Poisson
+    stream at `rate` requests/s and (b) closed-loop with `closed` requests at once
+    (saturation throughput); compared with the plain path, one tsqr_lstsq FP64 call per
+    request in sequence, synchronised after each. Requests cycle through a pool of
+    `pool_size` distinct device-resident problems; latencies are from submission to the
+    server's observation of completion. Each X is checked against the plain path."""
+    import torch
+    pool = make_served_pool(pool_size, seed)
+    torch.cuda.synchronize()
+    g = np.random.Generator(np.random.PCG64(seed + 1))
+
+    def lsq_flops(r):
+        m, n, k = r["m"], r["n"], r["k"]
+        return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + 4.0 * m * n * k
+
+    # plain path: one request at a time through tsqr_lstsq (FP64, fused Q^T B when n + k <= 128)
+    for r in pool[:4]:
+        ts.lstsq(r["A"], r["B"], leaf_h=r["leaf_h"], arity=2, two_level=True, prec=ts.FP64)
+    torch.cuda.synchronize()
+    order = [int(i) for i in g.integers(0, pool_size, size=plain_sample)]
+    t0 = time.perf_counter()
+    Xplain = {}
+    for i in order:
+        Xplain[i] = ts.lstsq(pool[i]["A"], pool[i]["B"], leaf_h=pool[i]["leaf_h"], arity=2, two_level=True,
+                             prec=ts.FP64)
+        torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / plain_sample
+    plain_fl = float(np.mean([lsq_flops(pool[i]) for i in order]))
+
+    def submit_all(srv, idx, prec, times=None):
+        outs = {}
+        start = time.perf_counter()
+        for j, i in enumerate(idx):
+            if times is not None:
+                while time.perf_counter() - start < times[j]:
+                    pass
+            t, (_, X) = srv.submit({"A": pool[i]["A"], "B": pool[i]["B"], "want_r": False, "prec": prec})
+            outs[t] = (i, X)
+        return outs
+
+    def collect(srv, n_expected, limit_s=300.0):
+        done = []
+        t_end = time.perf_counter() + limit_s
+        while len(done) < n_expected:
+            done += srv.poll()
+            if time.perf_counter() > t_end:
+                raise RuntimeError(f"served requests incomplete after {limit_s} s: {len(done)}/{n_expected}")
+            time.sleep(0.0002)
+        return done
+
+    def closed_loop(prec):
+        with ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8) as srv:
+            warm = [int(i) for i in g.integers(0, pool_size, size=64)]
+            submit_all(srv, warm, prec)
+            collect(srv, len(warm))
+            b0 = srv.stats()["batches"]
+            idx = [int(i) for i in g.integers(0, pool_size, size=closed)]
+            t0 = time.perf_counter()
+            outs = submit_all(srv, idx, prec)
+            done = collect(srv, closed)
+            t = time.perf_counter() - t0
+            st = srv.stats()
+        lat = np.array([d[1] for d in done])
+        errs = [float(torch.linalg.norm(X - Xplain[i]) / torch.linalg.norm(Xplain[i]))
+                for i, X in outs.values() if i in Xplain]
+        return {"requests": closed, "solves_per_s": closed / t,
+                "gflops_fp64_equiv": sum(lsq_flops(pool[i]) for i in idx) / t / 1e9,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "batches": st["batches"] - b0, "largest_batch": st["max_batch"],
+                "failed": sum(1 for d in done if d[2] != 0),
+                "max_rel_diff_vs_plain_fp64": max(errs) if errs else None}
+
+    res = {"closed_loop": {}}
+    for name, prec in (("fp64", ts.FP64), ("auto", ts.AUTO), ("mixed", ts.MIXED)):
+        res["closed_loop"][name] = closed_loop(prec)
+    best = max(res["closed_loop"], key=lambda n: res["closed_loop"][n]["solves_per_s"])
+    prec = {"fp64": ts.FP64, "auto": ts.AUTO, "mixed": ts.MIXED}[best]
+    # open loop: Poisson arrivals at `rate`
+    with ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8) as srv:
+        warm = [int(i) for i in g.integers(0, pool_size, size=64)]
+        submit_all(srv, warm, prec)
+        collect(srv, len(warm))
+        b0 = srv.stats()["batches"]
+        gaps = g.exponential(1.0 / rate, size=arrivals)
+        times = np.cumsum(gaps) - gaps[0]
+        idx = [int(i) for i in g.integers(0, pool_size, size=arrivals)]
+        t0 = time.perf_counter()
+        submit_all(srv, idx, prec, times)
+        t_sub = time.perf_counter() - t0
+        done = collect(srv, arrivals)
+        t_open = time.perf_counter() - t0
+        lat = np.array([d[1] for d in done])
+        res["open_loop"] = {"prec": best, "offered_per_s": rate, "arrivals": arrivals, "submit_span_s": t_sub,
+                            "completed_per_s": arrivals / t_open,
+                            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                            "batches": srv.stats()["batches"] - b0,
+                            "failed": sum(1 for d in done if d[2] != 0)}
+    res["plain_fp64"] = {"solves_per_s": 1.0 / t_plain, "ms_per_solve": t_plain * 1e3,
+                         "gflops": plain_fl / t_plain / 1e9, "sample": plain_sample}
+    res["speedup_closed_vs_plain"] = {k: v["solves_per_s"] / res["plain_fp64"]["solves_per_s"]
+                                      for k, v in res["closed_loop"].items()}
+    res["workload"] = (f"lstsq requests: m log-uniform [1e3, 1e6], n in {{16,32,64,128}}, k 1..8, kappa "
+                       f"log-uniform [1, 1e4], b = A x + 1e-6 N(0,1); pool of {pool_size} device-resident "
+                       f"problems; server: {streams} streams, <= {max_batch} per launch")
+    del pool
+    torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------------ reference
 def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -379,6 +529,10 @@ def bench_ours(args):
         tsbuild.build()
     if world > 1:
         dist.barrier()
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"served": bench_served(ts)}), flush=True)
+        return 0
 
     m, n = args.m, args.n
     two = args.tree == "two-level"
@@ -483,6 +637,8 @@ def bench_ours(args):
     mixed = None if args.no_mixed or rank != 0 else bench_mixed_lsq(ts)
     torch.cuda.empty_cache()
     batched = None if args.no_batch or rank != 0 else bench_batched(ts, args.batch_count)
+    torch.cuda.empty_cache()
+    served = None if args.no_serve or rank != 0 else bench_served(ts)
 
     if rank == 0:
         line = {
@@ -505,7 +661,7 @@ def bench_ours(args):
                          "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; no FP64 entry "
                                       "in the measured peaks)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
-            "mixed_lsq": mixed, "batched": batched,
+            "mixed_lsq": mixed, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -47,8 +47,9 @@ typedef enum {
 
 typedef enum {
   TSQR_FP64 = 0,  /* every operation in FP64 */
-  TSQR_MIXED = 1  /* leaves in FP32 (3xTF32 tensor-core updates), tree and
-                     refinement in FP64 (least squares only) */
+  TSQR_MIXED = 1, /* leaf factorizations in FP32 (A rounded on load), tree and
+                     refinement in FP64 */
+  TSQR_AUTO = 2   /* batch items only: FP64 or MIXED by a cost model (R-only items: FP64) */
 } tsqr_prec;
 
 /* flags for tsqr_factor */
@@ -210,14 +211,22 @@ typedef struct tsqr_batch_item {
   int64_t m;
   int32_t n;        /* 1 <= n <= 128, m >= n */
   int64_t lda;
-  const double *B;  /* device, m-by-k (ldb >= m) right-hand sides, or NULL with k = 0 */
+  const double *B;  /* device, m-by-k (ldb >= m) right-hand sides, or NULL with k = 0;
+                       not modified */
   int64_t ldb;
-  int32_t k;        /* 0 <= k, n + k <= 128 */
+  int32_t k;        /* 0 <= k <= 64; FP64 items: n + k <= 144 */
   double *R;        /* device, n-by-n (ldr >= n) output with diag(R) >= 0, or NULL */
   int64_t ldr;
-  double *X;        /* device, n-by-k (ldx >= n) least-squares solution, or NULL */
+  double *X;        /* device, n-by-k (ldx >= n) least-squares solution; may be NULL only
+                       for FP64 items */
   int64_t ldx;
-  int32_t prec;     /* TSQR_FP64, or TSQR_MIXED: FP32 leaf chains + FP64 tree (R only, k = 0) */
+  int32_t prec;     /* TSQR_FP64: FP64 TSQR of [A | B], X by back substitution.
+                       TSQR_MIXED: FP32 leaf chains + FP64 tree for R; with k > 0, X by
+                       corrected semi-normal-equation refinement in FP64 from X = 0
+                       (r = B - A X, R^T R dX = A^T r), at most 10 steps, stopping once the
+                       predicted remaining ||dX||_F/||X||_F is below 1e-12 or the
+                       corrections stop shrinking; R-only MIXED items carry FP32 accuracy.
+                       TSQR_AUTO: one of the two by a cost model (R-only items: FP64). */
 } tsqr_batch_item;
 
 /*
@@ -228,10 +237,53 @@ typedef struct tsqr_batch_item {
  *   status       host array of count int32 or NULL: 0, or TSQR_ERR_SINGULAR when the
  *                item's R has an exactly zero diagonal entry (its X is then undefined).
  *                Filling it synchronizes the stream.
+ *   info         host array of 2 * count doubles or NULL: for item q, info[2q] = refinement
+ *                steps run and info[2q + 1] = the last ||dX||_F / ||X||_F (the largest over
+ *                its groups of 8 right-hand sides); both 0 for items solved without
+ *                refinement. Filling it synchronizes the stream.
  *   Errors: TSQR_ERR_ARG (invalid item; nothing is enqueued), TSQR_ERR_OOM, TSQR_ERR_CUDA.
  */
 tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
-                             int32_t arity, void *stream, int32_t *status);
+                             int32_t arity, void *stream, int32_t *status, double *info);
+
+/*
+ * Continuous-batching server (the paper has no counterpart; it serves many independent
+ * least-squares requests with the batched kernel above). A worker thread owned by the
+ * server keeps up to `streams` batches in flight on the current device; whenever a
+ * stream is free it admits the oldest pending requests that fit the device-memory budget
+ * still free, up to max_batch of them, and runs them as one tsqr_batch_solve launch.
+ * Results are bitwise identical to solving the request alone with tsqr_batch_solve and
+ * the same chain_tiles (the batched kernel is deterministic per item).
+ *
+ * tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, &srv)
+ *   max_bytes    device-memory budget for in-flight requests' workspaces (bytes);
+ *                <= 0 = half the device memory free at creation. A request larger than
+ *                the whole budget runs alone once nothing else is in flight.
+ *   max_batch    >= 1, requests per launch.   streams  1..16 batches in flight.
+ *   chain_tiles  as for tsqr_batch_solve (0 = automatic).
+ *   Errors: TSQR_ERR_ARG, TSQR_ERR_OOM, TSQR_ERR_CUDA.
+ * tsqr_server_submit(srv, item, &ticket)
+ *   Validates the item (TSQR_ERR_ARG as tsqr_batch_solve, nothing queued) and queues a
+ *   copy of it; the item's device buffers must stay valid, and A/B unmodified, until its
+ *   ticket is returned by tsqr_server_poll. Tickets count up from 0 per server.
+ * tsqr_server_poll(srv, max, tickets, latency_s, status, &count)
+ *   Moves up to max completed requests into the host arrays (any may be NULL):
+ *   ticket, seconds from submission to completion, and the item status (0, or
+ *   TSQR_ERR_SINGULAR, or the error that made its batch fail). Never blocks.
+ * tsqr_server_drain(srv)       blocks until every submitted request has completed.
+ * tsqr_server_stats(srv, out)  out[6] (host): submitted, completed, batches launched,
+ *                              largest batch, budget bytes, bytes in flight.
+ * tsqr_server_destroy(srv)     finishes every queued request, then frees the server.
+ */
+typedef struct tsqr_server tsqr_server;
+tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t streams, int32_t chain_tiles,
+                               tsqr_server **srv);
+tsqr_status tsqr_server_submit(tsqr_server *srv, const tsqr_batch_item *item, int64_t *ticket);
+tsqr_status tsqr_server_poll(tsqr_server *srv, int32_t max, int64_t *tickets, double *latency_s,
+                             int32_t *status, int32_t *count);
+tsqr_status tsqr_server_drain(tsqr_server *srv);
+tsqr_status tsqr_server_stats(tsqr_server *srv, int64_t *out);
+tsqr_status tsqr_server_destroy(tsqr_server *srv);
 
 /* launch classes reported by the profiler */
 enum {
@@ -241,7 +293,8 @@ enum {
   TSQR_PROF_APPLY_Q = 3,
   TSQR_PROF_FORM_Q = 4,
   TSQR_PROF_SMALL = 5,         /* sign fix, scaling, triangular solve */
-  TSQR_PROF_BATCH = 6          /* the persistent batched kernel */
+  TSQR_PROF_BATCH = 6,         /* the persistent batched kernel */
+  TSQR_PROF_REFINE = 7         /* batched least-squares refinement steps */
 };
 
 /*

@@ -21,6 +21,7 @@ __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq"
 
 FP64 = 0
 MIXED = 1
+AUTO = 2
 INPLACE = 1
 TWO_LEVEL = 2
 TSQRError = _lib.TSQRError
@@ -146,55 +147,127 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
 
 
 PROFILE_KINDS = {0: "factor_chains", 1: "factor_tree", 2: "apply_qt", 3: "apply_q", 4: "form_q",
-                 5: "small", 6: "batch"}
+                 5: "small", 6: "batch", 7: "refine"}
 
 
-def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status: bool = False):
+def _fill_item(slot, it):
+    """Fills one tsqr_batch_item from a request dict; returns (tensors to keep alive,
+    (R, X) outputs)."""
+    import torch
+    A = it["A"]
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    B = it.get("B")
+    k = 0
+    ldb = m
+    X = it.get("X")
+    if B is not None:
+        ldb = _check_mat(B, "B", rows=m)
+        k = B.shape[1]
+        if X is None:
+            X = torch.empty((k, n), dtype=torch.float64, device=A.device).t()
+    R = it.get("R")
+    if R is None and it.get("want_r", True):
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    slot.A = A.data_ptr()
+    slot.m, slot.n, slot.lda = m, n, lda
+    slot.B = B.data_ptr() if B is not None else None
+    slot.ldb, slot.k = ldb, k
+    slot.R = R.data_ptr() if R is not None else None
+    slot.ldr = _check_mat(R, "R", rows=n, cols=n) if R is not None else n
+    slot.X = X.data_ptr() if X is not None else None
+    slot.ldx = _check_mat(X, "X", rows=n, cols=k) if X is not None else n
+    slot.prec = it.get("prec", FP64)
+    return [A, B, R, X], (R, X if k else None)
+
+
+def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status: bool = False,
+                info: bool = False):
     """Factor (and solve) many independent problems in one persistent launch.
 
     items: list of dicts with "A" (m-by-n column-major float64 CUDA tensor) and optional
     "B" (m-by-k), "R" and "X" output tensors (allocated here when missing and "want_r" /
     B are given) and "prec" (FP64 or MIXED; MIXED takes no B). Returns the list of
     (R, X) per item (None where not requested); with ``status`` also the per-item status
-    codes (this synchronizes the stream).
+    codes, and with ``info`` the per-item (refinement steps, last ||dX||/||X||) (both
+    synchronize the stream).
     """
-    import torch
     lib = _lib.load()
     arr = (_lib.BatchItem * max(1, len(items)))()
     keep = []
     outs = []
     for q, it in enumerate(items):
-        A = it["A"]
-        lda = _check_mat(A, "A")
-        m, n = A.shape
-        B = it.get("B")
-        k = 0
-        ldb = m
-        X = it.get("X")
-        if B is not None:
-            ldb = _check_mat(B, "B", rows=m)
-            k = B.shape[1]
-            if X is None:
-                X = torch.empty((k, n), dtype=torch.float64, device=A.device).t()
-        R = it.get("R")
-        if R is None and it.get("want_r", True):
-            R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
-        arr[q].A = A.data_ptr()
-        arr[q].m, arr[q].n, arr[q].lda = m, n, lda
-        arr[q].B = B.data_ptr() if B is not None else None
-        arr[q].ldb, arr[q].k = ldb, k
-        arr[q].R = R.data_ptr() if R is not None else None
-        arr[q].ldr = _check_mat(R, "R", rows=n, cols=n) if R is not None else n
-        arr[q].X = X.data_ptr() if X is not None else None
-        arr[q].ldx = _check_mat(X, "X", rows=n, cols=k) if X is not None else n
-        arr[q].prec = it.get("prec", FP64)
-        keep += [A, B, R, X]
-        outs.append((R, X if k else None))
+        kp, out = _fill_item(arr[q], it)
+        keep += kp
+        outs.append(out)
     st = (ctypes.c_int32 * max(1, len(items)))() if status else None
-    _lib.check(lib.tsqr_batch_solve(arr, len(items), chain_tiles, arity, _stream(stream), st), "tsqr_batch_solve")
+    inf = (ctypes.c_double * max(2, 2 * len(items)))() if info else None
+    _lib.check(lib.tsqr_batch_solve(arr, len(items), chain_tiles, arity, _stream(stream), st, inf),
+               "tsqr_batch_solve")
+    ret = [outs]
     if status:
-        return outs, [st[q] for q in range(len(items))]
-    return outs
+        ret.append([st[q] for q in range(len(items))])
+    if info:
+        ret.append([(int(inf[2 * q]), inf[2 * q + 1]) for q in range(len(items))])
+    return ret[0] if len(ret) == 1 else tuple(ret)
+
+
+class Server:
+    """Continuous-batching least-squares server on the current CUDA device.
+
+    submit() queues one request (a dict as for batch_solve) and returns its ticket and
+    its (R, X) output tensors, which are valid once poll() has returned the ticket.
+    Requests still in flight are kept alive here until then. The worker is native (a C++
+    thread inside the library); this class only marshals arguments.
+    """
+
+    def __init__(self, max_bytes: int = 0, max_batch: int = 256, streams: int = 2, chain_tiles: int = 0):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctypes.byref(self._h)),
+                   "tsqr_server_create")
+        self._live = {}
+
+    def submit(self, item):
+        slot = _lib.BatchItem()
+        keep, out = _fill_item(slot, item)
+        t = ctypes.c_int64(0)
+        _lib.check(self._lib.tsqr_server_submit(self._h, ctypes.byref(slot), ctypes.byref(t)), "tsqr_server_submit")
+        self._live[t.value] = keep
+        return t.value, out
+
+    def poll(self, max_count: int = 4096):
+        """Completed requests as a list of (ticket, latency seconds, status)."""
+        tk = (ctypes.c_int64 * max_count)()
+        lat = (ctypes.c_double * max_count)()
+        st = (ctypes.c_int32 * max_count)()
+        c = ctypes.c_int32(0)
+        _lib.check(self._lib.tsqr_server_poll(self._h, max_count, tk, lat, st, ctypes.byref(c)), "tsqr_server_poll")
+        res = [(tk[i], lat[i], st[i]) for i in range(c.value)]
+        for t, _, _ in res:
+            self._live.pop(t, None)
+        return res
+
+    def drain(self):
+        _lib.check(self._lib.tsqr_server_drain(self._h), "tsqr_server_drain")
+
+    def stats(self):
+        out = (ctypes.c_int64 * 6)()
+        _lib.check(self._lib.tsqr_server_stats(self._h, out), "tsqr_server_stats")
+        keys = ("submitted", "completed", "batches", "max_batch", "budget_bytes", "bytes_in_flight")
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if self._h:
+            _lib.check(self._lib.tsqr_server_destroy(self._h), "tsqr_server_destroy")
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def profile_collect(fn):

@@ -37,8 +37,16 @@ SIGNATURES = {
                           _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tsqr_solve_r": (_i32, [_vp, _dp, _i64, _i32, _dp, _i64, _dp, _vp]),
     "tsqr_lstsq_static": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _vp]),
-    "tsqr_batch_solve": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _vp, ctypes.POINTER(_i32)]),
+    "tsqr_batch_solve": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _vp, ctypes.POINTER(_i32),
+                                 ctypes.POINTER(ctypes.c_double)]),
     "tsqr_free": (_i32, [_vp]),
+    "tsqr_server_create": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    "tsqr_server_submit": (_i32, [_vp, ctypes.POINTER(BatchItem), ctypes.POINTER(_i64)]),
+    "tsqr_server_poll": (_i32, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "tsqr_server_drain": (_i32, [_vp]),
+    "tsqr_server_stats": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "tsqr_server_destroy": (_i32, [_vp]),
     "tsqr_profile_start": (_i32, []),
     "tsqr_profile_stop": (_i32, [_i64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(_i64)]),

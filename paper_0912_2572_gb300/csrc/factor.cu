@@ -132,7 +132,8 @@ __device__ __forceinline__ void gram_row_dispatch(const R *T, int ldt, int j, in
     case 5: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
     case 6: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
     case 7: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    default: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    case 8: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
+    default: if (CMAX >= 16) gram_row<(CMAX >= 16 ? 9 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
   }
 }
 
@@ -148,7 +149,8 @@ __device__ __forceinline__ void update_dispatch(R *T, int ldt, int j, int nc, in
     case 5: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
     case 6: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
     case 7: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    default: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    case 8: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
+    default: if (CMAX >= 16) trailing_update<(CMAX >= 16 ? 9 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
   }
 }
 
@@ -208,7 +210,7 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
   auto piv_ptr = [&](int j, int c) -> R * {
     return (c < n) ? p.V + pr + j + (int64_t)c * p.ldv : p.B + pr + j + (int64_t)(c - n) * p.ldb;
   };
-  constexpr int PFN = (CMAX * 16 + 31) / 32;
+  constexpr int PFN = (CMAX > 8 ? 144 + 31 : CMAX * 16 + 31) / 32;  // columns after the pivot
 
   for (int tt = 0; tt < job.tile_count; ++tt) {
     const TileDesc td = p.tiles[job.tile_begin + tt];
@@ -477,7 +479,8 @@ cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t
   if (cmax <= 1) return go(k_factor_batch<1>);
   if (cmax <= 2) return go(k_factor_batch<2>);
   if (cmax <= 4) return go(k_factor_batch<4>);
-  return go(k_factor_batch<8>);
+  if (cmax <= 8) return go(k_factor_batch<8>);
+  return go(k_factor_batch<16>);
 }
 
 }  // namespace tsqr

@@ -426,6 +426,19 @@ static void plan_info(const Plan &pl, int64_t *out) {
 // problem (about kappa * u), so further corrections change nothing measurable.
 constexpr double kRefineTol = 1e-13;
 
+// Batched mixed least squares (refine_batch.cu): rows per refinement task, the number of
+// refinement launches, and the stopping tolerance on the predicted remaining
+// ||dX||/||X|| (the last correction times rho / (1 - rho), rho the observed contraction).
+constexpr int64_t kRefineRows = 4096;
+constexpr int32_t kRefineSteps = 10;
+constexpr double kBatchRefineTol = 1e-12;
+// Cost model of TSQR_AUTO: share of the FP64 peak reached by the factor kernel and by the
+// refinement kernel, FP32 factor throughput over FP64, refinement steps assumed.
+constexpr double kFactorEff = 0.85;
+constexpr double kRefineEff = 0.8;
+constexpr double kFp32Ratio = 8.0;
+constexpr double kRefineStepsEst = 6.0;
+
 // Mixed-precision least squares: FP32 chains (leaves and flat chains), FP64 tree on the
 // compact pivot blocks, then Bjorck augmented-system refinement with FP64 residuals
 // (mixed.cu). Right-hand sides are refined in groups of at most 8 columns.
@@ -605,8 +618,9 @@ static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t ld
 }
 
 // ---------------------------------------------------------------- batched solve
-static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
-                               cudaStream_t s, int32_t *status) {
+tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                                       int32_t arity, cudaStream_t s, int32_t *status, int32_t *status_async,
+                                       double *info) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   const DeviceInfo di = device_info(dev);
@@ -614,12 +628,18 @@ static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int3
   if (arity == 0) arity = 2;
   const int L = chain_tiles > 0 ? chain_tiles : 8;
   std::vector<Plan> plans(count);
+  std::vector<int32_t> prec(count);
   size_t smem = 0;
   int cmax = 1, cps_min = 2;
+  bool any_refine = false;
   for (int32_t q = 0; q < count; ++q) {
     const tsqr_batch_item &it = items[q];
-    const bool mixed = it.prec == TSQR_MIXED;
-    const int nc = it.n + it.k;
+    prec[q] = resolve_batch_prec(it);
+    const bool mixed = prec[q] == TSQR_MIXED;
+    any_refine = any_refine || (mixed && it.k > 0);
+    // FP64 items fuse Q^T B into the factorization; mixed items factor A alone and
+    // solve by refinement afterwards
+    const int nc = mixed ? it.n : it.n + it.k;
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     int th = 0, cps = 0;
     if (!choose_tiles(di, it.n, nc, 1 << 20, th, cps, elem))
@@ -727,7 +747,7 @@ static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int3
     const size_t elem = pl.mixed ? sizeof(float) : sizeof(double);
     const size_t nrefl = pl.tiles.size() * (size_t)it.n;
     offs[q].V = take(elem * (size_t)it.m * it.n);
-    offs[q].B = it.k > 0 ? take(sizeof(double) * (size_t)it.m * it.k) : 0;
+    offs[q].B = (!pl.mixed && it.k > 0) ? take(sizeof(double) * (size_t)it.m * it.k) : 0;
     offs[q].tau = take(elem * nrefl);
     offs[q].scl = take(elem * nrefl);
     if (pl.mixed) {
@@ -742,6 +762,59 @@ static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int3
   const size_t o_tiles = take(sizeof(TileDesc) * (size_t)ntiles);
   const size_t o_cnt = take(sizeof(int32_t) * ((size_t)njobs + 1));
   const size_t o_st = take(sizeof(int32_t) * count);
+  // refinement of mixed least-squares items: one instance per group of <= 8 right-hand
+  // sides, tasks of kRefineRows rows
+  std::vector<int64_t> root(count, -1);  // where each item's R lands in its tree storage
+  for (int32_t j = 0; j < njobs; ++j)
+    if (jobs[j].parent < 0) root[jobs[j].inst] = jobs[j].row64;
+  struct RefOff {
+    int32_t item;
+    size_t P;
+  };
+  std::vector<RefOff> roffs;
+  std::vector<RefineInst> rinst;
+  std::vector<RefineTask> rtasks;
+  size_t rsmem = 0, o_rinst = 0, o_rtasks = 0, o_rflags = 0;
+  for (int32_t q = 0; q < count && any_refine; ++q) {
+    const tsqr_batch_item &it = items[q];
+    if (prec[q] != TSQR_MIXED || it.k == 0) continue;
+    if (root[q] < 0) return fail(TSQR_ERR_CUDA, "item %d: the plan has no root job", q);
+    const int32_t nt = (int32_t)((it.m + kRefineRows - 1) / kRefineRows);
+    for (int32_t c0 = 0; c0 < it.k; c0 += 8) {
+      RefineInst ri{};
+      ri.n = it.n;
+      ri.k = std::min(8, it.k - c0);
+      ri.kb = ri.k <= 1 ? 1 : (ri.k <= 2 ? 2 : (ri.k <= 4 ? 4 : 8));
+      ri.nt = nt;
+      ri.A = it.A;
+      ri.lda = it.lda;
+      ri.B = it.B + (int64_t)c0 * it.ldb;
+      ri.ldb = it.ldb;
+      ri.X = it.X + (int64_t)c0 * it.ldx;
+      ri.ldx = it.ldx;
+      ri.ldr = (int64_t)plans[q].launches[0].job_count * it.n;  // compact FP64 tree storage
+      const int32_t ix = (int32_t)rinst.size();
+      for (int32_t t = 0; t < nt; ++t) {
+        RefineTask tk{};
+        tk.row0 = (int64_t)t * kRefineRows;
+        tk.rows = (int32_t)std::min<int64_t>(kRefineRows, it.m - tk.row0);
+        tk.inst = ix;
+        tk.idx = t;
+        rtasks.push_back(tk);
+      }
+      const size_t oP = take(sizeof(double) * (size_t)nt * it.n * ri.k);
+      roffs.push_back({q, oP});
+      rinst.push_back(ri);
+      rsmem = std::max(rsmem, refine_smem_bytes(it.n, ri.kb));
+    }
+  }
+  size_t o_rhist = 0;
+  if (!rinst.empty()) {
+    o_rhist = take(sizeof(double) * kRefineSteps * rinst.size());  // -1 = step not run
+    o_rinst = take(sizeof(RefineInst) * rinst.size());
+    o_rtasks = take(sizeof(RefineTask) * rtasks.size());
+    o_rflags = take(sizeof(int32_t) * 2 * rinst.size());
+  }
   void *blk = nullptr;
   CUDA_TRY(pool_alloc(&blk, off, s));
   char *base = (char *)blk;
@@ -771,14 +844,15 @@ static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int3
     }
     bi.R = it.R;
     bi.ldr = it.ldr;
-    bi.X = it.X;
+    bi.X = pl.mixed ? nullptr : it.X;  // mixed items are solved by the refinement launches
     bi.ldx = it.ldx;
     bi.status = (int32_t *)(base + o_st) + q;
     bi.n = it.n;
-    bi.k = it.k;
+    bi.k = pl.mixed ? 0 : it.k;
     bi.ldt = pl.tile_h;
     bi.mixed = pl.mixed ? 1 : 0;
-    if (it.k > 0)
+    if (pl.mixed) bi.B = nullptr;
+    if (bi.k > 0)
       CUDA_TRY(cudaMemcpy2DAsync(bi.B, sizeof(double) * it.m, it.B, sizeof(double) * it.ldb, sizeof(double) * it.m,
                                  it.k, cudaMemcpyDeviceToDevice, s));
   }
@@ -799,15 +873,111 @@ static tsqr_status batch_solve(const tsqr_batch_item *items, int32_t count, int3
     ProfScope ps(TSQR_PROF_BATCH, s);
     CUDA_TRY(launch_factor_batch(bp, cmax, grid, smem, s));
   }
+  if (!rinst.empty()) {
+    int32_t *flags = (int32_t *)(base + o_rflags);  // counter, done per instance
+    for (size_t r = 0; r < rinst.size(); ++r) {
+      const RefOff &ro = roffs[r];
+      RefineInst &ri = rinst[r];
+      ri.R = inst[ro.item].V64 + root[ro.item];
+      ri.P = (double *)(base + ro.P);
+      ri.hist = (double *)(base + o_rhist) + (size_t)kRefineSteps * r;
+      ri.counter = flags + 2 * r;
+      ri.done = flags + 2 * r + 1;
+      ri.status = (int32_t *)(base + o_st) + ro.item;
+    }
+    CUDA_TRY(cudaMemcpyAsync(base + o_rinst, rinst.data(), sizeof(RefineInst) * rinst.size(), cudaMemcpyHostToDevice,
+                             s));
+    CUDA_TRY(cudaMemcpyAsync(base + o_rtasks, rtasks.data(), sizeof(RefineTask) * rtasks.size(),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 2 * rinst.size(), s));
+    {
+      const std::vector<double> neg((size_t)kRefineSteps * rinst.size(), -1.0);  // staged before return
+      CUDA_TRY(cudaMemcpyAsync(base + o_rhist, neg.data(), sizeof(double) * neg.size(), cudaMemcpyHostToDevice, s));
+    }
+    RefineParams rp{};
+    rp.inst = (const RefineInst *)(base + o_rinst);
+    rp.tasks = (const RefineTask *)(base + o_rtasks);
+    rp.max_steps = kRefineSteps;
+    rp.tol = kBatchRefineTol;
+    ProfScope ps(TSQR_PROF_REFINE, s);
+    for (int32_t step = 0; step < kRefineSteps; ++step) {
+      rp.step = step;
+      CUDA_TRY(launch_refine_batch(rp, (int)rtasks.size(), rsmem, s));
+    }
+  }
   tsqr_status st = TSQR_OK;
+  if (status_async) {
+    cudaError_t e = cudaMemcpyAsync(status_async, base + o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status copy: %s", cudaGetErrorString(e));
+  }
   if (status) {
     cudaError_t e = cudaMemcpyAsync(status, base + o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
   }
+  if (info) {
+    for (int32_t q = 0; q < count; ++q) info[2 * q] = info[2 * q + 1] = 0.0;
+    std::vector<double> hist((size_t)kRefineSteps * rinst.size());
+    cudaError_t e = cudaSuccess;
+    if (!hist.empty()) {
+      e = cudaMemcpyAsync(hist.data(), base + o_rhist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+      st = fail(TSQR_ERR_CUDA, "refinement history readback: %s", cudaGetErrorString(e));
+    } else {
+      for (size_t r = 0; r < rinst.size(); ++r) {
+        int steps = 0;
+        while (steps < kRefineSteps && hist[(size_t)kRefineSteps * r + steps] >= 0.0) ++steps;
+        double *o = info + 2 * roffs[r].item;
+        o[0] = std::max(o[0], (double)steps);
+        if (steps > 0) o[1] = std::max(o[1], hist[(size_t)kRefineSteps * r + steps - 1]);
+      }
+    }
+  }
   cudaFreeAsync(blk, s);
   return st;
 }
+
+tsqr_status tsqr::check_batch_item(const tsqr_batch_item &it, int32_t q) {
+  tsqr_status st = check_factor_args(it.A, it.m, it.n, it.lda, it.n, 2);
+  if (st != TSQR_OK) return fail(st, "item %d: %s", q, g_last_error.c_str());
+  if (it.prec != TSQR_FP64 && it.prec != TSQR_MIXED && it.prec != TSQR_AUTO)
+    return fail(TSQR_ERR_ARG, "item %d: unknown prec", q);
+  if (it.k < 0 || it.k > 64) return fail(TSQR_ERR_ARG, "item %d: k=%d outside [0, 64]", q, it.k);
+  if (it.prec == TSQR_FP64 && it.n + it.k > 144)
+    return fail(TSQR_ERR_ARG, "item %d: FP64 item with n + k = %d > 144", q, it.n + it.k);
+  if (it.k > 0 && (!it.B || it.ldb < it.m || (it.X && it.ldx < it.n))) return fail(TSQR_ERR_ARG, "item %d: bad B/X", q);
+  if (it.k > 0 && it.prec != TSQR_FP64 && !it.X) return fail(TSQR_ERR_ARG, "item %d: X is required", q);
+  if (it.R && it.ldr < it.n) return fail(TSQR_ERR_ARG, "item %d: ldr < n", q);
+  return TSQR_OK;
+}
+
+// FP64 or mixed for a TSQR_AUTO item, by a cost model in units of FP64 flops per row of A:
+// FP64 factors [A | B] (2 (n + k)^2 flops, at the factor kernel's share of the FP64
+// peak); mixed factors A on the FP32 pipe (2 n^2 flops at kFp32Ratio times the FP64 rate)
+// and then runs kRefineStepsEst refinement steps of 4 n kb FP64 flops. R-only items, and
+// items with n + k too wide to fuse, follow the accuracy and shape constraints first.
+int32_t tsqr::resolve_batch_prec(const tsqr_batch_item &it) {
+  if (it.prec != TSQR_AUTO) return it.prec;
+  if (it.k == 0) return TSQR_FP64;
+  if (it.n + it.k > 144) return TSQR_MIXED;
+  const double n = it.n, k = it.k;
+  const double kb = it.k <= 1 ? 1 : (it.k <= 2 ? 2 : (it.k <= 4 ? 4 : (it.k <= 8 ? 8 : 8 * std::ceil(k / 8))));
+  const double fp64 = 2.0 * (n + k) * (n + k) / kFactorEff;
+  const double mixed = 2.0 * n * n / (kFp32Ratio * kFactorEff) + kRefineStepsEst * 4.0 * n * kb / kRefineEff;
+  return mixed < fp64 ? TSQR_MIXED : TSQR_FP64;
+}
+
+size_t tsqr::batch_item_bytes(const tsqr_batch_item &it) {
+  const bool mixed = resolve_batch_prec(it) == TSQR_MIXED;
+  const size_t m = (size_t)it.m, n = (size_t)it.n, k = (size_t)it.k;
+  if (mixed)  // FP32 chains, FP64 tree blocks, refinement partials
+    return 4 * m * n + 8 * (m / 64 + 1) * n + 8 * (m / kRefineRows + 1) * n * k + n * n * 64 + 65536;
+  return 8 * m * n + 8 * m * k + n * n * 64 + 65536;
+}
+
+const char *tsqr::last_error_text() { return g_last_error.c_str(); }
 
 extern "C" {
 
@@ -983,25 +1153,19 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   return st;
 }
 
+
 tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
-                             void *stream, int32_t *status) {
+                             void *stream, int32_t *status, double *info) {
   g_last_error.clear();
   if (count < 0 || (count > 0 && !items)) return fail(TSQR_ERR_ARG, "bad items/count");
   if (chain_tiles < 0 || !(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "bad chain_tiles/arity");
   for (int32_t q = 0; q < count; ++q) {
-    const tsqr_batch_item &it = items[q];
-    tsqr_status st = check_factor_args(it.A, it.m, it.n, it.lda, it.n, 2);
-    if (st != TSQR_OK) return fail(st, "item %d: %s", q, g_last_error.c_str());
-    if (it.k < 0 || it.n + it.k > 128) return fail(TSQR_ERR_ARG, "item %d: k=%d with n=%d", q, it.k, it.n);
-    if (it.k > 0 && (!it.B || it.ldb < it.m || (it.X && it.ldx < it.n)))
-      return fail(TSQR_ERR_ARG, "item %d: bad B/X", q);
-    if (it.R && it.ldr < it.n) return fail(TSQR_ERR_ARG, "item %d: ldr < n", q);
-    if (it.prec != TSQR_FP64 && it.prec != TSQR_MIXED) return fail(TSQR_ERR_ARG, "item %d: unknown prec", q);
-    if (it.prec == TSQR_MIXED && it.k > 0) return fail(TSQR_ERR_ARG, "item %d: MIXED items take k = 0", q);
+    tsqr_status st = check_batch_item(items[q], q);
+    if (st != TSQR_OK) return st;
   }
   if (count == 0) return TSQR_OK;
   try {
-    return batch_solve(items, count, chain_tiles, arity, (cudaStream_t)stream, status);
+    return batch_solve_internal(items, count, chain_tiles, arity, (cudaStream_t)stream, status, nullptr, info);
   } catch (const std::bad_alloc &) {
     return fail(TSQR_ERR_OOM, "host allocation failed");
   }

@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/tsqr.h"
+
 namespace tsqr {
 
 enum TileKind : int32_t { GEQRT = 0, TSQRT = 1, TTQRT = 2 };
@@ -124,6 +126,54 @@ struct BatchParams {
 };
 
 cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s);
+
+// ------------------------------------------------ batched least-squares refinement
+// Mixed-precision least-squares items of a batch: after the batched factorization, one
+// launch per step of corrected semi-normal-equation refinement (refine_batch.cu). A
+// refinement instance is one item and a group of at most 8 right-hand sides.
+struct RefineInst {
+  const double *A;     // the item's A, m-by-n, lda
+  int64_t lda;
+  const double *B;     // the group's right-hand sides, m-by-k, ldb
+  int64_t ldb;
+  double *X;           // the group's solution columns, n-by-k, ldx (written from step 0)
+  int64_t ldx;
+  const double *R;     // the item's FP64 R (upper triangle; any diagonal signs), ldr
+  int64_t ldr;
+  double *P;           // partial A^T r of each task, nt blocks of n-by-k
+  int32_t *counter;    // task arrivals of the current step (reset by the last one)
+  int32_t *done;       // 1 once the group has converged or R is singular
+  int32_t *status;     // the item's status word (TSQR_ERR_SINGULAR)
+  double *hist;        // ||dX||_F / ||X||_F per step
+  int32_t n, k, kb, nt;  // kb = k rounded up to 1, 2, 4 or 8; nt = tasks
+};
+
+struct RefineTask {
+  int64_t row0;        // first row of the task's block
+  int32_t rows;
+  int32_t inst;        // refinement instance
+  int32_t idx;         // task index within the instance (partial slot)
+  int32_t pad;
+};
+
+struct RefineParams {
+  const RefineInst *inst;
+  const RefineTask *tasks;
+  int32_t step, max_steps;
+  double tol;          // stop once the predicted remaining ||dX|| / ||X|| is below tol
+};
+
+int refine_rows_per_chunk(int n);
+size_t refine_smem_bytes(int n, int kb);
+cudaError_t launch_refine_batch(const RefineParams &p, int ntasks, size_t smem_bytes, cudaStream_t s);
+
+// host side of the batched path (tsqr_api.cu), also driven by the server (server.cu)
+tsqr_status batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                                 cudaStream_t s, int32_t *status, int32_t *status_async, double *info);
+tsqr_status check_batch_item(const tsqr_batch_item &it, int32_t q);
+size_t batch_item_bytes(const tsqr_batch_item &it);  // device workspace estimate for admission
+int32_t resolve_batch_prec(const tsqr_batch_item &it);  // TSQR_FP64 or TSQR_MIXED
+const char *last_error_text();
 
 // ------------------------------------------------------------------ apply kernels
 template <typename R>

@@ -171,3 +171,19 @@ def test_tile_capacity_choice(lib):
     # the leaf height caps the tile
     info, _, _ = describe(lib, 100_000, 16, 100, 2, 0)
     assert info["tile_rows"] == 100
+
+
+def test_server_entry_points_reject_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.tsqr_server_create(0, 0, 2, 0, ctypes.byref(h)) == 1      # max_batch < 1
+    assert lib.tsqr_server_create(0, 16, 0, 0, ctypes.byref(h)) == 1     # no stream
+    assert lib.tsqr_server_create(0, 16, 17, 0, ctypes.byref(h)) == 1    # too many streams
+    assert lib.tsqr_server_create(0, 16, 2, -1, ctypes.byref(h)) == 1    # chain_tiles < 0
+    assert lib.tsqr_server_create(0, 16, 2, 0, None) == 1
+    assert not h.value
+    c = ctypes.c_int32(0)
+    assert lib.tsqr_server_submit(None, None, None) == 1
+    assert lib.tsqr_server_poll(None, 4, None, None, None, ctypes.byref(c)) == 1
+    assert lib.tsqr_server_drain(None) == 1
+    assert lib.tsqr_server_stats(None, None) == 1
+    assert lib.tsqr_server_destroy(None) == 0

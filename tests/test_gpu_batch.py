@@ -81,3 +81,81 @@ def test_batch_singular_item(cuda_lib):
     res, st = run([good[0], (A, B, 0), good[1]])
     assert st == [0, 4, 0]
     assert rel(res[0][1], oracle.lstsq(good[0][0], good[0][1])) <= 1e-12
+
+
+@pytest.mark.parametrize("n,k", [(128, 8), (128, 16), (120, 20), (100, 3)])
+def test_batch_wide_least_squares(cuda_lib, n, k):
+    """n + k up to 144: the persistent kernel's ninth column slot per half-warp."""
+    g = inputs.rng(n * 100 + k)
+    items = []
+    for q in range(5):
+        m = int(g.integers(n, 30000))
+        A = inputs.graded(m, n, 3.0, seed_g=q + 40, seed_v=q + 41)
+        B, _ = inputs.lstsq_rhs(A, k, 1e-6, q + 42)
+        items.append((A, B, 0))
+    res, st = run(items, chain_tiles=4)
+    assert st == [0] * len(items)
+    for (A, B, _), (R, X) in zip(items, res):
+        assert rel(R, oracle.r_factor(A)) <= 1e-12
+        assert rel(X, oracle.lstsq(A, B)) <= 1e-10
+
+
+def lsq_items(count, seed, prec, ns=(16, 32, 64, 100, 128), kmax=12, mhi=40000, dec_max=4.0):
+    g = inputs.rng(seed)
+    out = []
+    for q in range(count):
+        n = int(g.choice(ns))
+        m = max(int(np.exp(g.uniform(np.log(300), np.log(mhi)))), n)
+        k = int(g.integers(1, kmax + 1))
+        A = inputs.graded(m, n, float(g.uniform(0.0, dec_max)), seed_g=seed * 1000 + q, seed_v=seed * 1000 + q + 1)
+        B, _ = inputs.lstsq_rhs(A, k, 1e-6, seed * 1000 + q + 2)
+        out.append((A, B, prec))
+    return out
+
+
+def test_batch_mixed_least_squares_matches_oracle(cuda_lib):
+    """FP32 leaf chains, FP64 tree, FP64 refinement by corrected semi-normal equations:
+    ||x - x_oracle|| / ||x_oracle|| <= 1e-10 for kappa <= 1e4, including k > 8 (two
+    refinement groups) and ragged row blocks."""
+    items = lsq_items(24, 11, prec=1)
+    res, st = run(items)
+    assert st == [0] * len(items)
+    for (A, B, _), (R, X) in zip(items, res):
+        assert rel(X, oracle.lstsq(A, B)) <= 1e-10
+        assert rel(R, oracle.r_factor(A)) <= 1e-5  # R itself carries the FP32 leaves
+
+
+def test_batch_mixed_refinement_needs_more_than_one_step(cuda_lib):
+    """kappa = 1e4: the first semi-normal solve alone is far from FP64 accuracy, so the
+    result above is the refinement's doing."""
+    import paper_0912_2572_gb300 as ts
+    A = inputs.graded(20000, 64, 4.0, seed_g=5, seed_v=6)
+    B, _ = inputs.lstsq_rhs(A, 2, 1e-6, 7)
+    Xo = oracle.lstsq(A, B)
+    (R, X), = ts.batch_solve([{"A": to_dev(A), "B": to_dev(B), "prec": ts.MIXED}])
+    assert rel(to_host(X), Xo) <= 1e-10
+    # a plain FP32-accurate solve with the same R: x1 = R^{-1} R^{-T} A^T b
+    Rh = to_host(R)
+    x1 = np.linalg.solve(Rh, np.linalg.solve(Rh.T, A.T @ B))
+    assert rel(x1, Xo) > 1e-8
+
+
+def test_batch_auto_and_mixed_alone_equals_in_mix(cuda_lib):
+    items = lsq_items(16, 12, prec=2, kmax=8) + lsq_items(8, 13, prec=1, kmax=10)
+    res_mix, st = run(items, chain_tiles=8)
+    assert st == [0] * len(items)
+    for q in (0, 5, 17, 23):
+        res_alone, _ = run([items[q]], chain_tiles=8)
+        assert np.array_equal(res_alone[0][1], res_mix[q][1])
+        assert np.array_equal(res_alone[0][0], res_mix[q][0])
+    for (A, B, _), (R, X) in zip(items, res_mix):
+        assert rel(X, oracle.lstsq(A, B)) <= 1e-10
+
+
+def test_batch_mixed_singular_item(cuda_lib):
+    A = inputs.gaussian(5000, 12, 19)
+    A[:, 3] = 0.0
+    B = inputs.gaussian(5000, 2, 20)
+    good = lsq_items(2, 14, prec=1, kmax=3)
+    _, st = run([good[0], (A, B, 1), good[1]])
+    assert st == [0, 4, 0]

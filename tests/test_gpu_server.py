@@ -1,0 +1,120 @@
+"""The continuous-batching server: requests admitted by free device memory, batched into
+the persistent kernel on several streams. Each served result must be bitwise identical to
+the same request solved alone by the batched kernel, and match the FP64 oracle."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_2572_gb300 import inputs
+from conftest import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def requests(count, seed, mlo=300, mhi=40000, ns=(16, 32, 64, 128)):
+    g = inputs.rng(seed)
+    out = []
+    for q in range(count):
+        n = int(g.choice(ns))
+        m = max(int(np.exp(g.uniform(np.log(mlo), np.log(mhi)))), n)
+        k = int(g.integers(1, 9)) if n < 128 else 0
+        A = inputs.graded(m, n, 4.0, seed_g=seed * 1000 + q, seed_v=seed * 1000 + q + 1)
+        B = inputs.gaussian(m, k, seed * 1000 + q + 500) if k else None
+        out.append((A, B))
+    return out
+
+
+def serve(reqs, chain_tiles=8, **kw):
+    import paper_0912_2572_gb300 as ts
+    res = {}
+    with ts.Server(chain_tiles=chain_tiles, **kw) as srv:
+        outs = {}
+        for A, B in reqs:
+            item = {"A": to_dev(A)}
+            if B is not None:
+                item["B"] = to_dev(B)
+            t, out = srv.submit(item)
+            outs[t] = out
+        done = []
+        deadline = time.time() + 120
+        while len(done) < len(reqs) and time.time() < deadline:
+            done += srv.poll()
+            time.sleep(0.001)
+        stats = srv.stats()
+    assert len(done) == len(reqs)
+    for t, lat, st in done:
+        R, X = outs[t]
+        res[t] = (st, lat, to_host(R), to_host(X) if X is not None else None)
+    return res, stats
+
+
+def alone(A, B, chain_tiles=8):
+    import paper_0912_2572_gb300 as ts
+    item = {"A": to_dev(A)}
+    if B is not None:
+        item["B"] = to_dev(B)
+    (R, X), = ts.batch_solve([item], chain_tiles=chain_tiles)
+    return to_host(R), to_host(X) if X is not None else None
+
+
+def test_served_equals_alone_and_oracle(cuda_lib):
+    reqs = requests(48, 1)
+    res, stats = serve(reqs, max_batch=16, streams=2)
+    assert stats["completed"] == len(reqs) and stats["bytes_in_flight"] == 0
+    assert stats["batches"] >= 3
+    for t, (A, B) in enumerate(reqs):
+        st, lat, R, X = res[t]
+        assert st == 0 and lat > 0
+        R1, X1 = alone(A, B)
+        assert np.array_equal(R, R1)
+        if B is not None:
+            assert np.array_equal(X, X1)
+        if t % 6 == 0:
+            assert rel(R, oracle.r_factor(A)) <= 1e-12
+            if B is not None:
+                assert rel(X, oracle.lstsq(A, B)) <= 1e-10
+
+
+def test_admission_by_memory_budget(cuda_lib):
+    """A budget that holds one request at a time forces batches of one; each still runs."""
+    reqs = requests(6, 2, mlo=20000, mhi=30000, ns=(32,))
+    res, stats = serve(reqs, max_bytes=1, max_batch=64, streams=3)
+    assert stats["max_batch"] == 1 and stats["batches"] == len(reqs)
+    for t, (A, B) in enumerate(reqs):
+        st, _, R, X = res[t]
+        assert st == 0
+        assert np.array_equal(R, alone(A, B)[0])
+
+
+def test_server_reports_singular_and_rejects_bad_items(cuda_lib):
+    import paper_0912_2572_gb300 as ts
+    A = inputs.gaussian(3000, 8, 9)
+    A[:, 5] = 0.0
+    B = inputs.gaussian(3000, 1, 10)
+    good = requests(3, 3, ns=(16,))
+    res, _ = serve(good[:1] + [(A, B)] + good[1:], max_batch=8)
+    assert [res[t][0] for t in range(4)] == [0, 4, 0, 0]
+    with ts.Server() as srv:
+        bad = {"A": to_dev(inputs.gaussian(200, 8, 1)), "B": to_dev(inputs.gaussian(200, 140, 2))}  # n + k > 144
+        with pytest.raises(ts.TSQRError) as e:
+            srv.submit(bad)
+        assert e.value.status == 1
+        assert srv.stats()["submitted"] == 0
+
+
+def test_server_drain_and_destroy_finish_everything(cuda_lib):
+    import paper_0912_2572_gb300 as ts
+    reqs = requests(20, 4, mhi=5000)
+    srv = ts.Server(max_batch=4, streams=2)
+    keep = [srv.submit({"A": to_dev(A), **({"B": to_dev(B)} if B is not None else {})}) for A, B in reqs]
+    srv.drain()
+    assert srv.stats()["completed"] == len(reqs)
+    assert len(srv.poll()) == len(reqs)
+    srv.close()
+    assert keep
