@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
     {
       const int j0 = p.trans ? 0 : n - 1;
       int lo, hi;
-      refl_rows(kind, j0, ht, lo, hi);
+      refl_rows(kind, j0, ht, lo, hi, td.off);
 #pragma unroll
       for (int r = 0; r < RW; ++r) {
         const int i = lo + lane + 32 * r;
@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
     for (int s = 0; s < n; ++s) {
       const int j = p.trans ? s : n - 1 - s;
       int lo, hi;
-      refl_rows(kind, j, ht, lo, hi);
+      refl_rows(kind, j, ht, lo, hi, td.off);
       if (s + 1 < n) {
         const int jn = p.trans ? s + 1 : n - 2 - s;
         int lo2, hi2;
-        refl_rows(kind, jn, ht, lo2, hi2);
+        refl_rows(kind, jn, ht, lo2, hi2, td.off);
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
           const int i = lo2 + lane + 32 * r;
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
     R xv[RM], xn[RM];
     {
       int lo, hi;
-      refl_rows(kind, j0, ht, lo, hi);
+      refl_rows(kind, j0, ht, lo, hi, td.off);
 #pragma unroll
       for (int r = 0; r < RM; ++r) {
         const int i = lo + hl + 16 * r;
@@ -404,12 +404,12 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
       const bool more = (s + 1 < n);
       const int jn = p.trans ? s + 1 : n - 2 - s;
       int lo, hi;
-      refl_rows(kind, j, ht, lo, hi);
+      refl_rows(kind, j, ht, lo, hi, td.off);
       const int cs = p.formq ? max(0, j - col0) : 0;  // first column this reflector touches
       // prefetch the next reflector's tail (registers) and pivot row (warp 1)
       if (more) {
         int lo2, hi2;
-        refl_rows(kind, jn, ht, lo2, hi2);
+        refl_rows(kind, jn, ht, lo2, hi2, td.off);
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
           const int i = lo2 + hl + 16 * r;

@@ -214,9 +214,11 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
 
   for (int tt = 0; tt < job.tile_count; ++tt) {
     const TileDesc td = p.tiles[job.tile_begin + tt];
-    const int ht = td.nrows, kind = td.kind;
+    const int ht = td.nrows, kind = td.kind, off = td.off;
     const int64_t r0 = td.row0;
     const bool ge = (kind == GEQRT);
+    // a TTQRT piece starting at row `off` of the child is untouched by reflectors j < off
+    const int j0 = (kind == TTQRT) ? off : 0;
 
     // stage the tile: GEQRT/TSQRT tiles come from A (first touch), TTQRT from V
     for (int c = warp; c < nc; c += kThreads / 32) {
@@ -230,12 +232,16 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
       }
     }
     if (!ge)
-      for (int c = tid; c < nc; c += kThreads) PV[c] = __ldcg(piv_ptr(0, c));
+      for (int c = tid; c < nc; c += kThreads) PV[c] = (c >= j0) ? __ldcg(piv_ptr(j0, c)) : R(0);
+    for (int j = tid; j < j0; j += kThreads) {  // identity reflectors
+      p.tau[td.refl + j] = R(0);
+      p.scl[td.refl + j] = R(0);
+    }
     __syncthreads();
 
-    for (int j = 0; j < n; ++j) {
+    for (int j = j0; j < n; ++j) {
       int lo, hi;
-      refl_rows(kind, j, ht, lo, hi);
+      refl_rows(kind, j, ht, lo, hi, off);
       // warp 1 prefetches pivot row j+1 (not written before step j+1)
       R pf[PFN];
       const bool do_pf = (!ge) && warp == 1 && (j + 1 < n);
@@ -292,7 +298,7 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
     for (int c = warp; c < nc; c += kThreads / 32) {
       R *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
       const R *src = T + (size_t)c * ldt;
-      const int lim = (kind == TTQRT && c < n) ? min(ht, c + 1) : ht;
+      const int lim = (kind == TTQRT && c < n) ? max(0, min(ht, c + 1 - off)) : ht;
       for (int i = lane; i < lim; i += 32) dst[i] = src[i];
     }
     __syncthreads();
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.scl = chain ? static_cast<double *>(in.scl) : in.scl64;
         fp.n = in.n;
         fp.nc = in.n + in.k;
-        fp.ldt = chain ? in.ldt : in.n;
+        fp.ldt = chain ? in.ldt : in.ldt_tree;
         run_job<CMAX, double>(fp, jd, smraw);
       }
       if (bj.parent < 0) {
@@ -458,7 +464,11 @@ int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved
   const size_t extra = factor_smem_bytes(nc, 0, elem);
   if (per_cta <= extra) return 0;
   int rows = (int)((per_cta - extra) / (elem * (size_t)nc));
-  return rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
+  rows = rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
+  // FP32: the two half-warps of a warp read neighbouring columns; an odd multiple of 16
+  // words between columns puts them on disjoint halves of the 32 shared-memory banks
+  if (elem == 4 && rows >= 32 && (rows & 31) == 0) rows -= 16;
+  return rows;
 }
 
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {

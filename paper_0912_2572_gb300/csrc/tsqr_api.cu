@@ -187,6 +187,36 @@ static void plan_build(Plan &pl, int64_t chains_target) {
   }
 }
 
+// Splits every TTQRT tile into pieces of at most h rows of the child's triangle, so that
+// a tree node needs no more shared memory than a chain tile (the batched kernel runs
+// both in one launch). Reflector indices are renumbered tile by tile. Returns the piece
+// height (n when nothing is split).
+static int split_tree_tiles(Plan &pl, int h) {
+  if (h <= 0 || h >= pl.n) return pl.n;
+  const int pieces = (pl.n + h - 1) / h;
+  const int ph = (pl.n + pieces - 1) / pieces;
+  std::vector<TileDesc> tiles;
+  tiles.reserve(pl.tiles.size() * 2);
+  for (JobDesc &jd : pl.jobs) {
+    const int32_t b = (int32_t)tiles.size();
+    for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t) {
+      const TileDesc &td = pl.tiles[t];
+      if (td.kind != TTQRT) {
+        TileDesc c = td;
+        c.refl = (int64_t)tiles.size() * pl.n;
+        tiles.push_back(c);
+        continue;
+      }
+      for (int o = 0; o < pl.n; o += ph)
+        tiles.push_back({td.row0 + o, (int64_t)tiles.size() * pl.n, std::min(ph, pl.n - o), TTQRT, o, 0});
+    }
+    jd.tile_begin = b;
+    jd.tile_count = (int32_t)tiles.size() - b;
+  }
+  pl.tiles.swap(tiles);
+  return ph;
+}
+
 // Chooses the tile height and CTAs per SM of the factor kernel for nc columns: two
 // resident CTAs when the tile still holds at least n rows (one CTA's scalar phase is
 // then hidden behind the other's updates), otherwise one.
@@ -430,6 +460,7 @@ constexpr double kRefineTol = 1e-13;
 // refinement launches, and the stopping tolerance on the predicted remaining
 // ||dX||/||X|| (the last correction times rho / (1 - rho), rho the observed contraction).
 constexpr int64_t kRefineRows = 4096;
+constexpr size_t kBatchSmemSlack = 256;
 constexpr int32_t kRefineSteps = 10;
 constexpr double kBatchRefineTol = 1e-12;
 // Cost model of TSQR_AUTO: share of the FP64 peak reached by the factor kernel and by the
@@ -623,12 +654,15 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
                                        double *info) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  const DeviceInfo di = device_info(dev);
+  DeviceInfo di = device_info(dev);
+  // the persistent kernel has a few bytes of static shared memory, and allocations are
+  // rounded up: budget for both so that two CTAs per SM still fit where planned
+  di.reserved += kBatchSmemSlack;
   if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
   if (arity == 0) arity = 2;
   const int L = chain_tiles > 0 ? chain_tiles : 8;
   std::vector<Plan> plans(count);
-  std::vector<int32_t> prec(count);
+  std::vector<int32_t> prec(count), tree_rows(count);
   size_t smem = 0;
   int cmax = 1, cps_min = 2;
   bool any_refine = false;
@@ -648,8 +682,11 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     const int64_t G = std::max<int64_t>(1, (tiles + L / 2) / L);
     tsqr_status st = make_plan_on(di, plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
     if (st != TSQR_OK) return st;
+    // tree nodes (FP64) in pieces that fit the chains' CTAs per SM
+    const int node_rows = tree_rows[q] = split_tree_tiles(
+        plans[q], factor_max_rows(nc, plans[q].ctas_per_sm, di.smem_sm, di.reserved, di.optin, sizeof(double)));
     smem = std::max(smem, factor_smem_bytes(nc, plans[q].tile_h, elem));
-    smem = std::max(smem, factor_smem_bytes(nc, it.n, sizeof(double)));  // tree nodes
+    smem = std::max(smem, factor_smem_bytes(nc, node_rows, sizeof(double)));
     smem = std::max(smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
     while (16 * cmax < nc) cmax *= 2;
     cps_min = std::min(cps_min, plans[q].ctas_per_sm);
@@ -721,11 +758,15 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       bj.tile_count = jd.tile_count;
       bj.inst = q;
       bj.parent = -1;
-      bj.nchild = jd.tile_count + 1;
+      int32_t nchild = 1;
       const int32_t first = chain_of(jd.piv_row);
       jobs[gidx[q][holder[first]]].parent = gidx[q][j];
-      for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t)
+      for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t) {
+        if (pl.tiles[t].off != 0) continue;  // a later piece of the same child
         jobs[gidx[q][holder[chain_of(pl.tiles[t].row0)]]].parent = gidx[q][j];
+        ++nchild;
+      }
+      bj.nchild = nchild;
       holder[first] = (int32_t)j;
     }
   }
@@ -850,6 +891,7 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     bi.n = it.n;
     bi.k = pl.mixed ? 0 : it.k;
     bi.ldt = pl.tile_h;
+    bi.ldt_tree = tree_rows[q];
     bi.mixed = pl.mixed ? 1 : 0;
     if (pl.mixed) bi.B = nullptr;
     if (bi.k > 0)
@@ -861,18 +903,8 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
   CUDA_TRY(cudaMemcpyAsync(base + o_tiles, tiles.data(), sizeof(TileDesc) * (size_t)ntiles, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(base + o_cnt, 0, sizeof(int32_t) * ((size_t)njobs + 1), s));
   CUDA_TRY(cudaMemsetAsync(base + o_st, 0, sizeof(int32_t) * count, s));
-  BatchParams bp{};
-  bp.inst = (const BatchInst *)(base + o_inst);
-  bp.jobs = (const BatchJob *)(base + o_jobs);
-  bp.tiles = (const TileDesc *)(base + o_tiles);
-  bp.counters = (int32_t *)(base + o_cnt);
-  bp.queue = bp.counters + njobs;
-  bp.nchains = nchains;
-  const int grid = di.sms * cps_min;
-  {
-    ProfScope ps(TSQR_PROF_BATCH, s);
-    CUDA_TRY(launch_factor_batch(bp, cmax, grid, smem, s));
-  }
+  // every host-to-device copy of the call is issued before its first kernel: a copy
+  // from pageable memory may wait for the stream to drain
   if (!rinst.empty()) {
     int32_t *flags = (int32_t *)(base + o_rflags);  // counter, done per instance
     for (size_t r = 0; r < rinst.size(); ++r) {
@@ -894,6 +926,20 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       const std::vector<double> neg((size_t)kRefineSteps * rinst.size(), -1.0);  // staged before return
       CUDA_TRY(cudaMemcpyAsync(base + o_rhist, neg.data(), sizeof(double) * neg.size(), cudaMemcpyHostToDevice, s));
     }
+  }
+  BatchParams bp{};
+  bp.inst = (const BatchInst *)(base + o_inst);
+  bp.jobs = (const BatchJob *)(base + o_jobs);
+  bp.tiles = (const TileDesc *)(base + o_tiles);
+  bp.counters = (int32_t *)(base + o_cnt);
+  bp.queue = bp.counters + njobs;
+  bp.nchains = nchains;
+  const int grid = di.sms * cps_min;
+  {
+    ProfScope ps(TSQR_PROF_BATCH, s);
+    CUDA_TRY(launch_factor_batch(bp, cmax, grid, smem, s));
+  }
+  if (!rinst.empty()) {
     RefineParams rp{};
     rp.inst = (const RefineInst *)(base + o_rinst);
     rp.tasks = (const RefineTask *)(base + o_rtasks);

@@ -26,8 +26,10 @@ enum TileKind : int32_t { GEQRT = 0, TSQRT = 1, TTQRT = 2 };
 struct TileDesc {
   int64_t row0;   // first global row of the tile
   int64_t refl;   // index of reflector 0 of this tile in the tau/scale arrays
-  int32_t nrows;  // rows in the tile (TTQRT: n)
+  int32_t nrows;  // rows in the tile (TTQRT: n, or a piece of the child's triangle)
   int32_t kind;   // TileKind
+  int32_t off;    // TTQRT piece: the tile's row 0 is row `off` of the child's triangle
+  int32_t pad;
 };
 
 struct JobDesc {
@@ -41,8 +43,10 @@ struct LaunchDesc {
   int32_t job_count;
 };
 
-// Tail rows [lo, hi) of reflector j within a tile of `ht` rows.
-__host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int &hi) {
+// Tail rows [lo, hi) of reflector j within a tile of `ht` rows (empty when hi <= lo).
+// A TTQRT tile holds rows off..off+ht-1 of the child's triangle, whose column j is
+// nonzero on rows 0..j only.
+__host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int &hi, int off = 0) {
   if (kind == GEQRT) {
     lo = j + 1;
     hi = ht;
@@ -51,7 +55,9 @@ __host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int 
     hi = ht;
   } else {
     lo = 0;
-    hi = j + 1;
+    hi = j + 1 - off;
+    if (hi > ht) hi = ht;
+    if (hi < 0) hi = 0;
   }
 }
 
@@ -106,6 +112,7 @@ struct BatchInst {
   int64_t ldx;
   int32_t *status;  // device flag set to 4 when R is singular (solve only)
   int32_t n, k, ldt, mixed;
+  int32_t ldt_tree, pad;  // shared-memory rows of a tree-node tile (a piece of a triangle)
 };
 
 struct BatchJob {   // chain jobs first (queue order), then tree nodes
