@@ -251,21 +251,20 @@ __global__ void __launch_bounds__(kRThreads, 2) k_refine_batch(const RefineParam
   const RefineTask tk = p.tasks[blockIdx.x];
   const RefineInst in = p.inst[tk.inst];
   if (__ldcg(in.done) != 0) return;
-  const int tb = in.n <= 32 ? 1 : (in.n <= 64 ? 2 : 4);
+  // exact right-hand-side count and column-tile count: a padded slot would still issue
+  // its DFMA (a predicated-off lane occupies the FP64 pipe)
+  const int tb = (in.n + 31) / 32;
+#define TSQR_REFINE_CASE(K, T) \
+  case K * 8 + T: refine_go<K, T>(p, tk, in, smraw); return;
+#define TSQR_REFINE_K(K) \
+  TSQR_REFINE_CASE(K, 1) TSQR_REFINE_CASE(K, 2) TSQR_REFINE_CASE(K, 3) TSQR_REFINE_CASE(K, 4)
   switch (in.kb * 8 + tb) {
-    case 1 * 8 + 1: refine_go<1, 1>(p, tk, in, smraw); return;
-    case 1 * 8 + 2: refine_go<1, 2>(p, tk, in, smraw); return;
-    case 1 * 8 + 4: refine_go<1, 4>(p, tk, in, smraw); return;
-    case 2 * 8 + 1: refine_go<2, 1>(p, tk, in, smraw); return;
-    case 2 * 8 + 2: refine_go<2, 2>(p, tk, in, smraw); return;
-    case 2 * 8 + 4: refine_go<2, 4>(p, tk, in, smraw); return;
-    case 4 * 8 + 1: refine_go<4, 1>(p, tk, in, smraw); return;
-    case 4 * 8 + 2: refine_go<4, 2>(p, tk, in, smraw); return;
-    case 4 * 8 + 4: refine_go<4, 4>(p, tk, in, smraw); return;
-    case 8 * 8 + 1: refine_go<8, 1>(p, tk, in, smraw); return;
-    case 8 * 8 + 2: refine_go<8, 2>(p, tk, in, smraw); return;
-    default: refine_go<8, 4>(p, tk, in, smraw); return;
+    TSQR_REFINE_K(1) TSQR_REFINE_K(2) TSQR_REFINE_K(3) TSQR_REFINE_K(4)
+    TSQR_REFINE_K(5) TSQR_REFINE_K(6) TSQR_REFINE_K(7) TSQR_REFINE_K(8)
+    default: return;
   }
+#undef TSQR_REFINE_K
+#undef TSQR_REFINE_CASE
 }
 
 }  // namespace

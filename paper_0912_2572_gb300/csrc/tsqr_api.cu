@@ -463,12 +463,14 @@ constexpr int64_t kRefineRows = 4096;
 constexpr size_t kBatchSmemSlack = 256;
 constexpr int32_t kRefineSteps = 10;
 constexpr double kBatchRefineTol = 1e-12;
-// Cost model of TSQR_AUTO: share of the FP64 peak reached by the factor kernel and by the
-// refinement kernel, FP32 factor throughput over FP64, refinement steps assumed.
-constexpr double kFactorEff = 0.85;
-constexpr double kRefineEff = 0.8;
-constexpr double kFp32Ratio = 8.0;
-constexpr double kRefineStepsEst = 6.0;
+// Cost model of TSQR_AUTO, in TFLOP/s measured on GB300 batches of served requests:
+// the FP64 factor kernel (lower for n < 32, where the column steps are short), the FP32
+// factor kernel (rising with n up to its plateau), the refinement kernel, and the
+// refinement steps counted at full cost (the first step, from x = 0, costs half).
+constexpr double kFp64Factor = 0.76, kFp64FactorNarrow = 0.6;
+constexpr double kFp32FactorPerCol = 0.053, kFp32FactorMax = 3.3;
+constexpr double kRefineTflops = 0.75, kRefineTflopsNarrow = 0.6;
+constexpr double kRefineStepsEst = 2.6;
 
 // Mixed-precision least squares: FP32 chains (leaves and flat chains), FP64 tree on the
 // compact pivot blocks, then Bjorck augmented-system refinement with FP64 residuals
@@ -825,7 +827,7 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       RefineInst ri{};
       ri.n = it.n;
       ri.k = std::min(8, it.k - c0);
-      ri.kb = ri.k <= 1 ? 1 : (ri.k <= 2 ? 2 : (ri.k <= 4 ? 4 : 8));
+      ri.kb = ri.k;
       ri.nt = nt;
       ri.A = it.A;
       ri.lda = it.lda;
@@ -999,19 +1001,20 @@ tsqr_status tsqr::check_batch_item(const tsqr_batch_item &it, int32_t q) {
   return TSQR_OK;
 }
 
-// FP64 or mixed for a TSQR_AUTO item, by a cost model in units of FP64 flops per row of A:
-// FP64 factors [A | B] (2 (n + k)^2 flops, at the factor kernel's share of the FP64
-// peak); mixed factors A on the FP32 pipe (2 n^2 flops at kFp32Ratio times the FP64 rate)
-// and then runs kRefineStepsEst refinement steps of 4 n kb FP64 flops. R-only items, and
-// items with n + k too wide to fuse, follow the accuracy and shape constraints first.
+// FP64 or mixed for a TSQR_AUTO item by the time per row of A the cost model predicts:
+// FP64 factors [A | B] (2 (n + k)^2 flops); mixed factors A in FP32 (2 n^2 flops) and
+// then refines (4 n k FP64 flops per step). R-only items keep FP64 accuracy; items too
+// wide to fuse B take the mixed path.
 int32_t tsqr::resolve_batch_prec(const tsqr_batch_item &it) {
   if (it.prec != TSQR_AUTO) return it.prec;
   if (it.k == 0) return TSQR_FP64;
   if (it.n + it.k > 144) return TSQR_MIXED;
   const double n = it.n, k = it.k;
-  const double kb = it.k <= 1 ? 1 : (it.k <= 2 ? 2 : (it.k <= 4 ? 4 : (it.k <= 8 ? 8 : 8 * std::ceil(k / 8))));
-  const double fp64 = 2.0 * (n + k) * (n + k) / kFactorEff;
-  const double mixed = 2.0 * n * n / (kFp32Ratio * kFactorEff) + kRefineStepsEst * 4.0 * n * kb / kRefineEff;
+  const double f64 = n >= 32 ? kFp64Factor : kFp64FactorNarrow;
+  const double f32 = std::min(kFp32FactorMax, kFp32FactorPerCol * n);
+  const double fp64 = 2.0 * (n + k) * (n + k) / f64;
+  const double fr = n >= 32 ? kRefineTflops : kRefineTflopsNarrow;
+  const double mixed = 2.0 * n * n / f32 + kRefineStepsEst * 4.0 * n * k / fr;
   return mixed < fp64 ? TSQR_MIXED : TSQR_FP64;
 }
 

@@ -152,7 +152,7 @@ struct RefineInst {
   int32_t *done;       // 1 once the group has converged or R is singular
   int32_t *status;     // the item's status word (TSQR_ERR_SINGULAR)
   double *hist;        // ||dX||_F / ||X||_F per step
-  int32_t n, k, kb, nt;  // kb = k rounded up to 1, 2, 4 or 8; nt = tasks
+  int32_t n, k, kb, nt;  // kb = the kernel's register width for k (k itself); nt = tasks
 };
 
 struct RefineTask {
