@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=10000)
     p.add_argument("--no-serve", action="store_true", help="skip the served least-squares workload")
     p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
+    p.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                   help="only run N mixed batches of 32 served-mix requests (a small case for ncu)")
     return p.parse_args()
 
 
@@ -534,6 +536,17 @@ def bench_ours(args):
     if args.serve_only:
         if rank == 0:
             print(json.dumps({"served": bench_served(ts)}), flush=True)
+        return 0
+    if args.profile_batch:
+        pool = make_served_pool(32, 11)
+        items = [{"A": r["A"], "B": r["B"], "want_r": False, "prec": ts.MIXED} for r in pool]
+        for _ in range(args.profile_batch):
+            ts.batch_solve(items, chain_tiles=8)
+        torch.cuda.synchronize()
+        _, prof = ts.profile_collect(lambda: ts.batch_solve(items, chain_tiles=8))
+        rows = sum(r["m"] for r in pool)
+        print(json.dumps({"profile_batch": {"requests": len(pool), "rows": rows,
+                                            "phases_ms": {k: ms for k, ms in prof}}}), flush=True)
         return 0
 
     m, n = args.m, args.n

@@ -305,6 +305,232 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
   }
 }
 
+// ------------------------------------------------------ FP32 chains: register tiles
+// The FP32 chains of the mixed path keep their tile in registers. On the FP32 pipe the
+// shared-memory tile of the kernel above is bound by instruction issue (an address
+// computation and a shared-memory access per FMA) and a column step lasts a fraction of
+// a microsecond, so nothing on a step's critical path may go to L2. Here:
+//   * thread (hw, hl) holds columns hw + 16 t (t < CPT) of rows hl + 16 r (r < kF32Rpt)
+//     of a 128-row tile; a column step moves only the pivot column j (the reflector's
+//     tail) and the step's scalars through shared memory, and the Gram row and the
+//     rank-1 update are register FMAs over the columns still active;
+//   * the chain's R (its n pivot rows, n x nc) stays in shared memory for the whole chain:
+//     the leaf's first tile leaves it there, each triangle-on-tile step reads and
+//     rewrites its pivot row there, and R goes to global memory once, at the end;
+//   * the slot range of a step is the same for the two half-warps of a warp (their
+//     shuffles must match); a boundary slot is guarded per half-warp.
+template <int CPT, int T0>
+__device__ __forceinline__ void f32_gram(const float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j, int hw,
+                                         int hl, int nc, float *Pg) {
+  constexpr int NA = CPT - T0;
+  constexpr int C = pow2ceil(NA);
+  float acc[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) acc[t] = 0.f;
+#pragma unroll
+  for (int t = 0; t < NA; ++t)
+#pragma unroll
+    for (int r = 0; r < kF32Rpt; ++r) acc[t] = fmaf(x[r], v[T0 + t][r], acc[t]);
+  int idx;
+  const float s = treduce16<C, float>(acc, hl, idx);
+  const int c = hw + 16 * (T0 + idx);
+  if ((hl & (16 / C - 1)) == 0 && idx < NA && c >= j && c < nc) Pg[c] = s;
+}
+
+template <int CPT, int T0>
+__device__ __forceinline__ void f32_update(float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j, int hw,
+                                           int nc, const float *CF) {
+#pragma unroll
+  for (int t = T0; t < CPT; ++t) {
+    const int c = hw + 16 * t;
+    if (c <= j || c >= nc) continue;  // the first slot may hold column j or an earlier one
+    const float cf = CF[c];
+#pragma unroll
+    for (int r = 0; r < kF32Rpt; ++r) v[t][r] = fmaf(-cf, x[r], v[t][r]);
+  }
+}
+
+template <int CPT>
+__device__ __forceinline__ void f32_gram_dispatch(const float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j,
+                                                  int t0, int hw, int hl, int nc, float *Pg) {
+  switch (t0) {
+    case 0: f32_gram<CPT, 0>(v, x, j, hw, hl, nc, Pg); return;
+#define TSQR_F32_GRAM(T) \
+    case T: if (CPT > T) f32_gram<CPT, (CPT > T ? T : 0)>(v, x, j, hw, hl, nc, Pg); return;
+    TSQR_F32_GRAM(1) TSQR_F32_GRAM(2) TSQR_F32_GRAM(3) TSQR_F32_GRAM(4) TSQR_F32_GRAM(5) TSQR_F32_GRAM(6)
+    TSQR_F32_GRAM(7)
+#undef TSQR_F32_GRAM
+    default: return;
+  }
+}
+
+template <int CPT>
+__device__ __forceinline__ void f32_update_dispatch(float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j,
+                                                    int t0, int hw, int nc, const float *CF) {
+  switch (t0) {
+    case 0: f32_update<CPT, 0>(v, x, j, hw, nc, CF); return;
+#define TSQR_F32_UPD(T) \
+    case T: if (CPT > T) f32_update<CPT, (CPT > T ? T : 0)>(v, x, j, hw, nc, CF); return;
+    TSQR_F32_UPD(1) TSQR_F32_UPD(2) TSQR_F32_UPD(3) TSQR_F32_UPD(4) TSQR_F32_UPD(5) TSQR_F32_UPD(6)
+    TSQR_F32_UPD(7)
+#undef TSQR_F32_UPD
+    default: return;
+  }
+}
+
+// One chain job (a leaf's GEQRT tile, then TSQRT tiles; at most 16 * CPT columns) with
+// register tiles. Shared memory: the pivot column (kF32TileRows), the Gram row (ncp),
+// two pivot-row buffers for the leaf tile (2 ncp) and the chain's R (n rows of ncp + 1).
+template <int CPT>
+__device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, const JobDesc job, unsigned char *smraw) {
+  float *sm = reinterpret_cast<float *>(smraw);
+  const int n = p.n, nc = p.nc;
+  const int ncp = (nc + 7) & ~7;
+  float *xcol = sm;
+  float *PC = xcol + kF32TileRows;
+  float *PVb = PC + ncp;
+  const int ldr = ncp + 1;    // odd: the end-of-chain column walk is conflict-free
+  float *Rs = PVb + 2 * ncp;  // R(i, c) at Rs[i * ldr + c]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hw = tid >> 4, hl = tid & 15;
+  const int hw_hi = 2 * warp + 1;  // the larger column offset of the warp's half-warps
+  const int64_t pr = job.piv_row;
+  float v[CPT][kF32Rpt];
+
+  for (int tt = 0; tt < job.tile_count; ++tt) {
+    const TileDesc td = p.tiles[job.tile_begin + tt];
+    const int ht = td.nrows;
+    const int64_t r0 = td.row0;
+    const bool ge = (td.kind == GEQRT);
+    // load the tile (A is FP64, rounded here); rows past ht and columns past nc are 0
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = hw + 16 * t;
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        const int i = hl + 16 * r;
+        float val = 0.f;
+        if (c < nc && i < ht)
+          val = (c < n) ? (float)__ldg(p.A + r0 + i + (int64_t)c * p.lda)
+                        : __ldcg(p.B + r0 + i + (int64_t)(c - n) * p.ldb);
+        v[t][r] = val;
+      }
+    }
+    __syncthreads();
+
+    for (int j = 0; j < n; ++j) {
+      const int tj = j >> 4, jl = j & 15;
+      float *PV = ge ? PVb + (j & 1) * ncp : Rs + j * ldr;
+      // (A) publish the pivot column (its owner half-warp) and, for the leaf tile, the
+      //     pivot row (its owner lane in every half-warp)
+      if (hw == jl) {
+#pragma unroll
+        for (int t = 0; t < CPT; ++t)
+          if (t == tj)
+#pragma unroll
+            for (int r = 0; r < kF32Rpt; ++r) xcol[hl + 16 * r] = v[t][r];
+      }
+      if (ge && hl == jl) {
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r)
+          if (r == tj)
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) {
+              const int c = hw + 16 * t;
+              if (c >= j && c < nc) PV[c] = v[t][r];
+            }
+      }
+      __syncthreads();
+      // (B) the tail of column j on this lane's rows, then the Gram row
+      float x[kF32Rpt];
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        const int i = hl + 16 * r;
+        x[r] = (ge && i <= j) ? 0.f : xcol[i];
+      }
+      {
+        const int d = j - hw_hi;
+        f32_gram_dispatch<CPT>(v, x, j, d <= 0 ? 0 : (d + 15) >> 4, hw, hl, nc, PC);
+      }
+      __syncthreads();
+      // (C) warp 0: the reflector's scalars, the update coefficients and the new pivot row
+      if (warp == 0) {
+        const Refl<float> rf = reflector<float>(PV[j], PC[j]);
+        for (int c = j + 1 + lane; c < nc; c += 32) {
+          const float pk = PV[c];
+          const float w = fmaf(rf.scale, PC[c], pk);
+          PC[c] = rf.ts * w;
+          PV[c] = fmaf(-rf.tau, w, pk);
+        }
+        if (lane == 0) {
+          PV[j] = rf.beta;
+          p.tau[td.refl + j] = rf.tau;
+          p.scl[td.refl + j] = rf.scale;
+        }
+      }
+      __syncthreads();
+      // (D) the rank-1 update; on the leaf tile the owner lane of row j takes the new row
+      {
+        const int d = j + 1 - hw_hi;
+        f32_update_dispatch<CPT>(v, x, j, d <= 0 ? 0 : (d + 15) >> 4, hw, nc, PC);
+      }
+      if (ge && hl == jl) {
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r)
+          if (r == tj)
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) {
+              const int c = hw + 16 * t;
+              if (c >= j && c < nc) v[t][r] = PV[c];
+            }
+      }
+    }
+    __syncthreads();
+    // the leaf tile's R (rows < n, upper part; right-hand-side columns in full) becomes
+    // the chain's R in shared memory
+    if (ge) {
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int c = hw + 16 * t;
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r) {
+          const int i = hl + 16 * r;
+          if (c < nc && i < n && (i <= c || c >= n)) Rs[i * ldr + c] = v[t][r];
+        }
+      }
+    }
+    // write the tile back: the leaf tile holds R above and reflectors below the diagonal
+    // (R is rewritten from shared memory at the end), a TSQRT tile dense reflector tails
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = hw + 16 * t;
+      if (c >= nc) continue;
+      float *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        const int i = hl + 16 * r;
+        if (i < ht) dst[i] = v[t][r];
+      }
+    }
+    __syncthreads();
+  }
+  // the chain's R to its pivot rows in global memory
+  for (int e = tid; e < n * nc; e += kThreads) {
+    const int i = e % n, c = e / n;
+    if (i <= c || c >= n) {
+      float *dst = (c < n) ? p.V + pr + i + (int64_t)c * p.ldv : p.B + pr + i + (int64_t)(c - n) * p.ldb;
+      *dst = Rs[i * ldr + c];
+    }
+  }
+  __syncthreads();
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads, 2) k_factor_f32r(const FactorParamsT<float> p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  run_job_f32r<CPT>(p, p.jobs[p.job0 + blockIdx.x], smraw);
+}
+
 template <int CMAX, typename R>
 __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -385,7 +611,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.n = in.n;
         fp.nc = in.n;
         fp.ldt = in.ldt;
-        run_job<CMAX, float>(fp, jd, smraw);
+        switch (in.n <= 16 ? 1 : (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8))) {
+          case 1: run_job_f32r<1>(fp, jd, smraw); break;
+          case 2: if (CMAX >= 2) run_job_f32r<(CMAX >= 2 ? 2 : 1)>(fp, jd, smraw); break;
+          case 4: if (CMAX >= 4) run_job_f32r<(CMAX >= 4 ? 4 : 1)>(fp, jd, smraw); break;
+          default: if (CMAX >= 8) run_job_f32r<(CMAX >= 8 ? 8 : 1)>(fp, jd, smraw); break;
+        }
         // hand the chain's triangle to the FP64 tree storage
         const float *Vs = static_cast<const float *>(in.V) + bj.piv_row;
         for (int e = threadIdx.x; e < in.n * in.n; e += blockDim.x) {
@@ -451,6 +682,7 @@ cudaError_t launch_factor_any(const FactorParamsT<R> &p, int njobs, cudaStream_t
 
 size_t factor_smem_bytes(int nc, int ldt, size_t elem) {
   const size_t ncp = (size_t)((nc + 7) & ~7);
+  if (elem == sizeof(float)) return sizeof(float) * ((size_t)kF32TileRows + 3 * ncp + (size_t)nc * (ncp + 1));
   return elem * ((size_t)nc * (size_t)ldt + 2 * ncp);
 }
 
@@ -476,7 +708,18 @@ cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_
 }
 
 cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s) {
-  return launch_factor_any(p, njobs, s);
+  if (njobs <= 0) return cudaSuccess;
+  const size_t bytes = factor_smem_bytes(p.nc, 0, sizeof(float));
+  auto go = [&](auto kernel) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    kernel<<<njobs, kThreads, bytes, s>>>(p);
+    return cudaGetLastError();
+  };
+  if (p.nc <= 16) return go(k_factor_f32r<1>);
+  if (p.nc <= 32) return go(k_factor_f32r<2>);
+  if (p.nc <= 64) return go(k_factor_f32r<4>);
+  return go(k_factor_f32r<8>);
 }
 
 cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s) {

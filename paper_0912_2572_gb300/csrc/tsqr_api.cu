@@ -222,6 +222,12 @@ static int split_tree_tiles(Plan &pl, int h) {
 // then hidden behind the other's updates), otherwise one.
 static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &tile_h, int &cps,
                          size_t elem = sizeof(double)) {
+  if (elem == sizeof(float)) {  // register-tile FP32 chains: fixed 128-row tiles
+    if (nc > 128) return false;
+    tile_h = std::min(kF32TileRows, std::max(leaf_h, n));
+    cps = 2;
+    return true;
+  }
   for (int c = 2; c >= 1; --c) {
     int rows = factor_max_rows(nc, c, di.smem_sm, di.reserved, di.optin, elem);
     rows = std::min(rows, 512);  // the apply kernels stage at most 512 rows per tile
@@ -245,6 +251,8 @@ static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n
   pl.mixed = mixed;
   if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double)))
     return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
+  // four waves of chains: the apply kernels run one warp per chain, so fewer chains would
+  // starve them (the batched path, which applies nothing, sets its own count)
   const int64_t chains = chains_override > 0 ? chains_override : (int64_t)di.sms * pl.ctas_per_sm * 4;
   try {
     plan_build(pl, chains);
@@ -461,6 +469,7 @@ constexpr double kRefineTol = 1e-13;
 // ||dX||/||X|| (the last correction times rho / (1 - rho), rho the observed contraction).
 constexpr int64_t kRefineRows = 4096;
 constexpr size_t kBatchSmemSlack = 256;
+constexpr int kMixedChainFactor = 4;
 constexpr int32_t kRefineSteps = 10;
 constexpr double kBatchRefineTol = 1e-12;
 // Cost model of TSQR_AUTO, in TFLOP/s measured on GB300 batches of served requests:
@@ -681,7 +690,9 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     if (!choose_tiles(di, it.n, nc, 1 << 20, th, cps, elem))
       return fail(TSQR_ERR_UNSUPPORTED, "item %d: no tile fits shared memory", q);
     const int64_t tiles = (it.m + th - 1) / th;
-    const int64_t G = std::max<int64_t>(1, (tiles + L / 2) / L);
+    // mixed items: FP32 chains kMixedChainFactor times longer (fewer FP64 tree combines)
+    const int64_t Lq = mixed ? (int64_t)L * kMixedChainFactor : L;
+    const int64_t G = std::max<int64_t>(1, (tiles + Lq / 2) / Lq);
     tsqr_status st = make_plan_on(di, plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
     if (st != TSQR_OK) return st;
     // tree nodes (FP64) in pieces that fit the chains' CTAs per SM

@@ -83,6 +83,12 @@ struct FactorParamsT {
 };
 using FactorParams = FactorParamsT<double>;
 
+// FP32 chains keep their tile in registers: kF32Rpt rows per lane, 16 lanes per column.
+constexpr int kF32Rpt = 8;
+constexpr int kF32TileRows = 16 * kF32Rpt;
+
+// Shared memory of a factor job: the tile plus its step buffers (FP64), or only the
+// step buffers of a register-tile FP32 chain (elem = 4).
 size_t factor_smem_bytes(int nc, int ldt, size_t elem = sizeof(double));
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s);
 cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s);

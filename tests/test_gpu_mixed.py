@@ -25,6 +25,8 @@ def rel(a, b):
     (5000, 8, 10, 2, 128, 2, True),
     (3000, 100, 2, 4, 200, 2, True),
     (777, 5, 1, 4, 64, 0, False),
+    (60_000, 128, 3, 4, 128, 2, True),
+    (9000, 120, 9, 3, 256, 4, True),
 ])
 def test_mixed_lstsq_matches_fp64_oracle(cuda_lib, m, n, k, dec, h, arity, two):
     import paper_0912_2572_gb300 as ts
