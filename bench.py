@@ -276,6 +276,22 @@ def bench_batched(ts, count):
     tune = {f"L{L}_a{ar}": run(sample, L, ar) for L, ar in cands}
     L_best, ar_best = min(cands, key=lambda c: tune[f"L{c[0]}_a{c[1]}"])
     t_batch = run(items, L_best, ar_best, reps=2)
+    # the same batch planned once and replayed as a CUDA graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = ts.BatchPlan(items, chain_tiles=L_best, arity=ar_best)
+    t_plan = time.perf_counter() - t0
+    plan.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    t_replay = e0.elapsed_time(e1) / 3
+    plan_status, _ = plan.results()
+    plan.close()
     # one launch per instance and the plain API, on the first 500 instances
     few = items[:min(500, count)]
     torch.cuda.synchronize()
@@ -296,6 +312,10 @@ def bench_batched(ts, count):
             "autotune_ms_on_1000": tune, "chain_tiles": L_best, "arity": ar_best,
             "batched_ms": t_batch, "batched_instances_per_s": count / (t_batch * 1e-3),
             "batched_gflops": flops / (t_batch * 1e-3) / 1e9,
+            "plan_create_s": t_plan, "graph_replay_ms": t_replay,
+            "graph_replay_instances_per_s": count / (t_replay * 1e-3),
+            "graph_replay_gflops": flops / (t_replay * 1e-3) / 1e9,
+            "graph_replay_failed": sum(1 for x in plan_status if x != 0),
             "one_launch_per_instance_instances_per_s": 1.0 / t_one,
             "plain_tsqr_factor_instances_per_s": 1.0 / t_plain,
             "speedup_vs_one_launch_per_instance": t_one * count / (t_batch * 1e-3),

@@ -247,6 +247,32 @@ tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_
                              int32_t arity, void *stream, int32_t *status, double *info);
 
 /*
+ * Reusable batch plans: a batch whose items keep their shapes and buffers (an iterative
+ * method factoring new data in the same arrays, a benchmark loop) is planned once and
+ * replayed as a CUDA graph, so a run costs no host planning and no table uploads.
+ *
+ * tsqr_batch_plan_create(items, count, chain_tiles, arity, &plan)
+ *   Validates the items as tsqr_batch_solve does, plans them, allocates the plan's device
+ *   workspace (cudaMalloc, synchronous) and captures one run as a CUDA graph. The item
+ *   structs are copied; the device buffers they point to must stay valid while the plan
+ *   exists. Errors: TSQR_ERR_ARG, TSQR_ERR_OOM, TSQR_ERR_UNSUPPORTED, TSQR_ERR_CUDA.
+ * tsqr_batch_plan_run(plan, stream)
+ *   Enqueues one run on stream: reads every item's A (and B) as they are when the run
+ *   executes and writes R and X, exactly as tsqr_batch_solve with the same chain_tiles
+ *   and arity. Runs of one plan must not overlap (the workspace is the plan's).
+ * tsqr_batch_plan_results(plan, status, info)
+ *   Waits for the last run and fills status (count int32) and info (2 * count doubles),
+ *   as tsqr_batch_solve does; either may be NULL. TSQR_ERR_ARG before the first run.
+ * tsqr_batch_plan_destroy(plan)  waits for the last run and frees the plan.
+ */
+typedef struct tsqr_batch_plan tsqr_batch_plan;
+tsqr_status tsqr_batch_plan_create(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                                   int32_t arity, tsqr_batch_plan **plan);
+tsqr_status tsqr_batch_plan_run(tsqr_batch_plan *plan, void *stream);
+tsqr_status tsqr_batch_plan_results(tsqr_batch_plan *plan, int32_t *status, double *info);
+tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
+
+/*
  * Continuous-batching server (the paper has no counterpart; it serves many independent
  * least-squares requests with the batched kernel above). A worker thread owned by the
  * server keeps up to `streams` batches in flight on the current device; whenever a

@@ -212,6 +212,50 @@ def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status
     return ret[0] if len(ret) == 1 else tuple(ret)
 
 
+class BatchPlan:
+    """A batch planned once and replayed as a CUDA graph (tsqr_batch_plan_*).
+
+    items: as for batch_solve. The plan keeps the tensors alive; overwrite the A and B
+    tensors in place between runs to solve new data. ``outputs`` is the list of (R, X).
+    """
+
+    def __init__(self, items, chain_tiles: int = 0, arity: int = 0):
+        self._lib = _lib.load()
+        arr = (_lib.BatchItem * max(1, len(items)))()
+        self._keep = []
+        self.outputs = []
+        for q, it in enumerate(items):
+            kp, out = _fill_item(arr[q], it)
+            self._keep += kp
+            self.outputs.append(out)
+        self._n = len(items)
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.tsqr_batch_plan_create(arr, len(items), chain_tiles, arity, ctypes.byref(self._h)),
+                   "tsqr_batch_plan_create")
+
+    def run(self, stream=None):
+        _lib.check(self._lib.tsqr_batch_plan_run(self._h, _stream(stream)), "tsqr_batch_plan_run")
+        return self.outputs
+
+    def results(self):
+        """(status list, [(refinement steps, last ||dX||/||X||)]) of the last run (waits for it)."""
+        st = (ctypes.c_int32 * self._n)()
+        inf = (ctypes.c_double * (2 * self._n))()
+        _lib.check(self._lib.tsqr_batch_plan_results(self._h, st, inf), "tsqr_batch_plan_results")
+        return [st[q] for q in range(self._n)], [(int(inf[2 * q]), inf[2 * q + 1]) for q in range(self._n)]
+
+    def close(self):
+        if self._h:
+            _lib.check(self._lib.tsqr_batch_plan_destroy(self._h), "tsqr_batch_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Server:
     """Continuous-batching least-squares server on the current CUDA device.
 

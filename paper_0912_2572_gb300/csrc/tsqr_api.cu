@@ -101,7 +101,7 @@ struct ProfScope {
   ProfRec r{};
   ProfScope(int32_t kind, cudaStream_t st) : s(st) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || kind < 0) return;  // kind < 0: never recorded (graph capture)
     r.kind = kind;
     if (cudaEventCreate(&r.a) != cudaSuccess) return;
     if (cudaEventCreate(&r.b) != cudaSuccess) {
@@ -660,27 +660,59 @@ static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t ld
 }
 
 // ---------------------------------------------------------------- batched solve
-tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
-                                       int32_t arity, cudaStream_t s, int32_t *status, int32_t *status_async,
-                                       double *info) {
+namespace {
+
+// Everything the batched path plans on the host for one set of items: the per-item
+// plans, the merged job and tile tables, the refinement tables, and the layout of the
+// one device block that holds workspaces and tables.
+struct BatchBuild {
+  int32_t count = 0;
+  std::vector<tsqr_batch_item> items;
+  std::vector<Plan> plans;
+  std::vector<int32_t> prec, tree_rows;
+  size_t smem = 0;
+  int cmax = 1, grid = 0;
+  int32_t nchains = 0, njobs = 0;
+  int64_t ntiles = 0;
+  std::vector<BatchJob> jobs;
+  std::vector<TileDesc> tiles;
+  std::vector<int64_t> root;  // where each item's R lands in its tree storage
+  struct Off {
+    size_t V, B, tau, scl, V64, tau64, scl64;
+  };
+  std::vector<Off> offs;
+  size_t o_inst = 0, o_jobs = 0, o_tiles = 0, o_cnt = 0, o_st = 0;
+  size_t o_rinst = 0, o_rtasks = 0, o_rflags = 0, o_rhist = 0, bytes = 0;
+  std::vector<int32_t> ritem;  // item of each refinement instance
+  std::vector<size_t> rP;      // its partials
+  std::vector<BatchInst> inst;
+  std::vector<RefineInst> rinst;
+  std::vector<RefineTask> rtasks;
+  size_t rsmem = 0;
+};
+
+tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                        BatchBuild &b) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
   // the persistent kernel has a few bytes of static shared memory, and allocations are
   // rounded up: budget for both so that two CTAs per SM still fit where planned
   di.reserved += kBatchSmemSlack;
-  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
   if (arity == 0) arity = 2;
   const int L = chain_tiles > 0 ? chain_tiles : 8;
-  std::vector<Plan> plans(count);
-  std::vector<int32_t> prec(count), tree_rows(count);
-  size_t smem = 0;
-  int cmax = 1, cps_min = 2;
+  b.count = count;
+  b.items.assign(items, items + count);
+  b.plans.resize(count);
+  b.prec.resize(count);
+  b.tree_rows.resize(count);
+  int cps_min = 2;
   bool any_refine = false;
   for (int32_t q = 0; q < count; ++q) {
     const tsqr_batch_item &it = items[q];
-    prec[q] = resolve_batch_prec(it);
-    const bool mixed = prec[q] == TSQR_MIXED;
+    b.prec[q] = resolve_batch_prec(it);
+    const bool mixed = b.prec[q] == TSQR_MIXED;
     any_refine = any_refine || (mixed && it.k > 0);
     // FP64 items fuse Q^T B into the factorization; mixed items factor A alone and
     // solve by refinement afterwards
@@ -693,29 +725,29 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     // mixed items: FP32 chains kMixedChainFactor times longer (fewer FP64 tree combines)
     const int64_t Lq = mixed ? (int64_t)L * kMixedChainFactor : L;
     const int64_t G = std::max<int64_t>(1, (tiles + Lq / 2) / Lq);
-    tsqr_status st = make_plan_on(di, plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
+    tsqr_status st = make_plan_on(di, b.plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
     if (st != TSQR_OK) return st;
     // tree nodes (FP64) in pieces that fit the chains' CTAs per SM
-    const int node_rows = tree_rows[q] = split_tree_tiles(
-        plans[q], factor_max_rows(nc, plans[q].ctas_per_sm, di.smem_sm, di.reserved, di.optin, sizeof(double)));
-    smem = std::max(smem, factor_smem_bytes(nc, plans[q].tile_h, elem));
-    smem = std::max(smem, factor_smem_bytes(nc, node_rows, sizeof(double)));
-    smem = std::max(smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
-    while (16 * cmax < nc) cmax *= 2;
-    cps_min = std::min(cps_min, plans[q].ctas_per_sm);
+    const int node_rows = b.tree_rows[q] = split_tree_tiles(
+        b.plans[q], factor_max_rows(nc, b.plans[q].ctas_per_sm, di.smem_sm, di.reserved, di.optin, sizeof(double)));
+    b.smem = std::max(b.smem, factor_smem_bytes(nc, b.plans[q].tile_h, elem));
+    b.smem = std::max(b.smem, factor_smem_bytes(nc, node_rows, sizeof(double)));
+    b.smem = std::max(b.smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
+    while (16 * b.cmax < nc) b.cmax *= 2;
+    cps_min = std::min(cps_min, b.plans[q].ctas_per_sm);
   }
-  // device-side job arrays: chains of every item (largest first), then tree nodes
+  b.grid = di.sms * cps_min;
+  // merged job table: chains of every item (largest first), then tree nodes
   struct Chain {
     double cost;
     int32_t item, job;
   };
   std::vector<Chain> chains;
-  std::vector<int64_t> tile_base(count), job_base(count);
-  int64_t ntiles = 0;
+  std::vector<int64_t> tile_base(count);
   for (int32_t q = 0; q < count; ++q) {
-    const Plan &pl = plans[q];
-    tile_base[q] = ntiles;
-    ntiles += (int64_t)pl.tiles.size();
+    const Plan &pl = b.plans[q];
+    tile_base[q] = b.ntiles;
+    b.ntiles += (int64_t)pl.tiles.size();
     for (int32_t c = 0; c < pl.launches[0].job_count; ++c) {
       const JobDesc &jd = pl.jobs[c];
       double rows = 0;
@@ -724,35 +756,34 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       chains.push_back({rows * w, q, c});
     }
   }
-  std::sort(chains.begin(), chains.end(), [](const Chain &a, const Chain &b) { return a.cost > b.cost; });
-  const int32_t nchains = (int32_t)chains.size();
+  std::sort(chains.begin(), chains.end(), [](const Chain &x, const Chain &y) { return x.cost > y.cost; });
+  b.nchains = (int32_t)chains.size();
   std::vector<std::vector<int32_t>> gidx(count);  // global job index of each plan job
-  for (int32_t q = 0; q < count; ++q) gidx[q].assign(plans[q].jobs.size(), -1);
-  for (int32_t c = 0; c < nchains; ++c) gidx[chains[c].item][chains[c].job] = c;
-  int32_t next = nchains;
+  for (int32_t q = 0; q < count; ++q) gidx[q].assign(b.plans[q].jobs.size(), -1);
+  for (int32_t c = 0; c < b.nchains; ++c) gidx[chains[c].item][chains[c].job] = c;
+  int32_t next = b.nchains;
   for (int32_t q = 0; q < count; ++q)
-    for (size_t j = plans[q].launches[0].job_count; j < plans[q].jobs.size(); ++j) gidx[q][j] = next++;
-  const int32_t njobs = next;
-  std::vector<BatchJob> jobs(njobs);
-  std::vector<TileDesc> tiles((size_t)ntiles);
+    for (size_t j = b.plans[q].launches[0].job_count; j < b.plans[q].jobs.size(); ++j) gidx[q][j] = next++;
+  b.njobs = next;
+  b.jobs.resize(b.njobs);
+  b.tiles.resize((size_t)b.ntiles);
   for (int32_t q = 0; q < count; ++q) {
-    const Plan &pl = plans[q];
-    for (size_t t = 0; t < pl.tiles.size(); ++t) tiles[tile_base[q] + t] = pl.tiles[t];
+    const Plan &pl = b.plans[q];
+    std::copy(pl.tiles.begin(), pl.tiles.end(), b.tiles.begin() + tile_base[q]);
     const int32_t G = pl.launches[0].job_count;
     // parents: follow which job currently holds each pivot block, level by level
     std::vector<int32_t> holder(G);  // by chain index
-    std::vector<std::pair<int64_t, int32_t>> rowkey;  // (tree-storage row, chain index)
+    std::vector<std::pair<int64_t, int32_t>> rowkey(G);  // (tree-storage row, chain index)
     for (int32_t c = 0; c < G; ++c) {
       holder[c] = c;
-      rowkey.push_back({pl.mixed ? (int64_t)c * pl.n : pl.jobs[c].piv_row, c});
+      rowkey[c] = {pl.mixed ? (int64_t)c * pl.n : pl.jobs[c].piv_row, c};
     }
     std::sort(rowkey.begin(), rowkey.end());
     auto chain_of = [&](int64_t row) {
-      auto it2 = std::lower_bound(rowkey.begin(), rowkey.end(), std::make_pair(row, (int32_t)-1));
-      return it2->second;
+      return std::lower_bound(rowkey.begin(), rowkey.end(), std::make_pair(row, (int32_t)-1))->second;
     };
     for (int32_t c = 0; c < G; ++c) {
-      BatchJob &bj = jobs[gidx[q][c]];
+      BatchJob &bj = b.jobs[gidx[q][c]];
       const JobDesc &jd = pl.jobs[c];
       bj.piv_row = jd.piv_row;
       bj.row64 = pl.mixed ? (int64_t)c * pl.n : jd.piv_row;
@@ -764,7 +795,7 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     }
     for (size_t j = G; j < pl.jobs.size(); ++j) {
       const JobDesc &jd = pl.jobs[j];
-      BatchJob &bj = jobs[gidx[q][j]];
+      BatchJob &bj = b.jobs[gidx[q][j]];
       bj.piv_row = jd.piv_row;
       bj.row64 = jd.piv_row;
       bj.tile_begin = (int32_t)(tile_base[q] + jd.tile_begin);
@@ -773,66 +804,57 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       bj.parent = -1;
       int32_t nchild = 1;
       const int32_t first = chain_of(jd.piv_row);
-      jobs[gidx[q][holder[first]]].parent = gidx[q][j];
+      b.jobs[gidx[q][holder[first]]].parent = gidx[q][j];
       for (int32_t t = jd.tile_begin; t < jd.tile_begin + jd.tile_count; ++t) {
         if (pl.tiles[t].off != 0) continue;  // a later piece of the same child
-        jobs[gidx[q][holder[chain_of(pl.tiles[t].row0)]]].parent = gidx[q][j];
+        b.jobs[gidx[q][holder[chain_of(pl.tiles[t].row0)]]].parent = gidx[q][j];
         ++nchild;
       }
       bj.nchild = nchild;
       holder[first] = (int32_t)j;
     }
   }
-  // one pool block: per-item workspaces, then the device copies of the arrays
-  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  b.root.assign(count, -1);
+  for (int32_t j = 0; j < b.njobs; ++j)
+    if (b.jobs[j].parent < 0) b.root[b.jobs[j].inst] = b.jobs[j].row64;
+  // device block: per-item workspaces, then the tables
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t off = 0;
-  auto take = [&](size_t b) {
+  auto take = [&](size_t x) {
     const size_t o = off;
-    off += up(b);
+    off += up(x);
     return o;
   };
-  struct Off {
-    size_t V, B, tau, scl, V64, tau64, scl64;
-  };
-  std::vector<Off> offs(count);
+  b.offs.resize(count);
   for (int32_t q = 0; q < count; ++q) {
     const tsqr_batch_item &it = items[q];
-    const Plan &pl = plans[q];
+    const Plan &pl = b.plans[q];
     const size_t elem = pl.mixed ? sizeof(float) : sizeof(double);
     const size_t nrefl = pl.tiles.size() * (size_t)it.n;
-    offs[q].V = take(elem * (size_t)it.m * it.n);
-    offs[q].B = (!pl.mixed && it.k > 0) ? take(sizeof(double) * (size_t)it.m * it.k) : 0;
-    offs[q].tau = take(elem * nrefl);
-    offs[q].scl = take(elem * nrefl);
+    BatchBuild::Off &o = b.offs[q];
+    o = {};
+    o.V = take(elem * (size_t)it.m * it.n);
+    o.B = (!pl.mixed && it.k > 0) ? take(sizeof(double) * (size_t)it.m * it.k) : 0;
+    o.tau = take(elem * nrefl);
+    o.scl = take(elem * nrefl);
     if (pl.mixed) {
       const int64_t Gn = (int64_t)pl.launches[0].job_count * it.n;
-      offs[q].V64 = take(sizeof(double) * (size_t)Gn * it.n);
-      offs[q].tau64 = take(sizeof(double) * nrefl);
-      offs[q].scl64 = take(sizeof(double) * nrefl);
+      o.V64 = take(sizeof(double) * (size_t)Gn * it.n);
+      o.tau64 = take(sizeof(double) * nrefl);
+      o.scl64 = take(sizeof(double) * nrefl);
     }
   }
-  const size_t o_inst = take(sizeof(BatchInst) * count);
-  const size_t o_jobs = take(sizeof(BatchJob) * njobs);
-  const size_t o_tiles = take(sizeof(TileDesc) * (size_t)ntiles);
-  const size_t o_cnt = take(sizeof(int32_t) * ((size_t)njobs + 1));
-  const size_t o_st = take(sizeof(int32_t) * count);
+  b.o_inst = take(sizeof(BatchInst) * count);
+  b.o_jobs = take(sizeof(BatchJob) * b.njobs);
+  b.o_tiles = take(sizeof(TileDesc) * (size_t)b.ntiles);
+  b.o_cnt = take(sizeof(int32_t) * ((size_t)b.njobs + 1));
+  b.o_st = take(sizeof(int32_t) * count);
   // refinement of mixed least-squares items: one instance per group of <= 8 right-hand
   // sides, tasks of kRefineRows rows
-  std::vector<int64_t> root(count, -1);  // where each item's R lands in its tree storage
-  for (int32_t j = 0; j < njobs; ++j)
-    if (jobs[j].parent < 0) root[jobs[j].inst] = jobs[j].row64;
-  struct RefOff {
-    int32_t item;
-    size_t P;
-  };
-  std::vector<RefOff> roffs;
-  std::vector<RefineInst> rinst;
-  std::vector<RefineTask> rtasks;
-  size_t rsmem = 0, o_rinst = 0, o_rtasks = 0, o_rflags = 0;
   for (int32_t q = 0; q < count && any_refine; ++q) {
     const tsqr_batch_item &it = items[q];
-    if (prec[q] != TSQR_MIXED || it.k == 0) continue;
-    if (root[q] < 0) return fail(TSQR_ERR_CUDA, "item %d: the plan has no root job", q);
+    if (b.prec[q] != TSQR_MIXED || it.k == 0) continue;
+    if (b.root[q] < 0) return fail(TSQR_ERR_CUDA, "item %d: the plan has no root job", q);
     const int32_t nt = (int32_t)((it.m + kRefineRows - 1) / kRefineRows);
     for (int32_t c0 = 0; c0 < it.k; c0 += 8) {
       RefineInst ri{};
@@ -846,50 +868,53 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
       ri.ldb = it.ldb;
       ri.X = it.X + (int64_t)c0 * it.ldx;
       ri.ldx = it.ldx;
-      ri.ldr = (int64_t)plans[q].launches[0].job_count * it.n;  // compact FP64 tree storage
-      const int32_t ix = (int32_t)rinst.size();
+      ri.ldr = (int64_t)b.plans[q].launches[0].job_count * it.n;  // compact FP64 tree storage
+      const int32_t ix = (int32_t)b.rinst.size();
       for (int32_t t = 0; t < nt; ++t) {
         RefineTask tk{};
         tk.row0 = (int64_t)t * kRefineRows;
         tk.rows = (int32_t)std::min<int64_t>(kRefineRows, it.m - tk.row0);
         tk.inst = ix;
         tk.idx = t;
-        rtasks.push_back(tk);
+        b.rtasks.push_back(tk);
       }
-      const size_t oP = take(sizeof(double) * (size_t)nt * it.n * ri.k);
-      roffs.push_back({q, oP});
-      rinst.push_back(ri);
-      rsmem = std::max(rsmem, refine_smem_bytes(it.n, ri.kb));
+      b.rP.push_back(take(sizeof(double) * (size_t)nt * it.n * ri.k));
+      b.ritem.push_back(q);
+      b.rinst.push_back(ri);
+      b.rsmem = std::max(b.rsmem, refine_smem_bytes(it.n, ri.kb));
     }
   }
-  size_t o_rhist = 0;
-  if (!rinst.empty()) {
-    o_rhist = take(sizeof(double) * kRefineSteps * rinst.size());  // -1 = step not run
-    o_rinst = take(sizeof(RefineInst) * rinst.size());
-    o_rtasks = take(sizeof(RefineTask) * rtasks.size());
-    o_rflags = take(sizeof(int32_t) * 2 * rinst.size());
+  if (!b.rinst.empty()) {
+    b.o_rhist = take(sizeof(double) * kRefineSteps * b.rinst.size());
+    b.o_rinst = take(sizeof(RefineInst) * b.rinst.size());
+    b.o_rtasks = take(sizeof(RefineTask) * b.rtasks.size());
+    b.o_rflags = take(sizeof(int32_t) * 2 * b.rinst.size());
   }
-  void *blk = nullptr;
-  CUDA_TRY(pool_alloc(&blk, off, s));
-  char *base = (char *)blk;
-  std::vector<BatchInst> inst(count);
-  for (int32_t q = 0; q < count; ++q) {
-    const tsqr_batch_item &it = items[q];
-    const Plan &pl = plans[q];
-    BatchInst &bi = inst[q];
+  b.bytes = off;
+  return TSQR_OK;
+}
+
+// Fills the device addresses of the instance and refinement tables for a block at base.
+void batch_bind(BatchBuild &b, char *base) {
+  b.inst.resize(b.count);
+  for (int32_t q = 0; q < b.count; ++q) {
+    const tsqr_batch_item &it = b.items[q];
+    const Plan &pl = b.plans[q];
+    const BatchBuild::Off &o = b.offs[q];
+    BatchInst &bi = b.inst[q];
+    bi = {};
     bi.A = it.A;
     bi.lda = it.lda;
-    bi.V = base + offs[q].V;
+    bi.V = base + o.V;
     bi.ldv = it.m;
-    bi.B = it.k > 0 ? (double *)(base + offs[q].B) : nullptr;
     bi.ldb = it.m;
-    bi.tau = base + offs[q].tau;
-    bi.scl = base + offs[q].scl;
+    bi.tau = base + o.tau;
+    bi.scl = base + o.scl;
     if (pl.mixed) {
-      bi.V64 = (double *)(base + offs[q].V64);
+      bi.V64 = (double *)(base + o.V64);
       bi.ldv64 = (int64_t)pl.launches[0].job_count * it.n;
-      bi.tau64 = (double *)(base + offs[q].tau64);
-      bi.scl64 = (double *)(base + offs[q].scl64);
+      bi.tau64 = (double *)(base + o.tau64);
+      bi.scl64 = (double *)(base + o.scl64);
     } else {
       bi.V64 = (double *)bi.V;
       bi.ldv64 = it.m;
@@ -900,102 +925,189 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     bi.ldr = it.ldr;
     bi.X = pl.mixed ? nullptr : it.X;  // mixed items are solved by the refinement launches
     bi.ldx = it.ldx;
-    bi.status = (int32_t *)(base + o_st) + q;
+    bi.status = (int32_t *)(base + b.o_st) + q;
     bi.n = it.n;
     bi.k = pl.mixed ? 0 : it.k;
+    bi.B = bi.k > 0 ? (double *)(base + o.B) : nullptr;
     bi.ldt = pl.tile_h;
-    bi.ldt_tree = tree_rows[q];
+    bi.ldt_tree = b.tree_rows[q];
     bi.mixed = pl.mixed ? 1 : 0;
-    if (pl.mixed) bi.B = nullptr;
+  }
+  int32_t *flags = (int32_t *)(base + b.o_rflags);  // counter, done per instance
+  for (size_t r = 0; r < b.rinst.size(); ++r) {
+    const int32_t q = b.ritem[r];
+    RefineInst &ri = b.rinst[r];
+    ri.R = b.inst[q].V64 + b.root[q];
+    ri.P = (double *)(base + b.rP[r]);
+    ri.hist = (double *)(base + b.o_rhist) + (size_t)kRefineSteps * r;
+    ri.counter = flags + 2 * r;
+    ri.done = flags + 2 * r + 1;
+    ri.status = (int32_t *)(base + b.o_st) + q;
+  }
+}
+
+// The tables, host to device. A copy from pageable memory may wait for the stream to
+// drain, so this is issued before any kernel of the call.
+tsqr_status batch_upload(const BatchBuild &b, char *base, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(base + b.o_inst, b.inst.data(), sizeof(BatchInst) * b.count, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(base + b.o_jobs, b.jobs.data(), sizeof(BatchJob) * b.njobs, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(base + b.o_tiles, b.tiles.data(), sizeof(TileDesc) * (size_t)b.ntiles,
+                           cudaMemcpyHostToDevice, s));
+  if (!b.rinst.empty()) {
+    CUDA_TRY(cudaMemcpyAsync(base + b.o_rinst, b.rinst.data(), sizeof(RefineInst) * b.rinst.size(),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(base + b.o_rtasks, b.rtasks.data(), sizeof(RefineTask) * b.rtasks.size(),
+                             cudaMemcpyHostToDevice, s));
+  }
+  return TSQR_OK;
+}
+
+// One run: the right-hand-side copies, counter and flag resets, the persistent kernel,
+// and the refinement launches. Device-side operations only, so it can be captured in a
+// CUDA graph.
+tsqr_status batch_enqueue(const BatchBuild &b, char *base, cudaStream_t s, bool profile) {
+  for (int32_t q = 0; q < b.count; ++q) {
+    const tsqr_batch_item &it = b.items[q];
+    const BatchInst &bi = b.inst[q];
     if (bi.k > 0)
       CUDA_TRY(cudaMemcpy2DAsync(bi.B, sizeof(double) * it.m, it.B, sizeof(double) * it.ldb, sizeof(double) * it.m,
                                  it.k, cudaMemcpyDeviceToDevice, s));
   }
-  CUDA_TRY(cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(BatchJob) * njobs, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(base + o_tiles, tiles.data(), sizeof(TileDesc) * (size_t)ntiles, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(base + o_cnt, 0, sizeof(int32_t) * ((size_t)njobs + 1), s));
-  CUDA_TRY(cudaMemsetAsync(base + o_st, 0, sizeof(int32_t) * count, s));
-  // every host-to-device copy of the call is issued before its first kernel: a copy
-  // from pageable memory may wait for the stream to drain
-  if (!rinst.empty()) {
-    int32_t *flags = (int32_t *)(base + o_rflags);  // counter, done per instance
-    for (size_t r = 0; r < rinst.size(); ++r) {
-      const RefOff &ro = roffs[r];
-      RefineInst &ri = rinst[r];
-      ri.R = inst[ro.item].V64 + root[ro.item];
-      ri.P = (double *)(base + ro.P);
-      ri.hist = (double *)(base + o_rhist) + (size_t)kRefineSteps * r;
-      ri.counter = flags + 2 * r;
-      ri.done = flags + 2 * r + 1;
-      ri.status = (int32_t *)(base + o_st) + ro.item;
-    }
-    CUDA_TRY(cudaMemcpyAsync(base + o_rinst, rinst.data(), sizeof(RefineInst) * rinst.size(), cudaMemcpyHostToDevice,
-                             s));
-    CUDA_TRY(cudaMemcpyAsync(base + o_rtasks, rtasks.data(), sizeof(RefineTask) * rtasks.size(),
-                             cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 2 * rinst.size(), s));
-    {
-      const std::vector<double> neg((size_t)kRefineSteps * rinst.size(), -1.0);  // staged before return
-      CUDA_TRY(cudaMemcpyAsync(base + o_rhist, neg.data(), sizeof(double) * neg.size(), cudaMemcpyHostToDevice, s));
-    }
+  CUDA_TRY(cudaMemsetAsync(base + b.o_cnt, 0, sizeof(int32_t) * ((size_t)b.njobs + 1), s));
+  CUDA_TRY(cudaMemsetAsync(base + b.o_st, 0, sizeof(int32_t) * b.count, s));
+  if (!b.rinst.empty()) {
+    CUDA_TRY(cudaMemsetAsync(base + b.o_rflags, 0, sizeof(int32_t) * 2 * b.rinst.size(), s));
+    // all-ones bytes are a NaN: "step not run" for the history readback
+    CUDA_TRY(cudaMemsetAsync(base + b.o_rhist, 0xff, sizeof(double) * kRefineSteps * b.rinst.size(), s));
   }
   BatchParams bp{};
-  bp.inst = (const BatchInst *)(base + o_inst);
-  bp.jobs = (const BatchJob *)(base + o_jobs);
-  bp.tiles = (const TileDesc *)(base + o_tiles);
-  bp.counters = (int32_t *)(base + o_cnt);
-  bp.queue = bp.counters + njobs;
-  bp.nchains = nchains;
-  const int grid = di.sms * cps_min;
+  bp.inst = (const BatchInst *)(base + b.o_inst);
+  bp.jobs = (const BatchJob *)(base + b.o_jobs);
+  bp.tiles = (const TileDesc *)(base + b.o_tiles);
+  bp.counters = (int32_t *)(base + b.o_cnt);
+  bp.queue = bp.counters + b.njobs;
+  bp.nchains = b.nchains;
   {
-    ProfScope ps(TSQR_PROF_BATCH, s);
-    CUDA_TRY(launch_factor_batch(bp, cmax, grid, smem, s));
+    ProfScope ps(profile ? TSQR_PROF_BATCH : -1, s);
+    CUDA_TRY(launch_factor_batch(bp, b.cmax, b.grid, b.smem, s));
   }
-  if (!rinst.empty()) {
+  if (!b.rinst.empty()) {
     RefineParams rp{};
-    rp.inst = (const RefineInst *)(base + o_rinst);
-    rp.tasks = (const RefineTask *)(base + o_rtasks);
+    rp.inst = (const RefineInst *)(base + b.o_rinst);
+    rp.tasks = (const RefineTask *)(base + b.o_rtasks);
     rp.max_steps = kRefineSteps;
     rp.tol = kBatchRefineTol;
-    ProfScope ps(TSQR_PROF_REFINE, s);
+    ProfScope ps(profile ? TSQR_PROF_REFINE : -1, s);
     for (int32_t step = 0; step < kRefineSteps; ++step) {
       rp.step = step;
-      CUDA_TRY(launch_refine_batch(rp, (int)rtasks.size(), rsmem, s));
+      CUDA_TRY(launch_refine_batch(rp, (int)b.rtasks.size(), b.rsmem, s));
     }
   }
-  tsqr_status st = TSQR_OK;
+  return TSQR_OK;
+}
+
+// Per-item (steps run, last ||dX||/||X||) from a host copy of the refinement history.
+void batch_info(const BatchBuild &b, const double *hist, double *info) {
+  for (int32_t q = 0; q < b.count; ++q) info[2 * q] = info[2 * q + 1] = 0.0;
+  for (size_t r = 0; r < b.rinst.size(); ++r) {
+    int steps = 0;
+    while (steps < kRefineSteps && hist[(size_t)kRefineSteps * r + steps] >= 0.0) ++steps;
+    double *o = info + 2 * b.ritem[r];
+    o[0] = std::max(o[0], (double)steps);
+    if (steps > 0) o[1] = std::max(o[1], hist[(size_t)kRefineSteps * r + steps - 1]);
+  }
+}
+
+}  // namespace
+
+tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                                       int32_t arity, cudaStream_t s, int32_t *status, int32_t *status_async,
+                                       double *info) {
+  BatchBuild b;
+  tsqr_status st = batch_build(items, count, chain_tiles, arity, b);
+  if (st != TSQR_OK) return st;
+  void *blk = nullptr;
+  CUDA_TRY(pool_alloc(&blk, b.bytes, s));
+  char *base = (char *)blk;
+  batch_bind(b, base);
+  st = batch_upload(b, base, s);
+  if (st == TSQR_OK) st = batch_enqueue(b, base, s, true);
+  if (st != TSQR_OK) {
+    cudaFreeAsync(blk, s);
+    return st;
+  }
   if (status_async) {
-    cudaError_t e = cudaMemcpyAsync(status_async, base + o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(status_async, base + b.o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status copy: %s", cudaGetErrorString(e));
   }
   if (status) {
-    cudaError_t e = cudaMemcpyAsync(status, base + o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(status, base + b.o_st, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
   }
   if (info) {
-    for (int32_t q = 0; q < count; ++q) info[2 * q] = info[2 * q + 1] = 0.0;
-    std::vector<double> hist((size_t)kRefineSteps * rinst.size());
+    std::vector<double> hist((size_t)kRefineSteps * b.rinst.size());
     cudaError_t e = cudaSuccess;
     if (!hist.empty()) {
-      e = cudaMemcpyAsync(hist.data(), base + o_rhist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(hist.data(), base + b.o_rhist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess)
       st = fail(TSQR_ERR_CUDA, "refinement history readback: %s", cudaGetErrorString(e));
-    } else {
-      for (size_t r = 0; r < rinst.size(); ++r) {
-        int steps = 0;
-        while (steps < kRefineSteps && hist[(size_t)kRefineSteps * r + steps] >= 0.0) ++steps;
-        double *o = info + 2 * roffs[r].item;
-        o[0] = std::max(o[0], (double)steps);
-        if (steps > 0) o[1] = std::max(o[1], hist[(size_t)kRefineSteps * r + steps - 1]);
-      }
-    }
+    else
+      batch_info(b, hist.data(), info);
   }
   cudaFreeAsync(blk, s);
   return st;
+}
+
+// ------------------------------------------------------------ reusable batch plans
+// A batch planned once and replayed as a CUDA graph: the tables are uploaded at creation,
+// and one run is the captured sequence of batch_enqueue plus the status and history
+// copies into pinned host buffers owned by the plan.
+struct tsqr_batch_plan {
+  BatchBuild b;
+  void *dmem = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *hstatus = nullptr;
+  double *hhist = nullptr;
+  cudaStream_t last = nullptr;
+  bool ran = false;
+};
+
+static void plan_release(tsqr_batch_plan *P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->dmem) cudaFree(P->dmem);
+  if (P->hstatus) cudaFreeHost(P->hstatus);
+  if (P->hhist) cudaFreeHost(P->hhist);
+  delete P;
+}
+
+static tsqr_status plan_capture(tsqr_batch_plan *P, cudaStream_t cs) {
+  const BatchBuild &b = P->b;
+  char *base = (char *)P->dmem;
+  CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  tsqr_status st = batch_enqueue(b, base, cs, false);
+  if (st == TSQR_OK) {
+    cudaError_t e = cudaMemcpyAsync(P->hstatus, base + b.o_st, sizeof(int32_t) * b.count, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && !b.rinst.empty())
+      e = cudaMemcpyAsync(P->hhist, base + b.o_rhist, sizeof(double) * kRefineSteps * b.rinst.size(),
+                          cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &g);  // always leave capture mode
+  if (st != TSQR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ee != cudaSuccess) return fail(TSQR_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+  P->graph = g;
+  CUDA_TRY(cudaGraphInstantiate(&P->exec, g, 0));
+  return TSQR_OK;
 }
 
 tsqr_status tsqr::check_batch_item(const tsqr_batch_item &it, int32_t q) {
@@ -1213,6 +1325,84 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   return st;
 }
 
+
+tsqr_status tsqr_batch_plan_create(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                                   tsqr_batch_plan **out) {
+  g_last_error.clear();
+  if (!out) return fail(TSQR_ERR_ARG, "null plan pointer");
+  *out = nullptr;
+  if (count < 1 || !items) return fail(TSQR_ERR_ARG, "bad items/count");
+  if (chain_tiles < 0 || !(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "bad chain_tiles/arity");
+  for (int32_t q = 0; q < count; ++q) {
+    tsqr_status st = check_batch_item(items[q], q);
+    if (st != TSQR_OK) return st;
+  }
+  tsqr_batch_plan *P = nullptr;
+  try {
+    P = new tsqr_batch_plan();
+    tsqr_status st = batch_build(items, count, chain_tiles, arity, P->b);
+    if (st != TSQR_OK) {
+      plan_release(P);
+      return st;
+    }
+  } catch (const std::bad_alloc &) {
+    plan_release(P);
+    return fail(TSQR_ERR_OOM, "host allocation failed");
+  }
+  cudaStream_t cs = nullptr;
+  auto bail = [&](tsqr_status st) {
+    if (cs) cudaStreamDestroy(cs);
+    plan_release(P);
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&P->dmem, P->b.bytes);
+  if (e != cudaSuccess) return bail(fail(TSQR_ERR_OOM, "plan workspace of %zu bytes: %s", P->b.bytes, cudaGetErrorString(e)));
+  e = cudaMallocHost(&P->hstatus, sizeof(int32_t) * count);
+  if (e == cudaSuccess && !P->b.rinst.empty())
+    e = cudaMallocHost(&P->hhist, sizeof(double) * kRefineSteps * P->b.rinst.size());
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(fail(TSQR_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e)));
+  batch_bind(P->b, (char *)P->dmem);
+  tsqr_status st = batch_upload(P->b, (char *)P->dmem, cs);
+  if (st == TSQR_OK) {
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "plan upload: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK) st = plan_capture(P, cs);
+  if (st != TSQR_OK) return bail(st);
+  cudaStreamDestroy(cs);
+  *out = P;
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_batch_plan_run(tsqr_batch_plan *P, void *stream) {
+  if (!P) return fail(TSQR_ERR_ARG, "null plan");
+  CUDA_TRY(cudaGraphLaunch(P->exec, (cudaStream_t)stream));
+  P->last = (cudaStream_t)stream;
+  P->ran = true;
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_batch_plan_results(tsqr_batch_plan *P, int32_t *status, double *info) {
+  if (!P) return fail(TSQR_ERR_ARG, "null plan");
+  if (!P->ran) return fail(TSQR_ERR_ARG, "the plan has not run");
+  CUDA_TRY(cudaStreamSynchronize(P->last));
+  if (status) std::copy(P->hstatus, P->hstatus + P->b.count, status);
+  if (info) {
+    if (P->b.rinst.empty())
+      std::fill(info, info + 2 * P->b.count, 0.0);
+    else
+      batch_info(P->b, P->hhist, info);
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *P) {
+  if (!P) return TSQR_OK;
+  if (P->ran) cudaStreamSynchronize(P->last);
+  plan_release(P);
+  return TSQR_OK;
+}
 
 tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
                              void *stream, int32_t *status, double *info) {

@@ -187,3 +187,14 @@ def test_server_entry_points_reject_bad_arguments(lib):
     assert lib.tsqr_server_drain(None) == 1
     assert lib.tsqr_server_stats(None, None) == 1
     assert lib.tsqr_server_destroy(None) == 0
+
+
+def test_batch_plan_entry_points_reject_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.tsqr_batch_plan_create(None, 1, 0, 0, ctypes.byref(h)) == 1
+    assert lib.tsqr_batch_plan_create(None, 0, 0, 0, ctypes.byref(h)) == 1
+    assert lib.tsqr_batch_plan_create(None, 1, 0, 0, None) == 1
+    assert not h.value
+    assert lib.tsqr_batch_plan_run(None, None) == 1
+    assert lib.tsqr_batch_plan_results(None, None, None) == 1
+    assert lib.tsqr_batch_plan_destroy(None) == 0

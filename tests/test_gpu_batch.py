@@ -159,3 +159,35 @@ def test_batch_mixed_singular_item(cuda_lib):
     good = lsq_items(2, 14, prec=1, kmax=3)
     _, st = run([good[0], (A, B, 1), good[1]])
     assert st == [0, 4, 0]
+
+
+def test_batch_plan_replay_equals_batch_solve(cuda_lib):
+    """A plan captured once as a CUDA graph gives bitwise the results of tsqr_batch_solve,
+    and picks up new data written in place into the same buffers."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    items = lsq_items(10, 21, prec=2, kmax=9) + make_items(6, 22)
+    dev = [{"A": to_dev(A), "prec": p, **({"B": to_dev(B)} if B is not None else {})} for A, B, p in items]
+    ref, st = ts.batch_solve(dev, chain_tiles=8, status=True)
+    with ts.BatchPlan(dev, chain_tiles=8) as plan:
+        for _ in range(2):
+            outs = plan.run()
+            status, info = plan.results()
+            assert status == st
+            for (R0, X0), (R1, X1) in zip(ref, outs):
+                assert torch.equal(R0, R1)
+                if X0 is not None:
+                    assert torch.equal(X0, X1)
+        # new data in the same buffers
+        for q, d in enumerate(dev):
+            d["A"].mul_(2.0)
+        outs = plan.run()
+        plan.results()
+        ref2 = ts.batch_solve(dev, chain_tiles=8)
+        for (R0, X0), (R1, X1) in zip(ref2, outs):
+            assert torch.equal(R0, R1)
+            if X0 is not None:
+                assert torch.equal(X0, X1)
+        for (A, B, p), (R, X) in zip(items[:10], outs[:10]):
+            # A doubled: x halves
+            assert rel(to_host(X) * 2.0, oracle.lstsq(A, B)) <= 1e-10
