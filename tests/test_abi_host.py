@@ -134,6 +134,10 @@ def check_plan(m, n, h, arity, flags, info, T, J):
                                          (10000, 7, 100, 3), (1000, 64, 64, 2), (130, 128, 128, 2),
                                          (2049, 1, 1, 2), (64, 64, 64, 2), (4_194_304, 64, 208, 2)])
 def test_pure_trees(lib, m, n, h, arity):
+    """A k-ary tree over P leaves has ceil(log_k P) sequential levels of n x n
+    triangle-on-triangle combines: for the binary tree this is the paper's message count
+    log2(P) for R only, each level adding one 2/3 n^3 combine to the critical path
+    (Table 1; Table 2 doubles both when Q is formed)."""
     info, T, J = describe(lib, m, n, h, arity, 0)
     chain_jobs, nlaunch = check_plan(m, n, h, arity, 0, info, T, J)
     P = max(1, m // h)
