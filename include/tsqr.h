@@ -118,12 +118,16 @@ tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *str
  *   leaf_h, arity, flags as in tsqr_factor (TSQR_INPLACE is ignored).
  *   prec       TSQR_FP64: FP64 TSQR of [A | B] (Q^T B fused into the factorization),
  *              then back substitution.
- *              TSQR_MIXED: FP32 leaf factorizations, FP64 tree, and FP64 augmented-
- *              system iterative refinement (Bjorck) starting from x = r = 0, so at most
- *              max_refine + 1 correction steps; it stops once ||dX||_F/||X||_F <= 1e-13.
- *              k <= 64; the right-hand sides are refined in groups of 8.
+ *              TSQR_MIXED: the batched engine on one item (see tsqr_batch_item): FP32 leaf
+ *              chains of 128-row tiles, the FP64 tree with `arity` (0 = binary), and
+ *              corrected semi-normal-equation refinement in FP64 from X = 0 (r = B - A X,
+ *              R^T R dX = A^T r), at most max_refine + 1 steps, stopping once the predicted
+ *              remaining ||dX||_F/||X||_F is below 1e-12 or the corrections stop
+ *              shrinking; leaf_h and flags do not apply. k <= 64, refined in groups of 8.
+ *              Synchronizes the stream.
  *   info       host array of length max_refine + 1 or NULL: info[s] = ||dX||_F/||X||_F
- *              after correction s (TSQR_MIXED), info[0] = 0 for TSQR_FP64. Filling it
+ *              of correction s (the largest over the groups of 8 right-hand sides; 0 for
+ *              steps not run) for TSQR_MIXED, info[0] = 0 for TSQR_FP64. Filling it
  *              synchronizes the stream.
  *   Errors: TSQR_ERR_ARG, TSQR_ERR_SINGULAR (some r_jj == 0; X is then undefined),
  *           TSQR_ERR_OOM, TSQR_ERR_CUDA. Detecting a singular R synchronizes the

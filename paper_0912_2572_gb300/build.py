@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             list(ex.map(run, jobs))
-    if force or _stale(LIB, objs):
+    if force or _stale(LIB, objs + [CSRC]):  # the folder's time changes when a source is removed
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
         os.replace(tmp, LIB)

@@ -530,8 +530,4 @@ cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t 
   return launch_apply_any(p, njobs, s);
 }
 
-cudaError_t launch_apply(const ApplyParamsT<float> &p, int njobs, cudaStream_t s) {
-  return launch_apply_any(p, njobs, s);
-}
-
 }  // namespace tsqr

@@ -525,12 +525,6 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
   __syncthreads();
 }
 
-template <int CPT>
-__global__ void __launch_bounds__(kThreads, 2) k_factor_f32r(const FactorParamsT<float> p) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  run_job_f32r<CPT>(p, p.jobs[p.job0 + blockIdx.x], smraw);
-}
-
 template <int CMAX, typename R>
 __global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -705,21 +699,6 @@ int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved
 
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {
   return launch_factor_any(p, njobs, s);
-}
-
-cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s) {
-  if (njobs <= 0) return cudaSuccess;
-  const size_t bytes = factor_smem_bytes(p.nc, 0, sizeof(float));
-  auto go = [&](auto kernel) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    kernel<<<njobs, kThreads, bytes, s>>>(p);
-    return cudaGetLastError();
-  };
-  if (p.nc <= 16) return go(k_factor_f32r<1>);
-  if (p.nc <= 32) return go(k_factor_f32r<2>);
-  if (p.nc <= 64) return go(k_factor_f32r<4>);
-  return go(k_factor_f32r<8>);
 }
 
 cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s) {

@@ -289,14 +289,12 @@ struct DevPlan {
   int device = -1;
   JobDesc *jobs = nullptr;
   TileDesc *tiles = nullptr;
-  int64_t *piv = nullptr;  // pivot row of every chain (launch-0 job), for the mixed path
   ~DevPlan() {
     int cur = 0;
     cudaGetDevice(&cur);
     if (device >= 0) cudaSetDevice(device);
     if (jobs) cudaFree(jobs);
     if (tiles) cudaFree(tiles);
-    if (piv) cudaFree(piv);
     cudaSetDevice(cur);
   }
 };
@@ -306,7 +304,8 @@ static std::list<std::shared_ptr<DevPlan>> g_plans;  // most recent first
 constexpr size_t kPlanCacheSize = 64;
 
 static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int flags,
-                            std::shared_ptr<DevPlan> &out, bool mixed = false) {
+                            std::shared_ptr<DevPlan> &out) {
+  const bool mixed = false;  // the mixed path plans through the batched engine
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   flags &= TSQR_TWO_LEVEL;
@@ -333,13 +332,6 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
   CUDA_TRY(cudaMalloc(&dp->tiles, sizeof(TileDesc) * pl.tiles.size()));
   CUDA_TRY(cudaMemcpy(dp->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(dp->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(), cudaMemcpyHostToDevice));
-  if (mixed) {
-    const int32_t G = pl.launches[0].job_count;
-    std::vector<int64_t> piv(G);
-    for (int32_t c = 0; c < G; ++c) piv[c] = pl.jobs[c].piv_row;
-    CUDA_TRY(cudaMalloc(&dp->piv, sizeof(int64_t) * G));
-    CUDA_TRY(cudaMemcpy(dp->piv, piv.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice));
-  }
   std::lock_guard<std::mutex> lk(g_plan_mu);
   g_plans.push_front(dp);
   while (g_plans.size() > kPlanCacheSize) g_plans.pop_back();
@@ -460,10 +452,6 @@ static void plan_info(const Plan &pl, int64_t *out) {
   out[7] = pl.ctas_per_sm;
 }
 
-// Refinement stops once ||dx||/||x|| <= kRefineTol: x is then at the FP64 floor of the
-// problem (about kappa * u), so further corrections change nothing measurable.
-constexpr double kRefineTol = 1e-13;
-
 // Batched mixed least squares (refine_batch.cu): rows per refinement task, the number of
 // refinement launches, and the stopping tolerance on the predicted remaining
 // ||dX||/||X|| (the last correction times rho / (1 - rho), rho the observed contraction).
@@ -480,184 +468,6 @@ constexpr double kFp64Factor = 0.76, kFp64FactorNarrow = 0.6;
 constexpr double kFp32FactorPerCol = 0.053, kFp32FactorMax = 3.3;
 constexpr double kRefineTflops = 0.75, kRefineTflopsNarrow = 0.6;
 constexpr double kRefineStepsEst = 2.6;
-
-// Mixed-precision least squares: FP32 chains (leaves and flat chains), FP64 tree on the
-// compact pivot blocks, then Bjorck augmented-system refinement with FP64 residuals
-// (mixed.cu). Right-hand sides are refined in groups of at most 8 columns.
-static tsqr_status run_lstsq_mixed(const double *A, int64_t m, int n, int64_t lda, const double *B, int64_t ldb,
-                                   int k, double *X, int64_t ldx, int leaf_h, int arity, int flags, int max_refine,
-                                   cudaStream_t s, double *info) {
-  std::shared_ptr<DevPlan> dp;
-  tsqr_status st = get_plan(m, n, n, leaf_h, arity, flags, dp, true);
-  if (st != TSQR_OK) return st;
-  const Plan &pl = dp->plan;
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  const DeviceInfo di = device_info(dev);
-  const int G = pl.launches[0].job_count;
-  const int64_t Gn = (int64_t)G * n;
-  const size_t nrefl = pl.tiles.size() * (size_t)n;
-  const int kk = std::min(k, 8);
-  const int steps = max_refine + 1;
-  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  // one pool block for everything
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t o = off;
-    off += up(bytes);
-    return o;
-  };
-  const size_t o_V32 = take(sizeof(float) * (size_t)m * n);
-  const size_t o_t32 = take(sizeof(float) * nrefl), o_s32 = take(sizeof(float) * nrefl);
-  const size_t o_V64 = take(sizeof(double) * (size_t)Gn * n);
-  const size_t o_t64 = take(sizeof(double) * nrefl), o_s64 = take(sizeof(double) * nrefl);
-  const size_t o_B32 = take(sizeof(float) * (size_t)m * kk);
-  const size_t o_B64 = take(sizeof(double) * (size_t)Gn * kk);
-  const size_t o_r = take(sizeof(double) * (size_t)m * kk);
-  const size_t o_x = take(sizeof(double) * (size_t)n * kk);
-  const size_t o_g = take(sizeof(double) * (size_t)n * kk);
-  const size_t o_h = take(sizeof(double) * (size_t)steps);
-  const size_t o_f = take(sizeof(int32_t) * 2);
-  void *blk = nullptr;
-  CUDA_TRY(pool_alloc(&blk, off, s));
-  char *base = (char *)blk;
-  float *V32 = (float *)(base + o_V32), *tau32 = (float *)(base + o_t32), *scl32 = (float *)(base + o_s32);
-  double *V64 = (double *)(base + o_V64), *tau64 = (double *)(base + o_t64), *scl64 = (double *)(base + o_s64);
-  float *B32 = (float *)(base + o_B32);
-  double *B64 = (double *)(base + o_B64), *r = (double *)(base + o_r), *x = (double *)(base + o_x);
-  double *g = (double *)(base + o_g), *hist = (double *)(base + o_h);
-  int32_t *done = (int32_t *)(base + o_f), *status = done + 1;
-  std::vector<double> hinfo;
-  int32_t hstatus = 0;
-
-  auto body = [&]() -> tsqr_status {
-    // factorization: FP32 chains, pivot blocks to FP64, FP64 tree
-    FactorParamsT<float> f32{};
-    f32.A = A;
-    f32.lda = lda;
-    f32.V = V32;
-    f32.ldv = m;
-    f32.jobs = dp->jobs;
-    f32.tiles = dp->tiles;
-    f32.tau = tau32;
-    f32.scl = scl32;
-    f32.n = n;
-    f32.nc = n;
-    f32.ldt = pl.tile_h;
-    f32.job0 = 0;
-    {
-      ProfScope ps(TSQR_PROF_FACTOR_CHAINS, s);
-      CUDA_TRY(launch_factor(f32, G, s));
-    }
-    {
-      ProfScope ps(TSQR_PROF_SMALL, s);
-      CUDA_TRY(launch_gather_r(V32, m, dp->piv, G, n, V64, Gn, s));
-    }
-    FactorParamsT<double> f64{};
-    f64.V = V64;
-    f64.ldv = Gn;
-    f64.jobs = dp->jobs;
-    f64.tiles = dp->tiles;
-    f64.tau = tau64;
-    f64.scl = scl64;
-    f64.n = n;
-    f64.nc = n;
-    f64.ldt = n;
-    for (size_t q = 1; q < pl.launches.size(); ++q) {
-      f64.job0 = pl.launches[q].job_begin;
-      ProfScope ps(TSQR_PROF_FACTOR_TREE, s);
-      CUDA_TRY(launch_factor(f64, pl.launches[q].job_count, s));
-    }
-    ApplyParamsT<float> a32{};
-    a32.V = V32;
-    a32.ldv = m;
-    a32.B = B32;
-    a32.ldb = m;
-    a32.jobs = dp->jobs;
-    a32.tiles = dp->tiles;
-    a32.tau = tau32;
-    a32.scl = scl32;
-    a32.n = n;
-    a32.ldt = pl.tile_h;
-    a32.job0 = 0;
-    a32.done = done;
-    ApplyParamsT<double> a64{};
-    a64.V = V64;
-    a64.ldv = Gn;
-    a64.B = B64;
-    a64.ldb = Gn;
-    a64.jobs = dp->jobs;
-    a64.tiles = dp->tiles;
-    a64.tau = tau64;
-    a64.scl = scl64;
-    a64.n = n;
-    a64.ldt = n;
-    a64.done = done;
-    const int nl = (int)pl.launches.size();
-    for (int c0 = 0; c0 < k; c0 += 8) {
-      const int kc = std::min(8, k - c0);
-      a32.k = a64.k = kc;
-      CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * kk, s));
-      CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)n * kk, s));
-      CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * (size_t)steps, s));
-      CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(int32_t) * 2, s));
-      for (int step = 0; step < steps; ++step) {
-        {
-          ProfScope ps(TSQR_PROF_SMALL, s);
-          CUDA_TRY(launch_resid(A, lda, m, n, kc, B + (int64_t)c0 * ldb, ldb, r, x, B32, g, step == 0, done,
-                                di.sms, s));
-        }
-        a32.trans = 1;
-        {
-          ProfScope ps(TSQR_PROF_APPLY_QT, s);
-          CUDA_TRY(launch_apply(a32, G, s));
-        }
-        CUDA_TRY(launch_gather_b(B32, m, dp->piv, G, n, kc, B64, Gn, done, s));
-        a64.trans = 1;
-        for (int q = 1; q < nl; ++q) {
-          a64.job0 = pl.launches[q].job_begin;
-          ProfScope ps(TSQR_PROF_APPLY_QT, s);
-          CUDA_TRY(launch_apply(a64, pl.launches[q].job_count, s));
-        }
-        {
-          ProfScope ps(TSQR_PROF_SMALL, s);
-          CUDA_TRY(launch_refine_step(V64, Gn, n, kc, B64, Gn, g, x, hist, step, kRefineTol, done, status, s));
-        }
-        if (step + 1 == steps) break;  // the last correction of x needs no new residual
-        a64.trans = 0;
-        for (int q = nl - 1; q >= 1; --q) {
-          a64.job0 = pl.launches[q].job_begin;
-          ProfScope ps(TSQR_PROF_APPLY_Q, s);
-          CUDA_TRY(launch_apply(a64, pl.launches[q].job_count, s));
-        }
-        CUDA_TRY(launch_scatter_b(B32, m, dp->piv, G, n, kc, B64, Gn, done, s));
-        a32.trans = 0;
-        {
-          ProfScope ps(TSQR_PROF_APPLY_Q, s);
-          CUDA_TRY(launch_apply(a32, G, s));
-        }
-      }
-      CUDA_TRY(cudaMemcpy2DAsync(X + (int64_t)c0 * ldx, sizeof(double) * ldx, x, sizeof(double) * n,
-                                 sizeof(double) * n, kc, cudaMemcpyDeviceToDevice, s));
-      if (info && c0 == 0) {
-        hinfo.resize(steps);
-        CUDA_TRY(cudaMemcpyAsync(hinfo.data(), hist, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
-      }
-      int32_t st_c = 0;
-      CUDA_TRY(cudaMemcpyAsync(&st_c, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      CUDA_TRY(cudaStreamSynchronize(s));
-      if (st_c) hstatus = st_c;
-    }
-    return TSQR_OK;
-  };
-  st = body();
-  cudaFreeAsync(blk, s);
-  if (st != TSQR_OK) return st;
-  if (info)
-    for (int i = 0; i < steps; ++i) info[i] = i < (int)hinfo.size() ? hinfo[i] : 0.0;
-  if (hstatus == 4) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
-  return TSQR_OK;
-}
 
 // ---------------------------------------------------------------- batched solve
 namespace {
@@ -689,10 +499,12 @@ struct BatchBuild {
   std::vector<RefineInst> rinst;
   std::vector<RefineTask> rtasks;
   size_t rsmem = 0;
+  int32_t max_steps = kRefineSteps;  // refinement launches (mixed least-squares items)
 };
 
 tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
-                        BatchBuild &b) {
+                        BatchBuild &b, int32_t max_steps = kRefineSteps) {
+  b.max_steps = max_steps;
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   DeviceInfo di = device_info(dev);
@@ -885,7 +697,7 @@ tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t cha
     }
   }
   if (!b.rinst.empty()) {
-    b.o_rhist = take(sizeof(double) * kRefineSteps * b.rinst.size());
+    b.o_rhist = take(sizeof(double) * b.max_steps * b.rinst.size());
     b.o_rinst = take(sizeof(RefineInst) * b.rinst.size());
     b.o_rtasks = take(sizeof(RefineTask) * b.rtasks.size());
     b.o_rflags = take(sizeof(int32_t) * 2 * b.rinst.size());
@@ -939,7 +751,7 @@ void batch_bind(BatchBuild &b, char *base) {
     RefineInst &ri = b.rinst[r];
     ri.R = b.inst[q].V64 + b.root[q];
     ri.P = (double *)(base + b.rP[r]);
-    ri.hist = (double *)(base + b.o_rhist) + (size_t)kRefineSteps * r;
+    ri.hist = (double *)(base + b.o_rhist) + (size_t)b.max_steps * r;
     ri.counter = flags + 2 * r;
     ri.done = flags + 2 * r + 1;
     ri.status = (int32_t *)(base + b.o_st) + q;
@@ -978,7 +790,7 @@ tsqr_status batch_enqueue(const BatchBuild &b, char *base, cudaStream_t s, bool 
   if (!b.rinst.empty()) {
     CUDA_TRY(cudaMemsetAsync(base + b.o_rflags, 0, sizeof(int32_t) * 2 * b.rinst.size(), s));
     // all-ones bytes are a NaN: "step not run" for the history readback
-    CUDA_TRY(cudaMemsetAsync(base + b.o_rhist, 0xff, sizeof(double) * kRefineSteps * b.rinst.size(), s));
+    CUDA_TRY(cudaMemsetAsync(base + b.o_rhist, 0xff, sizeof(double) * b.max_steps * b.rinst.size(), s));
   }
   BatchParams bp{};
   bp.inst = (const BatchInst *)(base + b.o_inst);
@@ -995,10 +807,10 @@ tsqr_status batch_enqueue(const BatchBuild &b, char *base, cudaStream_t s, bool 
     RefineParams rp{};
     rp.inst = (const RefineInst *)(base + b.o_rinst);
     rp.tasks = (const RefineTask *)(base + b.o_rtasks);
-    rp.max_steps = kRefineSteps;
+    rp.max_steps = b.max_steps;
     rp.tol = kBatchRefineTol;
     ProfScope ps(profile ? TSQR_PROF_REFINE : -1, s);
-    for (int32_t step = 0; step < kRefineSteps; ++step) {
+    for (int32_t step = 0; step < b.max_steps; ++step) {
       rp.step = step;
       CUDA_TRY(launch_refine_batch(rp, (int)b.rtasks.size(), b.rsmem, s));
     }
@@ -1011,11 +823,51 @@ void batch_info(const BatchBuild &b, const double *hist, double *info) {
   for (int32_t q = 0; q < b.count; ++q) info[2 * q] = info[2 * q + 1] = 0.0;
   for (size_t r = 0; r < b.rinst.size(); ++r) {
     int steps = 0;
-    while (steps < kRefineSteps && hist[(size_t)kRefineSteps * r + steps] >= 0.0) ++steps;
+    while (steps < b.max_steps && hist[(size_t)b.max_steps * r + steps] >= 0.0) ++steps;
     double *o = info + 2 * b.ritem[r];
     o[0] = std::max(o[0], (double)steps);
-    if (steps > 0) o[1] = std::max(o[1], hist[(size_t)kRefineSteps * r + steps - 1]);
+    if (steps > 0) o[1] = std::max(o[1], hist[(size_t)b.max_steps * r + steps - 1]);
   }
+}
+
+// One mixed least-squares problem through the batched engine: FP32 chains, FP64 tree,
+// corrected semi-normal-equation refinement, at most max_steps steps. hist (host,
+// max_steps doubles, or NULL) receives ||dX||/||X|| per step, the largest over the groups
+// of 8 right-hand sides (0 for steps not run).
+tsqr_status lstsq_mixed_batched(const tsqr_batch_item &it, int32_t arity, int32_t max_steps, cudaStream_t s,
+                                double *hist) {
+  BatchBuild b;
+  tsqr_status st = batch_build(&it, 1, 0, arity, b, max_steps);
+  if (st != TSQR_OK) return st;
+  void *blk = nullptr;
+  CUDA_TRY(pool_alloc(&blk, b.bytes, s));
+  char *base = (char *)blk;
+  batch_bind(b, base);
+  st = batch_upload(b, base, s);
+  if (st == TSQR_OK) st = batch_enqueue(b, base, s, true);
+  int32_t hstatus = 0;
+  std::vector<double> h((size_t)b.max_steps * b.rinst.size());
+  if (st == TSQR_OK) {
+    cudaError_t e = cudaMemcpyAsync(&hstatus, base + b.o_st, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && hist)
+      e = cudaMemcpyAsync(h.data(), base + b.o_rhist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
+  }
+  cudaFreeAsync(blk, s);
+  if (st != TSQR_OK) return st;
+  if (hist) {
+    for (int32_t step = 0; step < b.max_steps; ++step) {
+      double v = 0.0;
+      for (size_t r = 0; r < b.rinst.size(); ++r) {
+        const double x = h[(size_t)b.max_steps * r + step];
+        if (x >= 0.0) v = std::max(v, x);
+      }
+      hist[step] = v;
+    }
+  }
+  if (hstatus == TSQR_ERR_SINGULAR) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
+  return TSQR_OK;
 }
 
 }  // namespace
@@ -1046,7 +898,7 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
   }
   if (info) {
-    std::vector<double> hist((size_t)kRefineSteps * b.rinst.size());
+    std::vector<double> hist((size_t)b.max_steps * b.rinst.size());
     cudaError_t e = cudaSuccess;
     if (!hist.empty()) {
       e = cudaMemcpyAsync(hist.data(), base + b.o_rhist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
@@ -1094,7 +946,7 @@ static tsqr_status plan_capture(tsqr_batch_plan *P, cudaStream_t cs) {
   if (st == TSQR_OK) {
     cudaError_t e = cudaMemcpyAsync(P->hstatus, base + b.o_st, sizeof(int32_t) * b.count, cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess && !b.rinst.empty())
-      e = cudaMemcpyAsync(P->hhist, base + b.o_rhist, sizeof(double) * kRefineSteps * b.rinst.size(),
+      e = cudaMemcpyAsync(P->hhist, base + b.o_rhist, sizeof(double) * b.max_steps * b.rinst.size(),
                           cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
   }
@@ -1272,9 +1124,24 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   if (max_refine < 0) return fail(TSQR_ERR_ARG, "max_refine < 0");
   if (prec != TSQR_FP64 && prec != TSQR_MIXED) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   flags &= ~TSQR_INPLACE;
-  if (prec == TSQR_MIXED)
-    return run_lstsq_mixed(A, m, n, lda, B, ldb, k, X, ldx, leaf_h, arity, flags, max_refine, (cudaStream_t)stream,
-                           info);
+  if (prec == TSQR_MIXED) {
+    tsqr_batch_item it{};
+    it.A = A;
+    it.m = m;
+    it.n = n;
+    it.lda = lda;
+    it.B = B;
+    it.ldb = ldb;
+    it.k = k;
+    it.X = X;
+    it.ldx = ldx;
+    it.prec = TSQR_MIXED;
+    try {
+      return lstsq_mixed_batched(it, arity == 0 ? 2 : arity, max_refine + 1, (cudaStream_t)stream, info);
+    } catch (const std::bad_alloc &) {
+      return fail(TSQR_ERR_OOM, "host allocation failed");
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   tsqr_factors *f = new (std::nothrow) tsqr_factors();
   if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
@@ -1359,7 +1226,7 @@ tsqr_status tsqr_batch_plan_create(const tsqr_batch_item *items, int32_t count, 
   if (e != cudaSuccess) return bail(fail(TSQR_ERR_OOM, "plan workspace of %zu bytes: %s", P->b.bytes, cudaGetErrorString(e)));
   e = cudaMallocHost(&P->hstatus, sizeof(int32_t) * count);
   if (e == cudaSuccess && !P->b.rinst.empty())
-    e = cudaMallocHost(&P->hhist, sizeof(double) * kRefineSteps * P->b.rinst.size());
+    e = cudaMallocHost(&P->hhist, sizeof(double) * P->b.max_steps * P->b.rinst.size());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail(TSQR_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e)));
   batch_bind(P->b, (char *)P->dmem);

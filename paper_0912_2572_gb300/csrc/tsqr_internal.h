@@ -91,7 +91,6 @@ constexpr int kF32TileRows = 16 * kF32Rpt;
 // step buffers of a register-tile FP32 chain (elem = 4).
 size_t factor_smem_bytes(int nc, int ldt, size_t elem = sizeof(double));
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s);
-cudaError_t launch_factor(const FactorParamsT<float> &p, int njobs, cudaStream_t s);
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
                     size_t optin_per_block, size_t elem = sizeof(double));
 
@@ -212,7 +211,6 @@ struct ApplyParamsT {
 using ApplyParams = ApplyParamsT<double>;
 
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s);
-cudaError_t launch_apply(const ApplyParamsT<float> &p, int njobs, cudaStream_t s);
 
 // ------------------------------------------------------------------- small kernels
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,
@@ -220,19 +218,6 @@ cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int
 cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double *d,
                               cudaStream_t s);
 cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s);
-// mixed-precision least squares (mixed.cu)
-cudaError_t launch_gather_r(const float *V32, int64_t ldv32, const int64_t *piv, int G, int n, double *V64,
-                            int64_t ldv64, cudaStream_t s);
-cudaError_t launch_gather_b(const float *B32, int64_t ldb32, const int64_t *piv, int G, int n, int k, double *B64,
-                            int64_t ldb64, const int32_t *done, cudaStream_t s);
-cudaError_t launch_scatter_b(float *B32, int64_t ldb32, const int64_t *piv, int G, int n, int k, const double *B64,
-                             int64_t ldb64, const int32_t *done, cudaStream_t s);
-cudaError_t launch_resid(const double *A, int64_t lda, int64_t m, int n, int k, const double *b, int64_t ldb,
-                         double *r, const double *x, float *B32, double *g, int first, const int32_t *done,
-                         int sms, cudaStream_t s);
-cudaError_t launch_refine_step(const double *R, int64_t ldr, int n, int k, double *B64, int64_t ldb64, double *g,
-                               double *x, double *hist, int step, double tol, int32_t *done, int32_t *status,
-                               cudaStream_t s);
 
 // X = R^{-1} (D C[0:n]) for the raw upper triangle R (leading dimension ldr) and the
 // optional sign vector d (NULL = no scaling); a zero pivot sets *status = 4.
