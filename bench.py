@@ -45,7 +45,23 @@ def flops_step(m, n, k=1):
     return {"factor": f, "form_q": f, "apply_qt": 4.0 * m * n * k - 2.0 * n * n * k, "solve": float(n * n * k)}
 
 
-def parse():
+def rank_max(x: float, world: int, device: str) -> float:
+    """The largest x over all ranks of the process group (x itself on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max_ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (t_max_ms * 1e-3)
+
+
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -68,7 +84,7 @@ def parse():
     p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
     p.add_argument("--profile-batch", type=int, default=0, metavar="N",
                    help="only run N mixed batches of 32 served-mix requests (a small case for ncu)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 # ------------------------------------------------------------------------ clocks
@@ -609,12 +625,8 @@ def bench_ours(args):
     if world > 1:
         dist.barrier()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = fl_step * args.steps * world / (t_max * 1e-3) / 1e9
+    t_max = rank_max(t_ms, world, "cuda")
+    value = whole_job_rate(fl_step * args.steps, world, t_max) / 1e9
 
     # --- per-phase times from the launch profile
     phase_ms = {}
@@ -655,12 +667,8 @@ def bench_ours(args):
             F.free()
         e1.record(stream)
         torch.cuda.synchronize()
-        te = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": fl_step * args.e2e_steps * world / (te * 1e-3) / 1e9, "unit": "Gflop/s",
+        te = rank_max(e0.elapsed_time(e1), world, "cuda")
+        e2e = {"value": whole_job_rate(fl_step * args.e2e_steps, world, te) / 1e9, "unit": "Gflop/s",
                "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
                "ms_per_step": te / args.e2e_steps}
         del Ah, Qh
