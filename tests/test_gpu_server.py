@@ -118,3 +118,35 @@ def test_server_drain_and_destroy_finish_everything(cuda_lib):
     assert len(srv.poll()) == len(reqs)
     srv.close()
     assert keep
+
+
+def test_concurrent_submitters(cuda_lib):
+    """Two host threads submit at once; every ticket completes once and every result is
+    bitwise the request solved alone."""
+    import threading
+    import paper_0912_2572_gb300 as ts
+    reqs = requests(24, 5, mhi=20000)
+    dev = [({"A": to_dev(A), **({"B": to_dev(B)} if B is not None else {})}) for A, B in reqs]
+    outs = {}
+    lock = threading.Lock()
+    with ts.Server(max_batch=8, streams=2, chain_tiles=8) as srv:
+        def worker(part):
+            for i in part:
+                t, out = srv.submit(dev[i])
+                with lock:
+                    outs[t] = (i, out)
+        th = [threading.Thread(target=worker, args=(range(k, len(dev), 2),)) for k in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        srv.drain()
+        done = srv.poll()
+    assert sorted(t for t, _, _ in done) == sorted(outs) and len(done) == len(reqs)
+    assert all(st == 0 for _, _, st in done)
+    for t, (i, (R, X)) in outs.items():
+        A, B = reqs[i]
+        R1, X1 = alone(A, B)
+        assert np.array_equal(to_host(R), R1)
+        if B is not None:
+            assert np.array_equal(to_host(X), X1)
