@@ -170,38 +170,41 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
     __syncwarp();
 
     const R *Vt = p.V + r0;
-    R xv[RW], xn[RW];
-    {
-      const int j0 = p.trans ? 0 : n - 1;
-      int lo, hi;
-      refl_rows(kind, j0, ht, lo, hi, td.off);
-#pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        const int i = lo + lane + 32 * r;
-        xv[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j0 * p.ldv) : R(0);
-      }
-    }
-    for (int s = 0; s < n; ++s) {
+    // the next D reflectors' tails (and tau, scale) are in flight while one is applied:
+    // each step is a short dependent chain, so one reflector ahead leaves HBM latency
+    // exposed
+    constexpr int D = RW <= 8 ? 4 : 2;
+    R xb[D][RW], tb[D], sb[D];
+    auto load_refl = [&](R(&dst)[RW], R &tau_d, R &scl_d, int s) {
       const int j = p.trans ? s : n - 1 - s;
       int lo, hi;
       refl_rows(kind, j, ht, lo, hi, td.off);
-      if (s + 1 < n) {
-        const int jn = p.trans ? s + 1 : n - 2 - s;
-        int lo2, hi2;
-        refl_rows(kind, jn, ht, lo2, hi2, td.off);
 #pragma unroll
-        for (int r = 0; r < RW; ++r) {
-          const int i = lo2 + lane + 32 * r;
-          xn[r] = (i < hi2) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : R(0);
-        }
+      for (int r = 0; r < RW; ++r) {
+        const int i = lo + lane + 32 * r;
+        dst[r] = (i < hi) ? __ldg(Vt + i + (int64_t)j * p.ldv) : R(0);
       }
-      const R tau = __ldg(p.tau + td.refl + j);
-      const R sc = __ldg(p.scl + td.refl + j);
-      constexpr int KP = pow2ceil(K);
-      R part[KP];
+      tau_d = __ldg(p.tau + td.refl + j);
+      scl_d = __ldg(p.scl + td.refl + j);
+    };
 #pragma unroll
-      for (int c = 0; c < KP; ++c) part[c] = R(0);
-      const int ra = (hi - lo + 31) >> 5;
+    for (int d = 0; d < D; ++d)
+      if (d < n) load_refl(xb[d], tb[d], sb[d], d);
+    for (int s0 = 0; s0 < n; s0 += D) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int s = s0 + d;
+        if (s >= n) break;
+        const int j = p.trans ? s : n - 1 - s;
+        int lo, hi;
+        refl_rows(kind, j, ht, lo, hi, td.off);
+        const R(&xv)[RW] = xb[d];
+        const R tau = tb[d], sc = sb[d];
+        constexpr int KP = pow2ceil(K);
+        R part[KP];
+#pragma unroll
+        for (int c = 0; c < KP; ++c) part[c] = R(0);
+        const int ra = (hi - lo + 31) >> 5;
 #define TSQR_WDOT(r)                                                                        \
   {                                                                                         \
     const int i = lo + lane + 32 * (r);                                                     \
@@ -209,22 +212,22 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
       _Pragma("unroll") for (int c = 0; c < K; ++c) part[c] = fma(xv[r], Bt[c * ldt + i], part[c]); \
     }                                                                                       \
   }
-      TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
+        TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
 #undef TSQR_WDOT
-      int idx;
-      const R tot = treduce32<KP, R>(part, lane, idx);
-      R cfv = R(0);
-      if ((lane & (32 / KP - 1)) == 0 && idx < K) {
-        R *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
-        const R piv = *pp;
-        const R w = fma(sc, tot, piv);
-        *pp = fma(-tau, w, piv);
-        cfv = tau * sc * w;
-      }
-      R cf[K];
+        int idx;
+        const R tot = treduce32<KP, R>(part, lane, idx);
+        R cfv = R(0);
+        if ((lane & (32 / KP - 1)) == 0 && idx < K) {
+          R *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
+          const R piv = *pp;
+          const R w = fma(sc, tot, piv);
+          *pp = fma(-tau, w, piv);
+          cfv = tau * sc * w;
+        }
+        R cf[K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(c));
-      __syncwarp();
+        for (int c = 0; c < K; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(c));
+        __syncwarp();
 #define TSQR_WUPD(r)                                                                        \
   {                                                                                         \
     const int i = lo + lane + 32 * (r);                                                     \
@@ -232,11 +235,11 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
       _Pragma("unroll") for (int c = 0; c < K; ++c) Bt[c * ldt + i] = fma(-cf[c], xv[r], Bt[c * ldt + i]); \
     }                                                                                       \
   }
-      TSQR_ROW_SLOTS(ra, RW, TSQR_WUPD)
+        TSQR_ROW_SLOTS(ra, RW, TSQR_WUPD)
 #undef TSQR_WUPD
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < RW; ++r) xv[r] = xn[r];
+        __syncwarp();
+        if (s + D < n) load_refl(xb[d], tb[d], sb[d], s + D);
+      }
     }
 #pragma unroll
     for (int c = 0; c < K; ++c) {
