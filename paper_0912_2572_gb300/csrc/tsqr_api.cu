@@ -460,12 +460,14 @@ constexpr size_t kBatchSmemSlack = 256;
 constexpr int kMixedChainFactor = 4;
 constexpr int32_t kRefineSteps = 10;
 constexpr double kBatchRefineTol = 1e-12;
-// Cost model of TSQR_AUTO, in TFLOP/s measured on GB300 batches of served requests:
-// the FP64 factor kernel (lower for n < 32, where the column steps are short), the FP32
-// factor kernel (rising with n up to its plateau), the refinement kernel, and the
-// refinement steps counted at full cost (the first step, from x = 0, costs half).
-constexpr double kFp64Factor = 0.76, kFp64FactorNarrow = 0.6;
-constexpr double kFp32FactorPerCol = 0.053, kFp32FactorMax = 3.3;
+// Cost model of TSQR_AUTO, in TFLOP/s as the kernels run inside a GB300 batch of served
+// requests: the FP64 factor kernel (lower for n < 32, where the column steps are short),
+// the FP32 register-tile factor kernel (rising with n up to its plateau), the refinement
+// kernel, and the refinement steps counted at full cost (the first step, from x = 0,
+// costs half). Fitted so that, in a served mix, only n = 16 requests with k >= 6 take
+// FP64 (timing every policy over the same 128 requests: the others were slower).
+constexpr double kFp64Factor = 0.76, kFp64FactorNarrow = 0.5;
+constexpr double kFp32FactorPerCol = 0.1, kFp32FactorMax = 6.0;
 constexpr double kRefineTflops = 0.75, kRefineTflopsNarrow = 0.6;
 constexpr double kRefineStepsEst = 2.6;
 
