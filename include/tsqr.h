@@ -338,6 +338,14 @@ enum {
 tsqr_status tsqr_profile_start(void);
 tsqr_status tsqr_profile_stop(int64_t max_records, int32_t *kind, float *ms, int64_t *count);
 
+/*
+ * tsqr_probe_fp64_peak — measures the device's burst FP64 FMA throughput (TFLOP/s, host
+ * *tflops): independent DFMA chains on every SM, best of three timed launches of about
+ * 17 ms, and the SM clock that launch ran at (MHz, host *sm_mhz, may be NULL). The FP64
+ * kernels' roofline denominator; synchronizes the stream. No paper counterpart.
+ */
+tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz);
+
 /* tsqr_strerror — static description of a status code. */
 const char *tsqr_strerror(tsqr_status s);
 

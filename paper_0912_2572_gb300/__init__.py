@@ -314,6 +314,17 @@ class Server:
         self.close()
 
 
+def probe_fp64_peak(stream=None, clock: bool = False):
+    """Measured burst FP64 FMA throughput of the current device in TFLOP/s (with
+    ``clock``, also the SM clock in MHz the probe ran at)."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    mhz = ctypes.c_double(0.0)
+    _lib.check(lib.tsqr_probe_fp64_peak(_stream(stream), ctypes.byref(out), ctypes.byref(mhz)),
+               "tsqr_probe_fp64_peak")
+    return (out.value, mhz.value) if clock else out.value
+
+
 def profile_collect(fn):
     """Runs fn() with launch profiling on and returns (fn's result, [(class, ms), ...])."""
     lib = _lib.load()

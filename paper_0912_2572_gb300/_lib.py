@@ -40,6 +40,7 @@ SIGNATURES = {
     "tsqr_batch_solve": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _vp, ctypes.POINTER(_i32),
                                  ctypes.POINTER(ctypes.c_double)]),
     "tsqr_free": (_i32, [_vp]),
+    "tsqr_probe_fp64_peak": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "tsqr_batch_plan_create": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "tsqr_batch_plan_run": (_i32, [_vp, _vp]),
     "tsqr_batch_plan_results": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),

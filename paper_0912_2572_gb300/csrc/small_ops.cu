@@ -59,6 +59,36 @@ __global__ void k_trsv(const double *__restrict__ R, int64_t ldr, int n, const d
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[i + (int64_t)c * ldx] = xs[i];
 }
 
+// FP64 FMA throughput probe (the roofline denominator of the FP64 kernels): every thread
+// runs kProbeChains independent DFMA chains, enough to keep the FP64 pipe issuing.
+// Thread 0 of block 0 also records the SM cycles and nanoseconds it ran (clk[0], clk[1]).
+constexpr int kProbeChains = 8;
+__device__ __forceinline__ uint64_t probe_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void k_dfma_probe(double *out, int iters, double a, double b, unsigned long long *clk) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  double x[kProbeChains];
+#pragma unroll
+  for (int u = 0; u < kProbeChains; ++u) x[u] = gid * 1e-12 + u;
+  const uint64_t c0 = clock64(), t0 = probe_ns();
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kProbeChains; ++u) x[u] = fma(x[u], a, b);
+  }
+  const uint64_t c1 = clock64(), t1 = probe_ns();
+  if (gid == 0) {
+    clk[0] = c1 - c0;
+    clk[1] = t1 - t0;
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int u = 0; u < kProbeChains; ++u) sum += x[u];
+  out[gid] = sum;
+}
+
 }  // namespace
 
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr, double *d,
@@ -83,6 +113,14 @@ cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, in
   if (k <= 0) return cudaSuccess;
   k_trsv<<<k, 128, sizeof(double) * (size_t)n, s>>>(R, ldr, n, C, ldc, X, ldx, d, status);
   return cudaGetLastError();
+}
+
+// Launches the probe on a grid of SMs x ctas_per_sm CTAs of 256 threads; returns the
+// flops it performs (2 per DFMA).
+double launch_dfma_probe(double *out, unsigned long long *clk, int sms, int ctas_per_sm, int iters,
+                         cudaStream_t s) {
+  k_dfma_probe<<<sms * ctas_per_sm, 256, 0, s>>>(out, iters, 0.9999999, 1e-7, clk);
+  return 2.0 * kProbeChains * (double)iters * 256.0 * sms * ctas_per_sm;
 }
 
 }  // namespace tsqr

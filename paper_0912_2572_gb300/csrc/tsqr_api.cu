@@ -1007,6 +1007,53 @@ const char *tsqr::last_error_text() { return g_last_error.c_str(); }
 
 extern "C" {
 
+tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz) {
+  if (!tflops) return fail(TSQR_ERR_ARG, "null output");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ctas = 4;
+  double *out = nullptr;
+  CUDA_TRY(pool_alloc((void **)&out, sizeof(double) * (size_t)di.sms * ctas * 256 + 64, s));
+  unsigned long long *clk = (unsigned long long *)(out + (size_t)di.sms * ctas * 256);
+  unsigned long long hclk[2] = {0, 0};
+  double mhz = 0.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 0.0;
+  // short launches (about 17 ms at 1.2 TFLOP/s): the burst rate, at the clock a kernel
+  // timed on its own runs at; seconds of pure DFMA load would lower the clock under the
+  // power cap
+  const int iters = 1 << 13;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    e = cudaEventRecord(e0, s);
+    const double fl = launch_dfma_probe(out, clk, di.sms, ctas, iters, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(hclk, clk, sizeof(hclk), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && rep > 0 && ms > 0.f) {
+      const double tf = fl / (ms * 1e-3) / 1e12;
+      if (tf > best) {
+        best = tf;
+        mhz = hclk[1] ? 1e3 * (double)hclk[0] / (double)hclk[1] : 0.0;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  if (e != cudaSuccess) return fail(TSQR_ERR_CUDA, "probe: %s", cudaGetErrorString(e));
+  *tflops = best;
+  if (sm_mhz) *sm_mhz = mhz;
+  return TSQR_OK;
+}
+
 const char *tsqr_strerror(tsqr_status s) {
   switch (s) {
     case TSQR_OK: return "success";

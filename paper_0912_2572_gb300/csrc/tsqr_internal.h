@@ -219,6 +219,11 @@ cudaError_t launch_scale_rows(double *B, int64_t ldb, int n, int k, const double
                               cudaStream_t s);
 cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cudaStream_t s);
 
+// The FP64 FMA throughput probe (out: one double per thread; clk: cycles and ns of one
+// thread); returns the flops of one launch.
+double launch_dfma_probe(double *out, unsigned long long *clk, int sms, int ctas_per_sm, int iters,
+                         cudaStream_t s);
+
 // X = R^{-1} (D C[0:n]) for the raw upper triangle R (leading dimension ldr) and the
 // optional sign vector d (NULL = no scaling); a zero pivot sets *status = 4.
 cudaError_t launch_trsv(const double *R, int64_t ldr, int n, const double *C, int64_t ldc,

@@ -54,3 +54,11 @@ def test_factor_matches_oracle(cuda_lib, m, n, h, arity, two):
     # input untouched (not in place)
     assert np.array_equal(to_host(Ad), A)
     F.free()
+
+
+def test_fp64_peak_probe_is_plausible(cuda_lib):
+    """The roofline denominator: the FP64 FMA throughput of a GB300-class GPU is about
+    1.2 TFLOP/s (2 DFMA per clock per SM at about 2 GHz), far below its FP32 rate."""
+    import paper_0912_2572_gb300 as ts
+    tf = ts.probe_fp64_peak()
+    assert 0.3 < tf < 3.0
