@@ -505,6 +505,42 @@ def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plai
                             "p99_ms": float(np.percentile(lat, 99) * 1e3),
                             "batches": srv.stats()["batches"] - b0,
                             "failed": sum(1 for d in done if d[2] != 0)}
+    # the plain path under Poisson arrivals: one request at a time, first come first
+    # served; latency from arrival to completion
+    def plain_open_loop(rate_, count):
+        gaps_ = g.exponential(1.0 / rate_, size=count)
+        arr = np.cumsum(gaps_) - gaps_[0]
+        ids = [int(i) for i in g.integers(0, pool_size, size=count)]
+        lat_ = []
+        start = time.perf_counter()
+        for a, i in zip(arr, ids):
+            while time.perf_counter() - start < a:
+                pass
+            ts.lstsq(pool[i]["A"], pool[i]["B"], leaf_h=pool[i]["leaf_h"], arity=2, two_level=True, prec=ts.FP64)
+            torch.cuda.synchronize()
+            lat_.append(time.perf_counter() - start - a)
+        lat_ = np.array(lat_)
+        return {"offered_per_s": rate_, "arrivals": count, "completed_per_s": count / (time.perf_counter() - start),
+                "p50_ms": float(np.percentile(lat_, 50) * 1e3), "p99_ms": float(np.percentile(lat_, 99) * 1e3)}
+
+    def served_open_loop(rate_, count, prec_):
+        with ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8) as srv:
+            warm = [int(i) for i in g.integers(0, pool_size, size=32)]
+            submit_all(srv, warm, prec_)
+            collect(srv, len(warm))
+            gaps_ = g.exponential(1.0 / rate_, size=count)
+            times_ = np.cumsum(gaps_) - gaps_[0]
+            idx_ = [int(i) for i in g.integers(0, pool_size, size=count)]
+            t0_ = time.perf_counter()
+            submit_all(srv, idx_, prec_, times_)
+            done_ = collect(srv, count)
+            t_ = time.perf_counter() - t0_
+        lat_ = np.array([d[1] for d in done_])
+        return {"offered_per_s": rate_, "arrivals": count, "completed_per_s": count / t_,
+                "p50_ms": float(np.percentile(lat_, 50) * 1e3), "p99_ms": float(np.percentile(lat_, 99) * 1e3)}
+
+    res["plain_open_loop"] = plain_open_loop(rate, 300)
+    res["low_rate_200_per_s"] = {"plain": plain_open_loop(200.0, 300), "served": served_open_loop(200.0, 300, prec)}
     res["plain_fp64"] = {"solves_per_s": 1.0 / t_plain, "ms_per_solve": t_plain * 1e3,
                          "gflops": plain_fl / t_plain / 1e9, "sample": plain_sample}
     res["speedup_closed_vs_plain"] = {k: v["solves_per_s"] / res["plain_fp64"]["solves_per_s"]
