@@ -191,3 +191,32 @@ def test_batch_plan_replay_equals_batch_solve(cuda_lib):
         for (A, B, p), (R, X) in zip(items[:10], outs[:10]):
             # A doubled: x halves
             assert rel(to_host(X) * 2.0, oracle.lstsq(A, B)) <= 1e-10
+
+
+def test_batch_strided_layouts(cuda_lib):
+    """Leading dimensions larger than the rows (views into bigger arrays) for A, B, R and X,
+    FP64 and mixed items alike."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    g = inputs.rng(31)
+    items, host = [], []
+    for q, prec in enumerate((ts.FP64, ts.MIXED, ts.AUTO, ts.FP64)):
+        m, n, k = int(g.integers(500, 9000)), int(g.choice([8, 32, 60])), int(g.integers(1, 6))
+        A = inputs.graded(m, n, 3.0, seed_g=100 + q, seed_v=200 + q)
+        B, _ = inputs.lstsq_rhs(A, k, 1e-6, 300 + q)
+        Abig = torch.zeros((n, m + 37), dtype=torch.float64, device="cuda")
+        Abig[:, :m] = torch.from_numpy(np.ascontiguousarray(A.T))
+        Bbig = torch.zeros((k, m + 5), dtype=torch.float64, device="cuda")
+        Bbig[:, :m] = torch.from_numpy(np.ascontiguousarray(B.T))
+        Rbig = torch.full((n, n + 3), 7.0, dtype=torch.float64, device="cuda")
+        Xbig = torch.full((k, n + 9), 7.0, dtype=torch.float64, device="cuda")
+        items.append({"A": Abig.t()[:m], "B": Bbig.t()[:m], "R": Rbig.t()[:n], "X": Xbig.t()[:n], "prec": prec})
+        host.append((A, B, prec, Rbig, Xbig))
+    outs, st = ts.batch_solve(items, status=True)
+    assert st == [0] * len(items)
+    for (A, B, prec, Rbig, Xbig), (R, X) in zip(host, outs):
+        n = A.shape[1]
+        assert rel(to_host(X), oracle.lstsq(A, B)) <= 1e-10
+        assert rel(to_host(R), oracle.r_factor(A)) <= (1e-12 if prec == ts.FP64 else 1e-5)
+        # padding past the leading rows is untouched
+        assert torch.all(Rbig[:, n:] == 7.0) and torch.all(Xbig[:, n:] == 7.0)

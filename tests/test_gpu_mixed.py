@@ -78,3 +78,21 @@ def test_mixed_full_size_16M_by_32(cuda_lib):
                        info=True)
     Xo = oracle.lstsq(A, B)
     assert rel(to_host(X), Xo) <= TOL
+
+
+def test_mixed_strided_and_many_rhs(cuda_lib):
+    """lda > m, ldb > m, ldx > n, and k = 20 right-hand sides (three refinement groups)."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    m, n, k = 30_000, 40, 20
+    A = inputs.graded(m, n, 4.0, seed_g=3, seed_v=4)
+    B, _ = inputs.lstsq_rhs(A, k, 1e-6, 5)
+    Abig = torch.zeros((n, m + 11), dtype=torch.float64, device="cuda")
+    Abig[:, :m] = torch.from_numpy(np.ascontiguousarray(A.T))
+    Bbig = torch.zeros((k, m + 3), dtype=torch.float64, device="cuda")
+    Bbig[:, :m] = torch.from_numpy(np.ascontiguousarray(B.T))
+    Xbig = torch.full((k, n + 6), 5.0, dtype=torch.float64, device="cuda")
+    X = Xbig.t()[:n]
+    ts.lstsq(Abig.t()[:m], Bbig.t()[:m], prec=ts.MIXED, X=X)
+    assert rel(to_host(X), oracle.lstsq(A, B)) <= TOL
+    assert torch.all(Xbig[:, n:] == 5.0)
