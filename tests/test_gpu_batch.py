@@ -220,3 +220,21 @@ def test_batch_strided_layouts(cuda_lib):
         assert rel(to_host(R), oracle.r_factor(A)) <= (1e-12 if prec == ts.FP64 else 1e-5)
         # padding past the leading rows is untouched
         assert torch.all(Rbig[:, n:] == 7.0) and torch.all(Xbig[:, n:] == 7.0)
+
+
+@pytest.mark.parametrize("m,n,k,prec", [(1, 1, 1, 0), (1, 1, 1, 1), (7, 1, 3, 1), (128, 128, 0, 0), (128, 128, 0, 1),
+                                        (129, 128, 8, 1), (128, 120, 8, 0), (16, 16, 1, 1), (5000, 1, 0, 1),
+                                        (300, 64, 0, 2)])
+def test_batch_degenerate_shapes(cuda_lib, m, n, k, prec):
+    """Single-row and single-column problems, m = n (one tile, no tree), R-only mixed
+    items, k = 0 FP64 items; alone and next to an ordinary item."""
+    A = inputs.graded(m, n, 2.0, seed_g=m + n, seed_v=k + 3) if n > 1 else inputs.gaussian(m, n, m)
+    B = inputs.gaussian(m, k, m + 1) if k else None
+    other = make_items(1, 40, k=0)[0]
+    res, st = run([(A, B, prec), other])
+    assert st == [0, 0]
+    R, X = res[0]
+    tolr = 1e-12 if prec in (0, 2) else 1e-5
+    assert rel(R, oracle.r_factor(A)) <= tolr
+    if k:
+        assert rel(X, oracle.lstsq(A, B)) <= 1e-10
