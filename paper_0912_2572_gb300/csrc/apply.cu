@@ -141,7 +141,6 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jid = blockIdx.x * 4 + warp;
   if (jid >= njobs) return;  // warp-uniform; this kernel uses no block barrier
-  if (p.done && *p.done) return;
   const int n = p.n, ldt = p.ldt;
   R *Bt = sm + (size_t)warp * ((size_t)ldt + n) * K;  // tile rows, column-major
   R *PR = Bt + (size_t)ldt * K;                        // pivot rows, PR[c*n + j]
@@ -359,7 +358,6 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
   extern __shared__ __align__(16) unsigned char smraw[];
   R *sm = reinterpret_cast<R *>(smraw);
   constexpr int KC = 16 * CMAX;
-  if (p.done && *p.done) return;  // uniform over the grid
   const int n = p.n, ldt = p.ldt;
   const int col0 = p.col0 + blockIdx.y * KC;
   const int kc = min(KC, p.k - (int)blockIdx.y * KC);

@@ -690,11 +690,7 @@ int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved
   const size_t extra = factor_smem_bytes(nc, 0, elem);
   if (per_cta <= extra) return 0;
   int rows = (int)((per_cta - extra) / (elem * (size_t)nc));
-  rows = rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
-  // FP32: the two half-warps of a warp read neighbouring columns; an odd multiple of 16
-  // words between columns puts them on disjoint halves of the 32 shared-memory banks
-  if (elem == 4 && rows >= 32 && (rows & 31) == 0) rows -= 16;
-  return rows;
+  return rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
 }
 
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {

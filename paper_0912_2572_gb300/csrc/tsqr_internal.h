@@ -205,7 +205,6 @@ struct ApplyParamsT {
   int32_t job0;
   int32_t trans;     // 1: Q^T (forward order), 0: Q (reverse order)
   int32_t formq;     // 1: forming the thin Q (tiles start at zero, column j >= ref j only)
-  const int32_t *done;  // optional device flag: the launch does nothing when *done != 0
 };
 
 using ApplyParams = ApplyParamsT<double>;
