@@ -73,7 +73,7 @@ def parse(argv=None):
     p.add_argument("--arity", type=int, default=2)
     p.add_argument("--tree", default="two-level", choices=["two-level", "pure"])
     p.add_argument("--decades", type=float, default=6.0)
-    p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--sweep", default="", help="write a leaf-height x tree sweep (factor only) to this file")
