@@ -37,7 +37,7 @@ FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20
 # DRAM bytes (read + write) per row of the factorization's chain launch, from the ncu
 # capture in profiles/k_factor_tsqr_fp64_4194304x64.md (m = 1,048,576, n = 64: 1.043 GB);
 # traffic grows with the rows, so it is scaled by m. Valid for n = 64 and that kernel build.
-CHAIN_DRAM_BYTES_PER_ROW_N64 = (543.894272e6 + 498.112e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
+CHAIN_DRAM_BYTES_PER_ROW_N64 = (543.698176e6 + 497.892096e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
 def flops_step(m, n, k=1):

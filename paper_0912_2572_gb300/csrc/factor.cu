@@ -21,6 +21,9 @@
 //     warp-uniform branches, not predicates;
 //   * the scalar work of a step (one rsqrt, one division) runs on warp 0 while the
 //     other CTA resident on the SM keeps the FP64 pipe busy (2 CTAs/SM by design).
+#include <cstdint>
+#include <type_traits>
+
 #include "tsqr_internal.h"
 
 namespace tsqr {
@@ -28,6 +31,21 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
+
+// One warp copies cnt doubles, 16 bytes per lane access when both addresses are 16-byte
+// aligned (the caller's leading dimension decides), 8 bytes otherwise. LD loads one
+// element or pair from the source (read-only input, or an L2 read of data another CTA of
+// the same launch may have written).
+template <typename LD1, typename LD2>
+__device__ __forceinline__ void warp_copy(double *dst, const double *src, int cnt, int lane, LD1 ld1, LD2 ld2) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const int c2 = cnt >> 1;
+    for (int i = lane; i < c2; i += 32) reinterpret_cast<double2 *>(dst)[i] = ld2(reinterpret_cast<const double2 *>(src) + i);
+    if ((cnt & 1) && lane == 0) dst[cnt - 1] = ld1(src + cnt - 1);
+  } else {
+    for (int i = lane; i < cnt; i += 32) dst[i] = ld1(src + i);
+  }
+}
 
 // Transpose-reduce over the 16 lanes of a half-warp: each lane holds C partial sums
 // (C a power of two <= 16). Stage s exchanges half of the values with the lane whose
@@ -223,12 +241,20 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
     // stage the tile: GEQRT/TSQRT tiles come from A (first touch), TTQRT from V
     for (int c = warp; c < nc; c += kThreads / 32) {
       R *dst = T + (size_t)c * ldt;
-      if (c < n && kind != TTQRT) {  // input A is FP64; the FP32 path rounds on load
+      if (c < n && kind != TTQRT) {  // input A is FP64; an FP32 tile rounds on load
         const double *src = p.A + r0 + (int64_t)c * p.lda;
-        for (int i = lane; i < ht; i += 32) dst[i] = R(src[i]);
+        if constexpr (std::is_same<R, double>::value)
+          warp_copy(dst, src, ht, lane, [](const double *q) { return __ldg(q); },
+                    [](const double2 *q) { return __ldg(q); });
+        else
+          for (int i = lane; i < ht; i += 32) dst[i] = R(src[i]);
       } else {
         const R *src = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
-        for (int i = lane; i < ht; i += 32) dst[i] = __ldcg(src + i);
+        if constexpr (std::is_same<R, double>::value)
+          warp_copy(dst, src, ht, lane, [](const double *q) { return __ldcg(q); },
+                    [](const double2 *q) { return __ldcg(q); });
+        else
+          for (int i = lane; i < ht; i += 32) dst[i] = __ldcg(src + i);
       }
     }
     if (!ge)
@@ -299,7 +325,10 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
       R *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
       const R *src = T + (size_t)c * ldt;
       const int lim = (kind == TTQRT && c < n) ? max(0, min(ht, c + 1 - off)) : ht;
-      for (int i = lane; i < lim; i += 32) dst[i] = src[i];
+      if constexpr (std::is_same<R, double>::value)
+        warp_copy(dst, src, lim, lane, [](const double *q) { return *q; }, [](const double2 *q) { return *q; });
+      else
+        for (int i = lane; i < lim; i += 32) dst[i] = src[i];
     }
     __syncthreads();
   }
