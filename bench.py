@@ -45,6 +45,14 @@ def flops_step(m, n, k=1):
     return {"factor": f, "form_q": f, "apply_qt": 4.0 * m * n * k - 2.0 * n * n * k, "solve": float(n * n * k)}
 
 
+def measured_hbm_gbs():
+    """The copy bandwidth in MEASURED_PEAKS.json (written by the driver), or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def rank_max(x: float, world: int, device: str) -> float:
     """The largest x over all ranks of the process group (x itself on one rank)."""
     if world <= 1:
@@ -797,6 +805,8 @@ def bench_ours(args):
             "roofline": {"kernel": "k_factor (leaf/flat-chain launch)", "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (CHAIN_DRAM_BYTES_PER_ROW_N64 * m if n == 64 else None),
+                         "hbm_gbs": (CHAIN_DRAM_BYTES_PER_ROW_N64 * m / (chain_ms * 1e-3) / 1e9 if n == 64 else None),
+                         "hbm_peak_gbs": measured_hbm_gbs(),
                          "peak_source": "measured" if peak_measured > 0 else "derived",
                          "peak_note": f"FP64 DFMA measured live by tsqr_probe_fp64_peak (independent DFMA chains "
                                       f"on every SM): {peak_measured:.3f} TFLOP/s at {probe_mhz:.0f} MHz; derived {sms} SMs x "
