@@ -285,12 +285,14 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
  * Results are bitwise identical to solving the request alone with tsqr_batch_solve and
  * the same chain_tiles (the batched kernel is deterministic per item).
  *
- * tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, &srv)
+ * tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctas_per_sm, &srv)
  *   max_bytes    device-memory budget for in-flight requests' workspaces (bytes);
  *                <= 0 = half the device memory free at creation. A request larger than
  *                the whole budget runs alone once nothing else is in flight.
  *   max_batch    >= 1, requests per launch.   streams  1..16 batches in flight.
  *   chain_tiles  as for tsqr_batch_solve (0 = automatic).
+ *   ctas_per_sm  CTAs per SM of the persistent kernel: 0 = as many as fit (2), 1 = one,
+ *                leaving room on every SM for the other streams' refinement launches.
  *   Errors: TSQR_ERR_ARG, TSQR_ERR_OOM, TSQR_ERR_CUDA.
  * tsqr_server_submit(srv, item, &ticket)
  *   Validates the item (TSQR_ERR_ARG as tsqr_batch_solve, nothing queued) and queues a
@@ -307,7 +309,7 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
  */
 typedef struct tsqr_server tsqr_server;
 tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t streams, int32_t chain_tiles,
-                               tsqr_server **srv);
+                               int32_t ctas_per_sm, tsqr_server **srv);
 tsqr_status tsqr_server_submit(tsqr_server *srv, const tsqr_batch_item *item, int64_t *ticket);
 tsqr_status tsqr_server_poll(tsqr_server *srv, int32_t max, int64_t *tickets, double *latency_s,
                              int32_t *status, int32_t *count);

@@ -265,11 +265,12 @@ class Server:
     thread inside the library); this class only marshals arguments.
     """
 
-    def __init__(self, max_bytes: int = 0, max_batch: int = 256, streams: int = 2, chain_tiles: int = 0):
+    def __init__(self, max_bytes: int = 0, max_batch: int = 256, streams: int = 2, chain_tiles: int = 0,
+                 ctas_per_sm: int = 0):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
-        _lib.check(self._lib.tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctypes.byref(self._h)),
-                   "tsqr_server_create")
+        _lib.check(self._lib.tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctas_per_sm,
+                                                ctypes.byref(self._h)), "tsqr_server_create")
         self._live = {}
 
     def submit(self, item):

@@ -45,7 +45,7 @@ struct SrvSlot {
 struct tsqr_server {
   int device = 0;
   size_t budget = 0, used = 0;
-  int32_t max_batch = 256, chain_tiles = 0;
+  int32_t max_batch = 256, chain_tiles = 0, ctas_per_sm = 0;
   std::vector<SrvSlot> slots;
   std::mutex mu;
   std::condition_variable cv, cv_done;
@@ -104,7 +104,7 @@ static void server_loop(tsqr_server *S) {
       for (size_t i = 0; i < batch.size(); ++i) items[i] = batch[i].item;
       lk.unlock();
       tsqr_status st = tsqr::batch_solve_internal(items.data(), (int32_t)items.size(), S->chain_tiles, 0, sl.stream,
-                                                  nullptr, sl.hstatus, nullptr);
+                                                  nullptr, sl.hstatus, nullptr, S->ctas_per_sm);
       if (st != TSQR_OK)
         for (size_t i = 0; i < items.size(); ++i) sl.hstatus[i] = (int32_t)st;
       cudaEventRecord(sl.event, sl.stream);
@@ -128,8 +128,9 @@ static void server_loop(tsqr_server *S) {
 extern "C" {
 
 tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t streams, int32_t chain_tiles,
-                               tsqr_server **out) {
-  if (!out || max_batch < 1 || streams < 1 || streams > 16 || chain_tiles < 0) return TSQR_ERR_ARG;
+                               int32_t ctas_per_sm, tsqr_server **out) {
+  if (!out || max_batch < 1 || streams < 1 || streams > 16 || chain_tiles < 0 || ctas_per_sm < 0 || ctas_per_sm > 2)
+    return TSQR_ERR_ARG;
   *out = nullptr;
   tsqr_server *S = new (std::nothrow) tsqr_server();
   if (!S) return TSQR_ERR_OOM;
@@ -145,6 +146,7 @@ tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t str
   S->budget = max_bytes > 0 ? (size_t)max_bytes : free_b / 2;
   S->max_batch = max_batch;
   S->chain_tiles = chain_tiles;
+  S->ctas_per_sm = ctas_per_sm;
   S->slots.resize(streams);
   for (SrvSlot &sl : S->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -505,7 +505,7 @@ struct BatchBuild {
 };
 
 tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
-                        BatchBuild &b, int32_t max_steps = kRefineSteps) {
+                        BatchBuild &b, int32_t max_steps = kRefineSteps, int32_t ctas_per_sm = 0) {
   b.max_steps = max_steps;
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -550,7 +550,9 @@ tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t cha
     while (16 * b.cmax < nc) b.cmax *= 2;
     cps_min = std::min(cps_min, b.plans[q].ctas_per_sm);
   }
-  b.grid = di.sms * cps_min;
+  // ctas_per_sm = 1 leaves room on every SM for a CTA of another stream's kernel (the
+  // server overlaps one batch's refinement with the next batch's factorization)
+  b.grid = di.sms * (ctas_per_sm > 0 ? std::min(cps_min, (int)ctas_per_sm) : cps_min);
   // merged job table: chains of every item (largest first), then tree nodes
   struct Chain {
     double cost;
@@ -876,9 +878,9 @@ tsqr_status lstsq_mixed_batched(const tsqr_batch_item &it, int32_t arity, int32_
 
 tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
                                        int32_t arity, cudaStream_t s, int32_t *status, int32_t *status_async,
-                                       double *info) {
+                                       double *info, int32_t ctas_per_sm) {
   BatchBuild b;
-  tsqr_status st = batch_build(items, count, chain_tiles, arity, b);
+  tsqr_status st = batch_build(items, count, chain_tiles, arity, b, kRefineSteps, ctas_per_sm);
   if (st != TSQR_OK) return st;
   void *blk = nullptr;
   CUDA_TRY(pool_alloc(&blk, b.bytes, s));

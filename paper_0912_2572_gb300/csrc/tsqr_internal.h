@@ -181,7 +181,8 @@ cudaError_t launch_refine_batch(const RefineParams &p, int ntasks, size_t smem_b
 
 // host side of the batched path (tsqr_api.cu), also driven by the server (server.cu)
 tsqr_status batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
-                                 cudaStream_t s, int32_t *status, int32_t *status_async, double *info);
+                                 cudaStream_t s, int32_t *status, int32_t *status_async, double *info,
+                                 int32_t ctas_per_sm = 0);
 tsqr_status check_batch_item(const tsqr_batch_item &it, int32_t q);
 size_t batch_item_bytes(const tsqr_batch_item &it);  // device workspace estimate for admission
 int32_t resolve_batch_prec(const tsqr_batch_item &it);  // TSQR_FP64 or TSQR_MIXED

@@ -179,11 +179,12 @@ def test_tile_capacity_choice(lib):
 
 def test_server_entry_points_reject_bad_arguments(lib):
     h = ctypes.c_void_p()
-    assert lib.tsqr_server_create(0, 0, 2, 0, ctypes.byref(h)) == 1      # max_batch < 1
-    assert lib.tsqr_server_create(0, 16, 0, 0, ctypes.byref(h)) == 1     # no stream
-    assert lib.tsqr_server_create(0, 16, 17, 0, ctypes.byref(h)) == 1    # too many streams
-    assert lib.tsqr_server_create(0, 16, 2, -1, ctypes.byref(h)) == 1    # chain_tiles < 0
-    assert lib.tsqr_server_create(0, 16, 2, 0, None) == 1
+    assert lib.tsqr_server_create(0, 0, 2, 0, 0, ctypes.byref(h)) == 1      # max_batch < 1
+    assert lib.tsqr_server_create(0, 16, 0, 0, 0, ctypes.byref(h)) == 1     # no stream
+    assert lib.tsqr_server_create(0, 16, 17, 0, 0, ctypes.byref(h)) == 1    # too many streams
+    assert lib.tsqr_server_create(0, 16, 2, -1, 0, ctypes.byref(h)) == 1    # chain_tiles < 0
+    assert lib.tsqr_server_create(0, 16, 2, 0, 3, ctypes.byref(h)) == 1     # ctas_per_sm > 2
+    assert lib.tsqr_server_create(0, 16, 2, 0, 0, None) == 1
     assert not h.value
     c = ctypes.c_int32(0)
     assert lib.tsqr_server_submit(None, None, None) == 1
