@@ -353,8 +353,9 @@ __device__ __forceinline__ void update_dispatch(R *Bt, int ldt, int cs, int kc, 
   }
 }
 
-template <int CMAX, int RM, typename R>
-__global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile(const ApplyParamsT<R> p) {
+// MINB: CTAs per SM the launch is planned for (3 only with 144-row tiles, RM = 9).
+template <int CMAX, int RM, typename R, int MINB>
+__global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyParamsT<R> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R *sm = reinterpret_cast<R *>(smraw);
   constexpr int KC = 16 * CMAX;
@@ -467,24 +468,27 @@ __global__ void __launch_bounds__(kTileThreads, (RM <= 16 ? 2 : 1)) k_apply_tile
   }
 }
 
-template <int CMAX, int RM, typename R>
+template <int CMAX, int RM, typename R, int MINB>
 cudaError_t launch_tile_t(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   constexpr int KC = 16 * CMAX;
   const size_t bytes = sizeof(R) * ((size_t)KC * p.ldt + 2 * KC);
-  cudaError_t e = cudaFuncSetAttribute(k_apply_tile<CMAX, RM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_tile<CMAX, RM, R, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   dim3 grid(njobs, (p.k + KC - 1) / KC);
-  k_apply_tile<CMAX, RM, R><<<grid, kTileThreads, bytes, s>>>(p);
+  k_apply_tile<CMAX, RM, R, MINB><<<grid, kTileThreads, bytes, s>>>(p);
   return cudaGetLastError();
 }
 
+// Rows per lane (RM) sized to the tile; the three-CTA build exists for 144-row tiles.
 template <int CMAX, typename R>
-cudaError_t launch_tile_rm(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
+cudaError_t launch_tile_rm(const ApplyParamsT<R> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
   const int rows_per_lane = (p.ldt + 15) / 16;
-  if (rows_per_lane <= 8) return launch_tile_t<CMAX, 8, R>(p, njobs, s);
-  if (rows_per_lane <= 16) return launch_tile_t<CMAX, 16, R>(p, njobs, s);
-  return launch_tile_t<CMAX, 32, R>(p, njobs, s);
+  if (rows_per_lane <= 8) return launch_tile_t<CMAX, 8, R, 2>(p, njobs, s);
+  if (rows_per_lane <= 9)
+    return ctas_per_sm >= 3 ? launch_tile_t<CMAX, 9, R, 3>(p, njobs, s) : launch_tile_t<CMAX, 9, R, 2>(p, njobs, s);
+  if (rows_per_lane <= 16) return launch_tile_t<CMAX, 16, R, 2>(p, njobs, s);
+  return launch_tile_t<CMAX, 32, R, 1>(p, njobs, s);
 }
 
 template <int K, int RW, typename R>
@@ -504,7 +508,7 @@ cudaError_t launch_warp_k(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
 }
 
 template <typename R>
-cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
+cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
   if (njobs <= 0 || p.k <= 0) return cudaSuccess;
   if (p.ldt > 512) return cudaErrorInvalidValue;
   if (p.k <= 8 && !p.formq) {
@@ -520,15 +524,15 @@ cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, cudaStream_t s
     }
   }
   // up to 64 columns per pass; fewer columns use a narrower tile
-  if (p.k <= 16) return launch_tile_rm<1, R>(p, njobs, s);
-  if (p.k <= 32) return launch_tile_rm<2, R>(p, njobs, s);
-  return launch_tile_rm<4, R>(p, njobs, s);
+  if (p.k <= 16) return launch_tile_rm<1, R>(p, njobs, ctas_per_sm, s);
+  if (p.k <= 32) return launch_tile_rm<2, R>(p, njobs, ctas_per_sm, s);
+  return launch_tile_rm<4, R>(p, njobs, ctas_per_sm, s);
 }
 
 }  // namespace
 
-cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s) {
-  return launch_apply_any(p, njobs, s);
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm) {
+  return launch_apply_any(p, njobs, ctas_per_sm, s);
 }
 
 }  // namespace tsqr

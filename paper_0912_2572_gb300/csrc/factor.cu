@@ -554,8 +554,10 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
   __syncthreads();
 }
 
-template <int CMAX, typename R>
-__global__ void __launch_bounds__(kThreads, 2) k_factor(const FactorParamsT<R> p) {
+// MINB = CTAs resident per SM the launch is planned for (2, or 3 with shorter tiles: more
+// independent column-step sequences per SM hide more of each step's serial latency).
+template <int CMAX, typename R, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_factor(const FactorParamsT<R> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   run_job<CMAX, R>(p, p.jobs[p.job0 + blockIdx.x], smraw);
 }
@@ -682,23 +684,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
   }
 }
 
-template <int CMAX, typename R>
+template <int CMAX, typename R, int MINB>
 cudaError_t launch_factor_t(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
   const size_t bytes = factor_smem_bytes(p.nc, p.ldt, sizeof(R));
-  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  k_factor<CMAX, R><<<njobs, kThreads, bytes, s>>>(p);
+  k_factor<CMAX, R, MINB><<<njobs, kThreads, bytes, s>>>(p);
   return cudaGetLastError();
 }
 
+template <typename R, int MINB>
+cudaError_t launch_factor_c(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
+  if (p.nc <= 16) return launch_factor_t<1, R, MINB>(p, njobs, s);
+  if (p.nc <= 32) return launch_factor_t<2, R, MINB>(p, njobs, s);
+  if (p.nc <= 64) return launch_factor_t<4, R, MINB>(p, njobs, s);
+  return launch_factor_t<8, R, MINB>(p, njobs, s);
+}
+
 template <typename R>
-cudaError_t launch_factor_any(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
+cudaError_t launch_factor_any(const FactorParamsT<R> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  if (p.nc <= 16) return launch_factor_t<1, R>(p, njobs, s);
-  if (p.nc <= 32) return launch_factor_t<2, R>(p, njobs, s);
-  if (p.nc <= 64) return launch_factor_t<4, R>(p, njobs, s);
-  return launch_factor_t<8, R>(p, njobs, s);
+  if (ctas_per_sm >= 3) return launch_factor_c<R, 3>(p, njobs, s);
+  return launch_factor_c<R, 2>(p, njobs, s);
 }
 
 }  // namespace
@@ -722,8 +730,24 @@ int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved
   return rows >= 16 ? (rows & ~15) : (rows & ~7);  // multiples of 16 keep the half-warps full
 }
 
-cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {
-  return launch_factor_any(p, njobs, s);
+bool factor_tile_choice(int n, int nc, int leaf_h, size_t smem_per_sm, size_t reserved_per_block,
+                        size_t optin_per_block, int max_cps, int &tile_h, int &cps) {
+  for (int c = max_cps < 3 ? max_cps : 3; c >= 1; --c) {
+    int rows = factor_max_rows(nc, c, smem_per_sm, reserved_per_block, optin_per_block);
+    if (rows > 512) rows = 512;  // the apply kernels stage at most 512 rows per tile
+    // a third CTA per SM pays only while its tile still holds two triangles' worth of rows
+    const int need = (c >= 3) ? 2 * n : n;
+    if (rows >= need && rows >= 8) {
+      tile_h = rows < (leaf_h > n ? leaf_h : n) ? rows : (leaf_h > n ? leaf_h : n);
+      cps = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm) {
+  return launch_factor_any(p, njobs, ctas_per_sm, s);
 }
 
 cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s) {

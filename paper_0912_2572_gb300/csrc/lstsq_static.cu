@@ -120,14 +120,8 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return TSQR_ERR_CUDA;
   const int nc = n + k;
-  int cps = 2;
-  int tile_h = factor_max_rows(nc, 2, smem_sm, reserved, optin);
-  if (tile_h < n) {
-    cps = 1;
-    tile_h = factor_max_rows(nc, 1, smem_sm, reserved, optin);
-  }
-  if (tile_h > 512) tile_h = 512;
-  if (tile_h < n || tile_h < 8) return TSQR_ERR_UNSUPPORTED;
+  int cps = 0, tile_h = 0;
+  if (!factor_tile_choice(n, nc, 1 << 20, smem_sm, reserved, optin, 3, tile_h, cps)) return TSQR_ERR_UNSUPPORTED;
   int ntiles = 0, njobs = 0, nlaunches = 0;
   if (!build_plan(m, n, tile_h, (int64_t)sms * cps * 4, ntiles, njobs, nlaunches))
     return TSQR_ERR_UNSUPPORTED;
@@ -176,7 +170,7 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
   p.ldt = tile_h;
   for (int q = 0; q < nlaunches; ++q) {
     p.job0 = g_launches[q].job_begin;
-    STATIC_TRY(launch_factor(p, g_launches[q].job_count, s));
+    STATIC_TRY(launch_factor(p, g_launches[q].job_count, s, q == 0 ? cps : 2));
   }
   STATIC_TRY(launch_trsv(V, m, n, W, m, k, X, ldx, nullptr, status, s));
   int32_t hstatus = 0;

@@ -220,28 +220,22 @@ static int split_tree_tiles(Plan &pl, int h) {
 // Chooses the tile height and CTAs per SM of the factor kernel for nc columns: two
 // resident CTAs when the tile still holds at least n rows (one CTA's scalar phase is
 // then hidden behind the other's updates), otherwise one.
+// max_cps: the persistent batched kernel is built for two CTAs per SM; the one-problem
+// launches may run three.
 static bool choose_tiles(const DeviceInfo &di, int n, int nc, int leaf_h, int &tile_h, int &cps,
-                         size_t elem = sizeof(double)) {
+                         size_t elem = sizeof(double), int max_cps = 3) {
   if (elem == sizeof(float)) {  // register-tile FP32 chains: fixed 128-row tiles
     if (nc > 128) return false;
     tile_h = std::min(kF32TileRows, std::max(leaf_h, n));
     cps = 2;
     return true;
   }
-  for (int c = 2; c >= 1; --c) {
-    int rows = factor_max_rows(nc, c, di.smem_sm, di.reserved, di.optin, elem);
-    rows = std::min(rows, 512);  // the apply kernels stage at most 512 rows per tile
-    if (rows >= n && rows >= 8) {
-      tile_h = std::min(rows, std::max(leaf_h, n));
-      cps = c;
-      return true;
-    }
-  }
-  return false;
+  return factor_tile_choice(n, nc, leaf_h, di.smem_sm, di.reserved, di.optin, max_cps, tile_h, cps);
 }
 
 static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n, int nc, int leaf_h,
-                                int arity, int flags, bool mixed = false, int64_t chains_override = 0) {
+                                int arity, int flags, bool mixed = false, int64_t chains_override = 0,
+                                int max_cps = 3) {
   pl.m = m;
   pl.n = n;
   pl.nc = nc;
@@ -249,7 +243,7 @@ static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n
   pl.arity = arity;
   pl.flags = flags & TSQR_TWO_LEVEL;
   pl.mixed = mixed;
-  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double)))
+  if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double), max_cps))
     return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
   // four waves of chains: the apply kernels run one warp per chain, so fewer chains would
   // starve them (the batched path, which applies nothing, sets its own count)
@@ -393,7 +387,7 @@ static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, dou
     const LaunchDesc &ld = pl.launches[q];
     p.job0 = ld.job_begin;
     ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
-    CUDA_TRY(launch_factor(p, ld.job_count, s));
+    CUDA_TRY(launch_factor(p, ld.job_count, s, q == 0 ? pl.ctas_per_sm : 2));
   }
   return TSQR_OK;
 }
@@ -421,10 +415,11 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
     p.col0 = c0;
     p.k = std::min(group, k - c0);
     for (int q = 0; q < nl; ++q) {
-      const LaunchDesc &ld = pl.launches[trans ? q : nl - 1 - q];
+      const int li = trans ? q : nl - 1 - q;  // launch 0 holds the chains
+      const LaunchDesc &ld = pl.launches[li];
       p.job0 = ld.job_begin;
       ProfScope ps(formq ? TSQR_PROF_FORM_Q : (trans ? TSQR_PROF_APPLY_QT : TSQR_PROF_APPLY_Q), s);
-      CUDA_TRY(launch_apply(p, ld.job_count, s));
+      CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2));
     }
   }
   return TSQR_OK;
@@ -533,13 +528,13 @@ tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t cha
     const int nc = mixed ? it.n : it.n + it.k;
     const size_t elem = mixed ? sizeof(float) : sizeof(double);
     int th = 0, cps = 0;
-    if (!choose_tiles(di, it.n, nc, 1 << 20, th, cps, elem))
+    if (!choose_tiles(di, it.n, nc, 1 << 20, th, cps, elem, 2))
       return fail(TSQR_ERR_UNSUPPORTED, "item %d: no tile fits shared memory", q);
     const int64_t tiles = (it.m + th - 1) / th;
     // mixed items: FP32 chains kMixedChainFactor times longer (fewer FP64 tree combines)
     const int64_t Lq = mixed ? (int64_t)L * kMixedChainFactor : L;
     const int64_t G = std::max<int64_t>(1, (tiles + Lq / 2) / Lq);
-    tsqr_status st = make_plan_on(di, b.plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G);
+    tsqr_status st = make_plan_on(di, b.plans[q], it.m, it.n, nc, th, arity, TSQR_TWO_LEVEL, mixed, G, 2);
     if (st != TSQR_OK) return st;
     // tree nodes (FP64) in pieces that fit the chains' CTAs per SM
     const int node_rows = b.tree_rows[q] = split_tree_tiles(

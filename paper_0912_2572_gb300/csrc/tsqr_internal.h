@@ -90,9 +90,16 @@ constexpr int kF32TileRows = 16 * kF32Rpt;
 // Shared memory of a factor job: the tile plus its step buffers (FP64), or only the
 // step buffers of a register-tile FP32 chain (elem = 4).
 size_t factor_smem_bytes(int nc, int ldt, size_t elem = sizeof(double));
-cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s);
+// ctas_per_sm: CTAs per SM the tile height was planned for (3 selects the build that fits
+// three in the register file; anything else, two).
+cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2);
 int factor_max_rows(int nc, int ctas_per_sm, size_t smem_per_sm, size_t reserved_per_block,
                     size_t optin_per_block, size_t elem = sizeof(double));
+// Tile height and CTAs per SM of an FP64 factorization (nc columns, n of them A's, leaves
+// of leaf_h rows): three CTAs per SM where their tile still holds 2n rows (more
+// independent column steps in flight per SM), else two, else one; at most max_cps.
+bool factor_tile_choice(int n, int nc, int leaf_h, size_t smem_per_sm, size_t reserved_per_block,
+                        size_t optin_per_block, int max_cps, int &tile_h, int &cps);
 
 // ---------------------------------------------------------- batched persistent kernel
 // One launch factors every instance of a batch: CTAs take chain jobs from an atomic queue;
@@ -210,7 +217,7 @@ struct ApplyParamsT {
 
 using ApplyParams = ApplyParamsT<double>;
 
-cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s);
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2);
 
 // ------------------------------------------------------------------- small kernels
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,

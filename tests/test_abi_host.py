@@ -164,14 +164,18 @@ def test_two_level_tree(lib, m, n, h, arity):
 
 
 def test_tile_capacity_choice(lib):
-    # n = 64: two CTAs per SM fit a 224-row tile; n = 128 needs one CTA per SM
+    # n = 64: three CTAs per SM fit a 144-row tile (>= 2n rows, so the third CTA is taken);
+    # n = 96: a three-CTA tile would hold 96 rows < 2n, so two CTAs with 144 rows;
+    # n = 128 needs one CTA per SM
     info, _, _ = describe(lib, 100_000, 64, 1024, 2, 2)
-    assert info["cps"] == 2 and info["tile_rows"] == 224
+    assert info["cps"] == 3 and info["tile_rows"] == 144
+    info, _, _ = describe(lib, 100_000, 96, 1024, 2, 2)
+    assert info["cps"] == 2 and info["tile_rows"] == 144
     info, _, _ = describe(lib, 100_000, 128, 1024, 2, 2)
     assert info["cps"] == 1 and info["tile_rows"] >= 128
     # the fused least-squares factorization sees n + k columns
     info, _, _ = describe(lib, 100_000, 64, 1024, 2, 2, nc=72)
-    assert info["tile_rows"] < 224
+    assert info["cps"] == 3 and info["tile_rows"] == 128
     # the leaf height caps the tile
     info, _, _ = describe(lib, 100_000, 16, 100, 2, 0)
     assert info["tile_rows"] == 100
