@@ -390,6 +390,12 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
     if (!ge)
       for (int c = tid; c < kc; c += kTileThreads) PV[c] = __ldcg(bp(pr + j0, c));
     R xv[RM], xn[RM];
+    // warp 0 holds the current reflector's scalars and loads the next one's a step ahead
+    R tau = R(0), sc = R(0), tau_n = R(0), sc_n = R(0);
+    if (warp == 0) {
+      tau = __ldg(p.tau + td.refl + j0);
+      sc = __ldg(p.scl + td.refl + j0);
+    }
     {
       int lo, hi;
       refl_rows(kind, j0, ht, lo, hi, td.off);
@@ -410,6 +416,10 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
       const int cs = p.formq ? max(0, j - col0) : 0;  // first column this reflector touches
       // prefetch the next reflector's tail (registers) and pivot row (warp 1)
       if (more) {
+        if (warp == 0) {
+          tau_n = __ldg(p.tau + td.refl + jn);
+          sc_n = __ldg(p.scl + td.refl + jn);
+        }
         int lo2, hi2;
         refl_rows(kind, jn, ht, lo2, hi2, td.off);
 #pragma unroll
@@ -431,8 +441,6 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
         dots_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
         __syncthreads();
         if (warp == 0) {
-          const R tau = __ldg(p.tau + td.refl + j);
-          const R sc = __ldg(p.scl + td.refl + j);
           const R ts = tau * sc;
           for (int c = cs + lane; c < kc; c += 32) {
             const R piv = ge ? Bt[(size_t)c * ldt + j] : PV[c];
@@ -457,6 +465,8 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
       }
 #pragma unroll
       for (int r = 0; r < RM; ++r) xv[r] = xn[r];
+      tau = tau_n;
+      sc = sc_n;
       __syncthreads();
     }
     for (int c = warp; c < kc; c += kTileThreads / 32) {

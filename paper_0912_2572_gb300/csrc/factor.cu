@@ -6,12 +6,13 @@
 // a leaf) or row j of the job's running triangle R held in global memory (TSQRT: the
 // flat-tree step [R; tile], TTQRT: the tree combine [R; R_child], paper §2.3).
 //
-// GB300 design notes. FP64 runs on a narrow pipe (2 DFMA/clk/SM, one warp instruction
-// per 16 cycles per SM) and a warp instruction costs the same with masked lanes, so the
-// kernel keeps warps full and spends FP64 issue slots only on the update itself:
-//   * per column step j the dot products p_k = sum_i b_ij b_ik (k >= j, including the
-//     squared norm at k = j) are one fused Gram-row pass, so one reduction per step;
-//   * half-warp h owns column pairs; each lane walks 1/16 of the rows, so a value is
+// GB300 design notes. FP64 runs on a narrow pipe (2 DFMA/clk/SM: each of the four SM
+// sub-partitions takes one FP64 warp instruction per 64 cycles) and a warp instruction
+// costs the same with masked lanes, so the kernel keeps warps full, spends FP64 issue
+// slots only on the factorization itself, and spreads them evenly over sub-partitions:
+//   * per column step j the dot products p_k = sum_i b_ij b_ik (k > j) are one Gram-row
+//     pass, so one reduction per step;
+//   * a worker half-warp owns columns; each lane walks 1/16 of the rows, so a value is
 //     reduced over only 16 lanes, by a transpose-reduce that spends about one DADD per
 //     value instead of four;
 //   * reflectors are stored unscaled with (tau, scale) beside them, so the update of a
@@ -19,8 +20,9 @@
 //   * every warp issues exactly as many column slots as it owns at each step: a
 //     predicated-off DFMA still occupies the FP64 pipe, so the column guards are
 //     warp-uniform branches, not predicates;
-//   * the scalar work of a step (one rsqrt, one division) runs on warp 0 while the
-//     other CTA resident on the SM keeps the FP64 pipe busy (2 CTAs/SM by design).
+//   * the reflector's scalar chain runs on its own warp, overlapped with the dot
+//     products (run_job below), and the column dealing rotates with the step so that no
+//     sub-partition's FP64 pipe carries more than its share.
 #include <cstdint>
 #include <type_traits>
 
@@ -79,15 +81,28 @@ __device__ __forceinline__ R treduce16(R (&v)[C], int hl, int &idx) {
 
 __host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
 
-// Gram row of step j: Pg[c] = sum_{i in [lo,hi)} T[j][i] T[c][i] for c in [j, nc) (c = j
-// is the squared norm of the pivot column's tail). Half-warp hw owns columns
-// j + hw + 16 t; this warp has exactly NS slots (t < NS), so no predicated-off DFMA is
-// issued; only half-warp 1 of the last slot can fall past nc.
+// Column slots. The FP64 job's column work is dealt to 14 worker half-warps (warps 0..6;
+// warp 7 is the scalar warp): worker rank v (0..13) owns columns cs + v + 14 t. The rank
+// of a warp rotates with the step, so the warp that takes the extra slot of an uneven
+// step changes from step to step: a CTA's warp w always runs on SM sub-partition w mod 4,
+// and with a fixed order the same sub-partition's FP64 pipe would carry the extra slots
+// of every CTA on the SM.
+constexpr int kColHalfWarps = 14;
+constexpr int kWorkerWarps = kColHalfWarps / 2;
+
+__host__ __device__ constexpr int job_nc_max(int cmax) { return cmax > 8 ? 144 : 16 * cmax; }
+__host__ __device__ constexpr int job_slots_max(int cmax) {
+  return (job_nc_max(cmax) + kColHalfWarps - 1) / kColHalfWarps;
+}
+
+// Gram row of step j: Pg[c] = sum_{i in [lo,hi)} T[j][i] T[c][i] for c = cs + v + 14 t
+// (t < NS), v this half-warp's worker rank. The warp issues exactly its NS slots, so no
+// predicated-off DFMA is issued; only half-warp 1 of the last slot can fall past nc.
 template <int NS, typename R>
-__device__ __forceinline__ void gram_row(const R *__restrict__ T, int ldt, int j, int nc, int lo,
-                                         int hi, int hw, int hl, R *__restrict__ Pg) {
+__device__ __forceinline__ void gram_row(const R *__restrict__ T, int ldt, int j, int cs, int nc, int lo,
+                                         int hi, int v, int hl, R *__restrict__ Pg) {
   constexpr int C = pow2ceil(NS);
-  const int cb = j + hw;
+  const int cb = cs + v;
   R acc[C];
 #pragma unroll
   for (int t = 0; t < C; ++t) acc[t] = R(0);
@@ -96,26 +111,25 @@ __device__ __forceinline__ void gram_row(const R *__restrict__ T, int ldt, int j
     const R x = Tj[i];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-      const int c = cb + 16 * t;
+      const int c = cb + kColHalfWarps * t;
       if (t < NS - 1 || c < nc) acc[t] = fma(x, T[(size_t)c * ldt + i], acc[t]);
     }
   }
   int idx;
   const R s = treduce16<C, R>(acc, hl, idx);
-  const int c = cb + 16 * idx;
+  const int c = cb + kColHalfWarps * idx;
   if ((hl & (16 / C - 1)) == 0 && idx < NS && c < nc) Pg[c] = s;
 }
 
-// Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c in (j, nc), i in [lo, hi);
-// half-warp hw owns columns j + 1 + hw + 16 t, this warp has exactly NS slots.
+// Trailing update of step j: T[c][i] -= CF[c] * T[j][i] for c = cs + v + 14 t, i in [lo, hi).
 template <int NS, typename R>
-__device__ __forceinline__ void trailing_update(R *__restrict__ T, int ldt, int j, int nc, int lo,
-                                                int hi, int hw, int hl, const R *__restrict__ CF) {
-  const int cb = j + 1 + hw;
+__device__ __forceinline__ void trailing_update(R *__restrict__ T, int ldt, int j, int cs, int nc, int lo,
+                                                int hi, int v, int hl, const R *__restrict__ CF) {
+  const int cb = cs + v;
   R cf[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
-    const int c = cb + 16 * t;
+    const int c = cb + kColHalfWarps * t;
     cf[t] = (c < nc) ? CF[c] : R(0);
   }
   const R *Tj = T + (size_t)j * ldt;
@@ -123,7 +137,7 @@ __device__ __forceinline__ void trailing_update(R *__restrict__ T, int ldt, int 
     const R x = Tj[i];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-      const int c = cb + 16 * t;
+      const int c = cb + kColHalfWarps * t;
       if (t < NS - 1 || c < nc) {
         R *q = T + (size_t)c * ldt + i;
         *q = fma(-cf[t], x, *q);
@@ -132,45 +146,45 @@ __device__ __forceinline__ void trailing_update(R *__restrict__ T, int ldt, int 
   }
 }
 
-// The warp's slot count: the first column of half-warp 0 is cs + 2*warp.
-__device__ __forceinline__ int warp_slots(int cs, int nc, int warp) {
-  const int r = nc - cs - 2 * warp;
-  return r <= 0 ? 0 : (r + 15) >> 4;
+// Slots of the worker warp of rank rw (its half-warps have ranks 2 rw and 2 rw + 1).
+__device__ __forceinline__ int worker_slots(int cs, int nc, int rw) {
+  const int r = nc - cs - 2 * rw;
+  return r <= 0 ? 0 : (r + kColHalfWarps - 1) / kColHalfWarps;
+}
+
+// Runs OP<NS>(...) for the warp's exact slot count (1..11, at most job_slots_max(CMAX)).
+#define TSQR_SLOT_CASES(OP, NSMAX, ARGS)                                                    \
+  switch (ns) {                                                                           \
+    case 1: OP<1, R> ARGS; return;                                                        \
+    case 2: if (NSMAX >= 2) OP<(NSMAX >= 2 ? 2 : 1), R> ARGS; return;                    \
+    case 3: if (NSMAX >= 3) OP<(NSMAX >= 3 ? 3 : 1), R> ARGS; return;                    \
+    case 4: if (NSMAX >= 4) OP<(NSMAX >= 4 ? 4 : 1), R> ARGS; return;                    \
+    case 5: if (NSMAX >= 5) OP<(NSMAX >= 5 ? 5 : 1), R> ARGS; return;                    \
+    case 6: if (NSMAX >= 6) OP<(NSMAX >= 6 ? 6 : 1), R> ARGS; return;                    \
+    case 7: if (NSMAX >= 7) OP<(NSMAX >= 7 ? 7 : 1), R> ARGS; return;                    \
+    case 8: if (NSMAX >= 8) OP<(NSMAX >= 8 ? 8 : 1), R> ARGS; return;                    \
+    case 9: if (NSMAX >= 9) OP<(NSMAX >= 9 ? 9 : 1), R> ARGS; return;                    \
+    case 10: if (NSMAX >= 10) OP<(NSMAX >= 10 ? 10 : 1), R> ARGS; return;                \
+    case 11: if (NSMAX >= 11) OP<(NSMAX >= 11 ? 11 : 1), R> ARGS; return;                \
+    default: return;                                                                      \
+  }
+
+template <int CMAX, typename R>
+__device__ __forceinline__ void gram_row_dispatch(const R *T, int ldt, int j, int cs, int nc, int lo, int hi,
+                                                  int v, int hl, int rw, R *Pg) {
+  constexpr int NM = job_slots_max(CMAX);
+  const int ns = worker_slots(cs, nc, rw);
+  TSQR_SLOT_CASES(gram_row, NM, (T, ldt, j, cs, nc, lo, hi, v, hl, Pg))
 }
 
 template <int CMAX, typename R>
-__device__ __forceinline__ void gram_row_dispatch(const R *T, int ldt, int j, int nc, int lo, int hi,
-                                                  int hw, int hl, int warp, R *Pg) {
-  switch (warp_slots(j, nc, warp)) {
-    case 0: return;
-    case 1: gram_row<1, R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 2: if (CMAX >= 2) gram_row<(CMAX >= 2 ? 2 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 3: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 3 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 4: if (CMAX >= 4) gram_row<(CMAX >= 4 ? 4 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 5: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 6: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 7: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    case 8: if (CMAX >= 8) gram_row<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-    default: if (CMAX >= 16) gram_row<(CMAX >= 16 ? 9 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, Pg); return;
-  }
+__device__ __forceinline__ void update_dispatch(R *T, int ldt, int j, int cs, int nc, int lo, int hi, int v,
+                                                int hl, int rw, const R *CF) {
+  constexpr int NM = job_slots_max(CMAX);
+  const int ns = worker_slots(cs, nc, rw);
+  TSQR_SLOT_CASES(trailing_update, NM, (T, ldt, j, cs, nc, lo, hi, v, hl, CF))
 }
-
-template <int CMAX, typename R>
-__device__ __forceinline__ void update_dispatch(R *T, int ldt, int j, int nc, int lo, int hi, int hw,
-                                                int hl, int warp, const R *CF) {
-  switch (warp_slots(j + 1, nc, warp)) {
-    case 0: return;
-    case 1: trailing_update<1, R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 2: if (CMAX >= 2) trailing_update<(CMAX >= 2 ? 2 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 3: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 3 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 4: if (CMAX >= 4) trailing_update<(CMAX >= 4 ? 4 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 5: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 5 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 6: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 6 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 7: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 7 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    case 8: if (CMAX >= 8) trailing_update<(CMAX >= 8 ? 8 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-    default: if (CMAX >= 16) trailing_update<(CMAX >= 16 ? 9 : 1), R>(T, ldt, j, nc, lo, hi, hw, hl, CF); return;
-  }
-}
+#undef TSQR_SLOT_CASES
 
 // Scalars of the reflector that maps x = [alpha; tail], ||tail||^2 = s2, onto beta e_1
 // (Golub & Van Loan's sign choice, beta = -sign(alpha) ||x||, sign(0) = +1), in the form
@@ -208,27 +222,47 @@ __device__ __forceinline__ Refl<R> reflector(R alpha, R s2) {
   return r;
 }
 
-// One job: the tiles of a chain or a tree node, run by the whole CTA (256 threads) in the
-// shared-memory buffer smraw. Reads of V and B go through L2 (ld.global.cg): in the
+// One FP64 job: the tiles of a chain or a tree node, run by the whole CTA (256 threads) in
+// the shared-memory buffer smraw. Reads of V and B go through L2 (ld.global.cg): in the
 // persistent batched kernel they may have been written by another CTA of the same launch.
-template <int CMAX, typename R>
-__device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc job, unsigned char *smraw) {
+//
+// Warp 7 is the scalar warp. A step's reflector (the pivot column's norm, one rsqrt, one
+// division) is a chain of about twenty dependent FP64 instructions, each waiting for the
+// FP64 pipe behind the other warps' DFMA streams; run between the dot products and the
+// update it took a quarter of every column step. Here the scalar warp computes the norm
+// and the reflector *while* the worker warps compute the step's dot products, so only
+// the two-deep coefficient step (w = p_k + scale g_k; coefficient ts w; new pivot entry
+// p_k - tau w) separates the dot products from the update. The hand-offs are
+// producer/consumer named barriers (bar.arrive / bar.sync); the end of the update is a
+// full barrier (the next norm and dot products read column j + 1).
+constexpr int kScalarWarp = kWorkerWarps;
+static_assert(kThreads == 32 * (kWorkerWarps + 1), "seven worker warps and the scalar warp");
+
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <int CMAX>
+__device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const JobDesc job, unsigned char *smraw) {
+  using R = double;
   R *sm = reinterpret_cast<R *>(smraw);
   const int n = p.n, nc = p.nc, ldt = p.ldt;
   const int ncp = (nc + 7) & ~7;
   R *T = sm;                            // tile, column-major, nc columns of ldt rows
-  R *PC = T + (size_t)nc * ldt;         // Gram row of the step, then (in place) the
-                                        // update coefficients tau*scale*w_k
-  R *PV = PC + ncp;                     // staged pivot row (TSQRT / TTQRT)
+  R *PC = T + (size_t)nc * ldt;         // the step's dot products (workers -> scalar warp),
+                                        // turned in place into update coefficients
+  R *PV = PC + ncp;                     // staged pivot row (TSQRT / TTQRT; scalar warp only)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int hw = tid >> 4, hl = tid & 15;
+  const bool sw = (warp == kScalarWarp);
+  const int hl = tid & 15, hsub = (tid >> 4) & 1;
   const int64_t pr = job.piv_row;
-
-  // pivot-row element (row pr + j, column c) in global memory
   auto piv_ptr = [&](int j, int c) -> R * {
     return (c < n) ? p.V + pr + j + (int64_t)c * p.ldv : p.B + pr + j + (int64_t)(c - n) * p.ldb;
   };
-  constexpr int PFN = (CMAX > 8 ? 144 + 31 : CMAX * 16 + 31) / 32;  // columns after the pivot
+  constexpr int PCN = (job_nc_max(CMAX) + 31) / 32;  // columns after the pivot, per lane
 
   for (int tt = 0; tt < job.tile_count; ++tt) {
     const TileDesc td = p.tiles[job.tile_begin + tt];
@@ -241,20 +275,14 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
     // stage the tile: GEQRT/TSQRT tiles come from A (first touch), TTQRT from V
     for (int c = warp; c < nc; c += kThreads / 32) {
       R *dst = T + (size_t)c * ldt;
-      if (c < n && kind != TTQRT) {  // input A is FP64; an FP32 tile rounds on load
+      if (c < n && kind != TTQRT) {
         const double *src = p.A + r0 + (int64_t)c * p.lda;
-        if constexpr (std::is_same<R, double>::value)
-          warp_copy(dst, src, ht, lane, [](const double *q) { return __ldg(q); },
-                    [](const double2 *q) { return __ldg(q); });
-        else
-          for (int i = lane; i < ht; i += 32) dst[i] = R(src[i]);
+        warp_copy(dst, src, ht, lane, [](const double *q) { return __ldg(q); },
+                  [](const double2 *q) { return __ldg(q); });
       } else {
         const R *src = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
-        if constexpr (std::is_same<R, double>::value)
-          warp_copy(dst, src, ht, lane, [](const double *q) { return __ldcg(q); },
-                    [](const double2 *q) { return __ldcg(q); });
-        else
-          for (int i = lane; i < ht; i += 32) dst[i] = __ldcg(src + i);
+        warp_copy(dst, src, ht, lane, [](const double *q) { return __ldcg(q); },
+                  [](const double2 *q) { return __ldcg(q); });
       }
     }
     if (!ge)
@@ -268,33 +296,51 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
     for (int j = j0; j < n; ++j) {
       int lo, hi;
       refl_rows(kind, j, ht, lo, hi, off);
-      // warp 1 prefetches pivot row j+1 (not written before step j+1)
-      R pf[PFN];
-      const bool do_pf = (!ge) && warp == 1 && (j + 1 < n);
-      if (do_pf) {
-#pragma unroll
-        for (int q = 0; q < PFN; ++q) {
-          const int c = j + 1 + lane + 32 * q;
-          pf[q] = (c < nc) ? __ldcg(piv_ptr(j + 1, c)) : R(0);
+      if (!sw) {
+        const int rw = (warp + j) % kWorkerWarps;  // this step's worker rank
+        const int v = 2 * rw + hsub;
+        gram_row_dispatch<CMAX, R>(T, ldt, j, j + 1, nc, lo, hi, v, hl, rw, PC);
+        bar_arrive_n(1, kThreads);
+        bar_sync_n(2, kThreads);
+        update_dispatch<CMAX, R>(T, ldt, j, j + 1, nc, lo, hi, v, hl, rw, PC);
+      } else {
+        // squared norm of the pivot column's tail (two partial sums per lane), then the reflector
+        const R *Tj = T + (size_t)j * ldt;
+        R a0 = R(0), a1 = R(0);
+        int i = lo + lane;
+        for (; i + 32 < hi; i += 64) {
+          const R x0 = Tj[i], x1 = Tj[i + 32];
+          a0 = fma(x0, x0, a0);
+          a1 = fma(x1, x1, a1);
         }
-      }
-
-      gram_row_dispatch<CMAX, R>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
-      __syncthreads();
-
-      if (warp == 0) {
-        // every lane computes the (warp-uniform) scalars: a warp instruction costs the
-        // same with one active lane or 32
-        const Refl<R> rf = reflector<R>(ge ? T[(size_t)j * ldt + j] : PV[j], PC[j]);
-        for (int c = j + 1 + lane; c < nc; c += 32) {
-          const R pk = ge ? T[(size_t)c * ldt + j] : PV[c];
-          const R w = fma(rf.scale, PC[c], pk);  // v^T x over pivot row + tail
-          const R npk = fma(-rf.tau, w, pk);
-          PC[c] = rf.ts * w;
-          if (ge)
-            T[(size_t)c * ldt + j] = npk;
-          else
-            *piv_ptr(j, c) = npk;
+        if (i < hi) a0 = fma(Tj[i], Tj[i], a0);
+        R s2 = a0 + a1;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) s2 += __shfl_xor_sync(kFull, s2, m);
+        const Refl<R> rf = reflector<R>(ge ? Tj[j] : PV[j], s2);
+        bar_sync_n(1, kThreads);  // the workers' dot products are in PC
+        R pk[PCN];
+#pragma unroll
+        for (int q = 0; q < PCN; ++q) {
+          const int c = j + 1 + lane + 32 * q;
+          if (c < nc) {
+            const R p0 = ge ? T[(size_t)c * ldt + j] : PV[c];
+            const R w = fma(rf.scale, PC[c], p0);
+            PC[c] = rf.ts * w;
+            pk[q] = fma(-rf.tau, w, p0);
+          }
+        }
+        bar_arrive_n(2, kThreads);  // the coefficients are in PC
+        // the new pivot row and the reflector's scalars, then the next pivot row's staging
+#pragma unroll
+        for (int q = 0; q < PCN; ++q) {
+          const int c = j + 1 + lane + 32 * q;
+          if (c < nc) {
+            if (ge)
+              T[(size_t)c * ldt + j] = pk[q];
+            else
+              *piv_ptr(j, c) = pk[q];
+          }
         }
         if (lane == 0) {
           if (ge)
@@ -304,16 +350,14 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
           p.tau[td.refl + j] = rf.tau;
           p.scl[td.refl + j] = rf.scale;
         }
-      }
-      __syncthreads();
-
-      update_dispatch<CMAX, R>(T, ldt, j, nc, lo, hi, hw, hl, warp, PC);
-      if (do_pf) {
+        if (!ge && j + 1 < n) {
 #pragma unroll
-        for (int q = 0; q < PFN; ++q) {
-          const int c = j + 1 + lane + 32 * q;
-          if (c < nc) PV[c] = pf[q];
+          for (int q = 0; q < PCN; ++q) {
+            const int c = j + 1 + lane + 32 * q;
+            if (c < nc) PV[c] = __ldcg(piv_ptr(j + 1, c));
+          }
         }
+        __syncwarp();
       }
       __syncthreads();
     }
@@ -325,10 +369,7 @@ __device__ __forceinline__ void run_job(const FactorParamsT<R> &p, const JobDesc
       R *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
       const R *src = T + (size_t)c * ldt;
       const int lim = (kind == TTQRT && c < n) ? max(0, min(ht, c + 1 - off)) : ht;
-      if constexpr (std::is_same<R, double>::value)
-        warp_copy(dst, src, lim, lane, [](const double *q) { return *q; }, [](const double2 *q) { return *q; });
-      else
-        for (int i = lane; i < lim; i += 32) dst[i] = src[i];
+      warp_copy(dst, src, lim, lane, [](const double *q) { return *q; }, [](const double2 *q) { return *q; });
     }
     __syncthreads();
   }
@@ -556,10 +597,10 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
 
 // MINB = CTAs resident per SM the launch is planned for (2, or 3 with shorter tiles: more
 // independent column-step sequences per SM hide more of each step's serial latency).
-template <int CMAX, typename R, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_factor(const FactorParamsT<R> p) {
+template <int CMAX, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_factor(const FactorParamsT<double> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  run_job<CMAX, R>(p, p.jobs[p.job0 + blockIdx.x], smraw);
+  run_job<CMAX>(p, p.jobs[p.job0 + blockIdx.x], smraw);
 }
 
 
@@ -663,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.n = in.n;
         fp.nc = in.n + in.k;
         fp.ldt = chain ? in.ldt : in.ldt_tree;
-        run_job<CMAX, double>(fp, jd, smraw);
+        run_job<CMAX>(fp, jd, smraw);
       }
       if (bj.parent < 0) {
         __threadfence();
@@ -684,29 +725,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
   }
 }
 
-template <int CMAX, typename R, int MINB>
-cudaError_t launch_factor_t(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
-  const size_t bytes = factor_smem_bytes(p.nc, p.ldt, sizeof(R));
-  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int CMAX, int MINB>
+cudaError_t launch_factor_t(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {
+  const size_t bytes = factor_smem_bytes(p.nc, p.ldt, sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(k_factor<CMAX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  k_factor<CMAX, R, MINB><<<njobs, kThreads, bytes, s>>>(p);
+  k_factor<CMAX, MINB><<<njobs, kThreads, bytes, s>>>(p);
   return cudaGetLastError();
 }
 
-template <typename R, int MINB>
-cudaError_t launch_factor_c(const FactorParamsT<R> &p, int njobs, cudaStream_t s) {
-  if (p.nc <= 16) return launch_factor_t<1, R, MINB>(p, njobs, s);
-  if (p.nc <= 32) return launch_factor_t<2, R, MINB>(p, njobs, s);
-  if (p.nc <= 64) return launch_factor_t<4, R, MINB>(p, njobs, s);
-  return launch_factor_t<8, R, MINB>(p, njobs, s);
+template <int MINB>
+cudaError_t launch_factor_c(const FactorParamsT<double> &p, int njobs, cudaStream_t s) {
+  if (p.nc <= 16) return launch_factor_t<1, MINB>(p, njobs, s);
+  if (p.nc <= 32) return launch_factor_t<2, MINB>(p, njobs, s);
+  if (p.nc <= 64) return launch_factor_t<4, MINB>(p, njobs, s);
+  return launch_factor_t<8, MINB>(p, njobs, s);
 }
 
-template <typename R>
-cudaError_t launch_factor_any(const FactorParamsT<R> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_factor_any(const FactorParamsT<double> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  if (ctas_per_sm >= 3) return launch_factor_c<R, 3>(p, njobs, s);
-  return launch_factor_c<R, 2>(p, njobs, s);
+  if (ctas_per_sm >= 3) return launch_factor_c<3>(p, njobs, s);
+  return launch_factor_c<2>(p, njobs, s);
 }
 
 }  // namespace
