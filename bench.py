@@ -34,10 +34,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TSQR Gflop/s & %roofline (4M×64 fp64); served LSQ solves/s, p99 vs plain path"
 FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20 TFLOP/s at 2.0 GHz)
-# DRAM bytes (read + write) per row of the factorization's chain launch, from the ncu
-# capture in profiles/k_factor_tsqr_fp64_4194304x64.md (m = 1,048,576, n = 64: 1.043 GB);
-# traffic grows with the rows, so it is scaled by m. Valid for n = 64 and that kernel build.
-CHAIN_DRAM_BYTES_PER_ROW_N64 = (543.698176e6 + 497.892096e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
+# DRAM bytes (read + write) per row of the factorization's chain launch, from an ncu
+# capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum at m = 1,048,576,
+# n = 64, 144-row tiles: 1.050 GB); traffic grows with the rows, so it is scaled by m.
+# Valid for n = 64 and that kernel build.
+CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.020288e6 + 503.156224e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
 def flops_step(m, n, k=1):

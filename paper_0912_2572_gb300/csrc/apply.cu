@@ -262,7 +262,10 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
 // pass) is staged in shared memory, the pivot row of each reflector is staged from
 // global memory (prefetched one reflector ahead), and the reflector tail is prefetched
 // into registers (every half-warp reads the same rows, so the loads hit L1). Half-warp hw
-// owns columns cs + hw + 16 t; each warp issues exactly its own slots.
+// owns columns cs + hw + 16 t; each warp issues exactly its own slots. The half-warp
+// ranks rotate with the reflector: a CTA's warp w always runs on SM sub-partition w mod 4,
+// and with a fixed order the lowest warps, which take the extra slots of uneven steps,
+// would load the same sub-partition's FP64 pipe in every CTA on the SM.
 constexpr int kTileThreads = 256;
 
 
@@ -437,8 +440,11 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
           pf[u] = (c < kc) ? __ldcg(bp(pr + jn, c)) : R(0);
         }
       }
+      // this reflector's rank of the warp; warp 0 keeps the scalar phase
+      const int rw = (warp + s) & 7;
+      const int hr = 2 * rw + (hw & 1);
       if (cs < kc) {
-        dots_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
+        dots_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hr, hl, rw, xv, PC);
         __syncthreads();
         if (warp == 0) {
           const R ts = tau * sc;
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
           }
         }
         __syncthreads();
-        update_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hw, hl, warp, xv, PC);
+        update_dispatch<CMAX, RM, R>(Bt, ldt, cs, kc, lo, hi, hr, hl, rw, xv, PC);
       }
       if (do_pf) {
 #pragma unroll
