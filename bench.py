@@ -85,6 +85,7 @@ def parse(argv=None):
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="skip the factorization autotuner report")
     p.add_argument("--sweep", default="", help="write a leaf-height x tree sweep (factor only) to this file")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
@@ -295,7 +296,8 @@ def bench_batched(ts, count):
     """Batched uneven TSQR: `count` instances, m log-uniform in [256, 65536], n uniform in
     {8, 16, 32, 64}, iid N(0,1) entries (device generator, seeded), alternately FP64 and
     FP32-mixed; R of every instance. One persistent launch for the whole batch, with the
-    chain length and tree arity picked by timing candidates on a 1000-instance sample;
+    chain length and tree arity picked by the library's autotuner (tsqr_batch_autotune) on a
+    1000-instance sample;
     compared with one launch per instance (the same kernel, batches of one) and with the
     plain multi-launch tsqr_factor, both timed on a sample and reported per instance."""
     import torch
@@ -328,10 +330,9 @@ def bench_batched(ts, count):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    sample = items[:min(1000, count)]
-    cands = [(L, ar) for L in (2, 4, 8, 16, 32) for ar in (2, 4)]
-    tune = {f"L{L}_a{ar}": run(sample, L, ar) for L, ar in cands}
-    L_best, ar_best = min(cands, key=lambda c: tune[f"L{c[0]}_a{c[1]}"])
+    # the library's autotuner times every (chain length, arity) on the first 1000 items
+    L_best, ar_best, table = ts.batch_autotune(items, sample=min(1000, count))
+    tune = {f"L{L}_a{ar}": ms for (L, ar), ms in table.items()}
     t_batch = run(items, L_best, ar_best, reps=2)
     # the same batch planned once and replayed as a CUDA graph
     torch.cuda.synchronize()
@@ -775,6 +776,13 @@ def bench_ours(args):
         e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
         del Ah, slots
 
+    # the library's factorization autotuner on the same matrix (leaf height x arity x tree
+    # form, factor only); reported beside the headline's fixed configuration
+    tuned = None
+    if rank == 0 and not args.no_tune:
+        tuned = ts.factor_autotune(Ad)
+        tuned["headline_factor_ms"] = factor_ms
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         if all_cpus:
@@ -815,7 +823,7 @@ def bench_ours(args):
                                       "measured-peaks file has no FP64 entry",
                          "frac_of_derived": achieved / peak_derived},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
-            "mixed_lsq": mixed, "batched": batched, "served": served,
+            "factor_autotune": tuned, "mixed_lsq": mixed, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

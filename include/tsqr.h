@@ -251,6 +251,31 @@ tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_
                              int32_t arity, void *stream, int32_t *status, double *info);
 
 /*
+ * Autotuners: each times its candidates on the caller's own data with CUDA events on the
+ * caller's stream (which it synchronizes) and returns the fastest. A candidate runs once
+ * untimed (planning, memory-pool growth), then twice timed; its time is the faster run.
+ *
+ * tsqr_batch_autotune(items, count, sample, stream, &chain_tiles, &arity, ms_table)
+ *   Runs the first `sample` items (0 = min(count, 1000)) as tsqr_batch_solve does, for
+ *   every chain length in {2, 4, 8, 16, 32} and tree arity in {2, 4}, and returns the
+ *   fastest pair (pass them to tsqr_batch_solve, tsqr_batch_plan_create or the server).
+ *   ms_table: host array of 10 floats or NULL: each pair's time in ms, chain length
+ *   outer, arity inner. The timing runs write the sampled items' outputs (the values a
+ *   tsqr_batch_solve call writes). Errors: TSQR_ERR_ARG (an invalid item as for
+ *   tsqr_batch_solve, count < 1, NULL items or outputs), TSQR_ERR_OOM, TSQR_ERR_CUDA.
+ * tsqr_factor_autotune(A, m, n, lda, stream, &leaf_h, &arity, &flags, &best_ms)
+ *   Times tsqr_factor (FP64) of A, which is not modified, for leaves of 1, 4 and 16
+ *   on-chip tiles, arity 2 and 4, the two-level and the pure tree, plus the flat tree
+ *   (arity 0) while A has at most one tile per SM, and returns the fastest leaf_h, arity
+ *   and flags (TSQR_TWO_LEVEL or 0); best_ms (may be NULL) receives its time in ms.
+ *   Errors: as tsqr_factor; TSQR_ERR_ARG for NULL outputs.
+ */
+tsqr_status tsqr_batch_autotune(const tsqr_batch_item *items, int32_t count, int32_t sample, void *stream,
+                                int32_t *chain_tiles, int32_t *arity, float *ms_table);
+tsqr_status tsqr_factor_autotune(const double *A, int64_t m, int32_t n, int64_t lda, void *stream,
+                                 int32_t *leaf_h, int32_t *arity, int32_t *flags, float *best_ms);
+
+/*
  * Reusable batch plans: a batch whose items keep their shapes and buffers (an iterative
  * method factoring new data in the same arrays, a benchmark loop) is planned once and
  * replayed as a CUDA graph, so a run costs no host planning and no table uploads.

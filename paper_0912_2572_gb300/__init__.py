@@ -17,7 +17,8 @@ import ctypes
 from . import _lib
 
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
-           "TSQRError", "profile_collect", "plan_describe", "batch_solve"]
+           "TSQRError", "profile_collect", "plan_describe", "batch_solve", "batch_autotune", "factor_autotune",
+           "AUTO", "BatchPlan", "Server", "probe_fp64_peak"]
 
 FP64 = 0
 MIXED = 1
@@ -210,6 +211,46 @@ def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status
     if info:
         ret.append([(int(inf[2 * q]), inf[2 * q + 1]) for q in range(len(items))])
     return ret[0] if len(ret) == 1 else tuple(ret)
+
+
+# candidate order of tsqr_batch_autotune's time table: chain tiles outer, arity inner
+BATCH_TUNE_CANDIDATES = [(L, a) for L in (2, 4, 8, 16, 32) for a in (2, 4)]
+
+
+def batch_autotune(items, sample: int = 0, stream=None):
+    """Picks the batched engine's chain length and tree arity by timing every candidate
+    on the first ``sample`` items (0 = up to 1000) with the library's native autotuner
+    (tsqr_batch_autotune; synchronizes the stream). Returns (chain_tiles, arity,
+    {(chain_tiles, arity): ms})."""
+    lib = _lib.load()
+    arr = (_lib.BatchItem * max(1, len(items)))()
+    keep = []
+    for q, it in enumerate(items):
+        kp, _ = _fill_item(arr[q], it)
+        keep += kp
+    L = ctypes.c_int32(0)
+    ar = ctypes.c_int32(0)
+    table = (ctypes.c_float * len(BATCH_TUNE_CANDIDATES))()
+    _lib.check(lib.tsqr_batch_autotune(arr, len(items), sample, _stream(stream), ctypes.byref(L),
+                                       ctypes.byref(ar), table), "tsqr_batch_autotune")
+    return L.value, ar.value, {c: table[q] for q, c in enumerate(BATCH_TUNE_CANDIDATES)}
+
+
+def factor_autotune(A, stream=None) -> dict:
+    """Picks leaf height, tree arity and tree form for tsqr_factor of A by timing the
+    candidates on A itself (tsqr_factor_autotune; A is not modified, the stream is
+    synchronized). Returns {"leaf_h", "arity", "two_level", "ms"}."""
+    lib = _lib.load()
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    h = ctypes.c_int32(0)
+    ar = ctypes.c_int32(0)
+    fl = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    _lib.check(lib.tsqr_factor_autotune(A.data_ptr(), m, n, lda, _stream(stream), ctypes.byref(h),
+                                        ctypes.byref(ar), ctypes.byref(fl), ctypes.byref(ms)),
+               "tsqr_factor_autotune")
+    return {"leaf_h": h.value, "arity": ar.value, "two_level": bool(fl.value & TWO_LEVEL), "ms": ms.value}
 
 
 class BatchPlan:

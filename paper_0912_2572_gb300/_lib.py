@@ -39,6 +39,10 @@ SIGNATURES = {
     "tsqr_lstsq_static": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _vp]),
     "tsqr_batch_solve": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _vp, ctypes.POINTER(_i32),
                                  ctypes.POINTER(ctypes.c_double)]),
+    "tsqr_batch_autotune": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _vp, ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)]),
+    "tsqr_factor_autotune": (_i32, [_dp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                     ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)]),
     "tsqr_free": (_i32, [_vp]),
     "tsqr_probe_fp64_peak": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "tsqr_batch_plan_create": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, ctypes.POINTER(_vp)]),

@@ -450,6 +450,10 @@ static void plan_info(const Plan &pl, int64_t *out) {
 // Batched mixed least squares (refine_batch.cu): rows per refinement task, the number of
 // refinement launches, and the stopping tolerance on the predicted remaining
 // ||dX||/||X|| (the last correction times rho / (1 - rho), rho the observed contraction).
+// the batched autotuner's candidates (tsqr_batch_autotune's ms_table order: chain tiles
+// outer, arity inner)
+constexpr int32_t kBatchTuneChainTiles[] = {2, 4, 8, 16, 32};
+constexpr int32_t kBatchTuneArity[] = {2, 4};
 constexpr int64_t kRefineRows = 4096;
 constexpr size_t kBatchSmemSlack = 256;
 constexpr int kMixedChainFactor = 4;
@@ -1314,6 +1318,127 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *P) {
   if (!P) return TSQR_OK;
   if (P->ran) cudaStreamSynchronize(P->last);
   plan_release(P);
+  return TSQR_OK;
+}
+
+// ------------------------------------------------------------------- autotuners
+// Both time their candidates with CUDA events on the caller's stream, on the caller's
+// own data, and return the fastest; each candidate runs once untimed first (planning,
+// pool growth) and then twice timed, keeping the faster run.
+namespace {
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+tsqr_status tsqr_batch_autotune(const tsqr_batch_item *items, int32_t count, int32_t sample, void *stream,
+                                int32_t *chain_tiles, int32_t *arity, float *ms_table) {
+  g_last_error.clear();
+  if (count < 1 || !items || !chain_tiles || !arity) return fail(TSQR_ERR_ARG, "bad items/count/outputs");
+  for (int32_t q = 0; q < count; ++q) {
+    tsqr_status st = check_batch_item(items[q], q);
+    if (st != TSQR_OK) return st;
+  }
+  const int32_t S = sample > 0 ? std::min(sample, count) : std::min<int32_t>(count, 1000);
+  cudaStream_t s = (cudaStream_t)stream;
+  EventPair ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  float best = 0.f;
+  int32_t q = 0;
+  try {
+    for (int32_t L : kBatchTuneChainTiles) {
+      for (int32_t ar : kBatchTuneArity) {
+        float t = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+          if (rep > 0) CUDA_TRY(cudaEventRecord(ev.a, s));
+          tsqr_status st = batch_solve_internal(items, S, L, ar, s, nullptr, nullptr, nullptr);
+          if (st != TSQR_OK) return st;
+          if (rep > 0) {
+            CUDA_TRY(cudaEventRecord(ev.b, s));
+            CUDA_TRY(cudaEventSynchronize(ev.b));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
+            t = (rep == 1) ? ms : std::min(t, ms);
+          }
+        }
+        if (ms_table) ms_table[q] = t;
+        if (q == 0 || t < best) {
+          best = t;
+          *chain_tiles = L;
+          *arity = ar;
+        }
+        ++q;
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    return fail(TSQR_ERR_OOM, "host allocation failed");
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_factor_autotune(const double *A, int64_t m, int32_t n, int64_t lda, void *stream, int32_t *leaf_h,
+                                 int32_t *arity, int32_t *flags, float *best_ms) {
+  g_last_error.clear();
+  tsqr_status st = check_factor_args(A, m, n, lda, n, 2);
+  if (st != TSQR_OK) return st;
+  if (!leaf_h || !arity || !flags) return fail(TSQR_ERR_ARG, "NULL output");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  int th = 0, cps = 0;
+  if (!factor_tile_choice(n, n, 1 << 20, (size_t)di.smem_sm, (size_t)di.reserved, (size_t)di.optin, 3, th, cps))
+    return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for n=%d", n);
+  // candidates: the two-level tree and the pure k-ary tree over leaves of 1, 4 and 16
+  // tiles; the flat tree (one chain, one CTA) only while it has at most one tile per SM
+  struct Cand {
+    int32_t h, ar, fl;
+  };
+  std::vector<Cand> cands;
+  for (int32_t mult : {1, 4, 16})
+    for (int32_t ar : {2, 4}) {
+      cands.push_back({th * mult, ar, TSQR_TWO_LEVEL});
+      cands.push_back({th * mult, ar, 0});
+    }
+  if ((m + th - 1) / th <= di.sms) cands.push_back({th, 0, 0});
+  cudaStream_t s = (cudaStream_t)stream;
+  EventPair ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  float best = 0.f;
+  bool have = false;
+  for (const Cand &c : cands) {
+    if ((int64_t)c.h > m) continue;
+    float t = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      if (rep > 0) CUDA_TRY(cudaEventRecord(ev.a, s));
+      tsqr_factors *F = nullptr;
+      st = tsqr_factor(A, m, n, lda, c.h, c.ar, TSQR_FP64, c.fl, stream, &F, nullptr, 0);
+      if (st != TSQR_OK) return st;
+      tsqr_free(F);
+      if (rep > 0) {
+        CUDA_TRY(cudaEventRecord(ev.b, s));
+        CUDA_TRY(cudaEventSynchronize(ev.b));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        t = (rep == 1) ? ms : std::min(t, ms);
+      }
+    }
+    if (!have || t < best) {
+      have = true;
+      best = t;
+      *leaf_h = c.h;
+      *arity = c.ar;
+      *flags = c.fl;
+    }
+  }
+  if (!have) return fail(TSQR_ERR_UNSUPPORTED, "no candidate fits m=%lld", (long long)m);
+  if (best_ms) *best_ms = best;
   return TSQR_OK;
 }
 

@@ -198,6 +198,21 @@ def test_server_entry_points_reject_bad_arguments(lib):
     assert lib.tsqr_server_destroy(None) == 0
 
 
+def test_autotuners_reject_bad_arguments(lib):
+    L, a, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    item = _lib.BatchItem()                   # A = NULL: an invalid item
+    item.m, item.n, item.lda = 100, 4, 100
+    assert lib.tsqr_batch_autotune(None, 1, 0, None, ctypes.byref(L), ctypes.byref(a), None) == 1
+    assert lib.tsqr_batch_autotune(ctypes.byref(item), 0, 0, None, ctypes.byref(L), ctypes.byref(a), None) == 1
+    assert lib.tsqr_batch_autotune(ctypes.byref(item), 1, 0, None, ctypes.byref(L), ctypes.byref(a), None) == 1
+    assert lib.tsqr_factor_autotune(None, 100, 4, 100, None, ctypes.byref(L), ctypes.byref(a), ctypes.byref(f),
+                                    None) == 1
+    assert lib.tsqr_factor_autotune(ctypes.c_void_p(256), 100, 4, 100, None, None, ctypes.byref(a),
+                                    ctypes.byref(f), None) == 1
+    assert lib.tsqr_factor_autotune(ctypes.c_void_p(256), 3, 4, 100, None, ctypes.byref(L), ctypes.byref(a),
+                                    ctypes.byref(f), None) == 1   # m < n
+
+
 def test_batch_plan_entry_points_reject_bad_arguments(lib):
     h = ctypes.c_void_p()
     assert lib.tsqr_batch_plan_create(None, 1, 0, 0, ctypes.byref(h)) == 1
