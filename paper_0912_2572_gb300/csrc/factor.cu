@@ -245,7 +245,11 @@ __device__ __forceinline__ void bar_arrive_n(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <int CMAX>
+// EARLY_PF: the scalar warp loads the next pivot row at the start of the step (its L2
+// latency overlaps the norm and the reflector, which matters on tree nodes, where the
+// update is short) instead of after the coefficients (fewer live registers: the batched
+// kernel, at its register cap, keeps that order).
+template <int CMAX, bool EARLY_PF>
 __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const JobDesc job, unsigned char *smraw) {
   using R = double;
   R *sm = reinterpret_cast<R *>(smraw);
@@ -304,6 +308,17 @@ __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const Jo
         bar_sync_n(2, kThreads);
         update_dispatch<CMAX, R>(T, ldt, j, j + 1, nc, lo, hi, v, hl, rw, PC);
       } else {
+        // the next pivot row (not written before step j+1) is loaded now, so its L2 latency
+        // overlaps this step's norm and reflector
+        R pf[PCN];
+        const bool do_pf = !ge && j + 1 < n;
+        if (EARLY_PF && do_pf) {
+#pragma unroll
+          for (int q = 0; q < PCN; ++q) {
+            const int c = j + 1 + lane + 32 * q;
+            pf[q] = (c < nc) ? __ldcg(piv_ptr(j + 1, c)) : R(0);
+          }
+        }
         // squared norm of the pivot column's tail (two partial sums per lane), then the reflector
         const R *Tj = T + (size_t)j * ldt;
         R a0 = R(0), a1 = R(0);
@@ -332,6 +347,7 @@ __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const Jo
         }
         bar_arrive_n(2, kThreads);  // the coefficients are in PC
         // the new pivot row and the reflector's scalars, then the next pivot row's staging
+        // (PV[c] for c > j was read above by this same lane)
 #pragma unroll
         for (int q = 0; q < PCN; ++q) {
           const int c = j + 1 + lane + 32 * q;
@@ -350,11 +366,11 @@ __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const Jo
           p.tau[td.refl + j] = rf.tau;
           p.scl[td.refl + j] = rf.scale;
         }
-        if (!ge && j + 1 < n) {
+        if (do_pf) {
 #pragma unroll
           for (int q = 0; q < PCN; ++q) {
             const int c = j + 1 + lane + 32 * q;
-            if (c < nc) PV[c] = __ldcg(piv_ptr(j + 1, c));
+            if (c < nc) PV[c] = EARLY_PF ? pf[q] : __ldcg(piv_ptr(j + 1, c));
           }
         }
         __syncwarp();
@@ -600,7 +616,7 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
 template <int CMAX, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_factor(const FactorParamsT<double> p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  run_job<CMAX>(p, p.jobs[p.job0 + blockIdx.x], smraw);
+  run_job<CMAX, true>(p, p.jobs[p.job0 + blockIdx.x], smraw);
 }
 
 
@@ -704,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.n = in.n;
         fp.nc = in.n + in.k;
         fp.ldt = chain ? in.ldt : in.ldt_tree;
-        run_job<CMAX>(fp, jd, smraw);
+        run_job<CMAX, false>(fp, jd, smraw);
       }
       if (bj.parent < 0) {
         __threadfence();
