@@ -524,7 +524,8 @@ cudaError_t launch_warp_k(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
 }
 
 template <typename R>
-cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_sm, int cols_per_cta,
+                             cudaStream_t s) {
   if (njobs <= 0 || p.k <= 0) return cudaSuccess;
   if (p.ldt > 512) return cudaErrorInvalidValue;
   if (p.k <= 8 && !p.formq) {
@@ -539,16 +540,17 @@ cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_s
       default: return launch_warp_k<8, R>(p, njobs, s);
     }
   }
-  // up to 64 columns per pass; fewer columns use a narrower tile
-  if (p.k <= 16) return launch_tile_rm<1, R>(p, njobs, ctas_per_sm, s);
-  if (p.k <= 32) return launch_tile_rm<2, R>(p, njobs, ctas_per_sm, s);
+  // up to 64 columns per CTA; fewer columns (or a cap) use a narrower tile and more CTAs
+  if (p.k <= 16 || cols_per_cta <= 16) return launch_tile_rm<1, R>(p, njobs, ctas_per_sm, s);
+  if (p.k <= 32 || cols_per_cta <= 32) return launch_tile_rm<2, R>(p, njobs, ctas_per_sm, s);
   return launch_tile_rm<4, R>(p, njobs, ctas_per_sm, s);
 }
 
 }  // namespace
 
-cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm) {
-  return launch_apply_any(p, njobs, ctas_per_sm, s);
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm,
+                         int cols_per_cta) {
+  return launch_apply_any(p, njobs, ctas_per_sm, cols_per_cta, s);
 }
 
 }  // namespace tsqr

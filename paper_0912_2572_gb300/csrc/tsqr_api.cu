@@ -409,6 +409,7 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
   p.trans = trans;
   p.formq = formq;
   const int nl = (int)pl.launches.size();
+  const int sms = device_info(F->device).sms;
   // B is processed in groups of at most 64 columns (8 for the warp kernel path)
   const int group = (k <= 8) ? 8 : 64;
   for (int c0 = 0; c0 < k; c0 += group) {
@@ -419,7 +420,10 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
       const LaunchDesc &ld = pl.launches[li];
       p.job0 = ld.job_begin;
       ProfScope ps(formq ? TSQR_PROF_FORM_Q : (trans ? TSQR_PROF_APPLY_QT : TSQR_PROF_APPLY_Q), s);
-      CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2));
+      // a tree level whose nodes, four CTAs each, still fit one wave of two CTAs per SM
+      // runs 16 columns per CTA: each node's reflector steps get shorter
+      const bool narrow = li > 0 && (int64_t)ld.job_count * 4 <= (int64_t)sms * 2;
+      CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2, narrow ? 16 : 64));
     }
   }
   return TSQR_OK;

@@ -217,7 +217,11 @@ struct ApplyParamsT {
 
 using ApplyParams = ApplyParamsT<double>;
 
-cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2);
+// cols_per_cta caps the columns of B one CTA of the tile kernel handles (16, 32 or 64): a
+// launch with few jobs (a tree level) spreads a job's columns over more CTAs; columns are
+// independent, so each one's arithmetic does not change.
+cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2,
+                         int cols_per_cta = 64);
 
 // ------------------------------------------------------------------- small kernels
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,

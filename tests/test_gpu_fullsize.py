@@ -1,5 +1,7 @@
 """Parity at the benchmark's full size and launch configuration: 4,194,304 x 64 FP64,
-A = G diag(sigma) V^T with sigma from 1 to 1e-6, two-level tree, 224-row tiles.
+A = G diag(sigma) V^T with sigma from 1 to 1e-6, two-level binary tree, leaves of one
+on-chip tile (the leaf height the benchmark derives the same way: 144 rows, three CTAs
+per SM on GB300).
 
 R is compared with the oracle's R of the whole matrix (relative Frobenius <= 1e-12);
 backward error ||A - QR||/||A|| and orthogonality ||Q^T Q - I|| are checked on rows the
@@ -23,7 +25,8 @@ def full_case(cuda_lib):
     A = inputs.graded(M, N, 6.0, seed_g=0, seed_v=1)
     b = inputs.gaussian(M, 1, seed=2)
     Ad = to_dev(A)
-    F = ts.factor(Ad, leaf_h=224, arity=2, two_level=True)
+    leaf_h = ts.plan_describe(M, N, 4096, 2, True)["tile_rows"]
+    F = ts.factor(Ad, leaf_h=leaf_h, arity=2, two_level=True)
     Q = F.form_q()
     bd = to_dev(b)
     F.apply_qt(bd)
