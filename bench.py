@@ -38,7 +38,7 @@ FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20
 # capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum at m = 1,048,576,
 # n = 64, 144-row tiles: 1.050 GB); traffic grows with the rows, so it is scaled by m.
 # Valid for n = 64 and that kernel build.
-CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.020288e6 + 503.156224e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
+CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.427328e6 + 502.893824e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
 def flops_step(m, n, k=1):
