@@ -539,14 +539,37 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
         f32_gram_dispatch<CPT>(v, x, j, d <= 0 ? 0 : (d + 15) >> 4, hw, hl, nc, PC);
       }
       __syncthreads();
-      // (C) warp 0: the reflector's scalars, the update coefficients and the new pivot row
+      // (C) warp 0: the reflector's scalars, the update coefficients and the new pivot row.
+      //     Up to 64 columns all loads go first (the columns are independent, and stores
+      //     between loads would serialize them: 5-10% faster chains at n <= 64); at 128
+      //     columns the extra live registers cost more than that.
       if (warp == 0) {
         const Refl<float> rf = reflector<float>(PV[j], PC[j]);
-        for (int c = j + 1 + lane; c < nc; c += 32) {
-          const float pk = PV[c];
-          const float w = fmaf(rf.scale, PC[c], pk);
-          PC[c] = rf.ts * w;
-          PV[c] = fmaf(-rf.tau, w, pk);
+        if constexpr (CPT <= 4) {
+          constexpr int QN = (16 * CPT + 31) / 32;
+          float pk[QN], g[QN];
+#pragma unroll
+          for (int q = 0; q < QN; ++q) {
+            const int c = j + 1 + lane + 32 * q;
+            pk[q] = (c < nc) ? PV[c] : 0.f;
+            g[q] = (c < nc) ? PC[c] : 0.f;
+          }
+#pragma unroll
+          for (int q = 0; q < QN; ++q) {
+            const int c = j + 1 + lane + 32 * q;
+            const float w = fmaf(rf.scale, g[q], pk[q]);
+            if (c < nc) {
+              PC[c] = rf.ts * w;
+              PV[c] = fmaf(-rf.tau, w, pk[q]);
+            }
+          }
+        } else {
+          for (int c = j + 1 + lane; c < nc; c += 32) {
+            const float pk = PV[c];
+            const float w = fmaf(rf.scale, PC[c], pk);
+            PC[c] = rf.ts * w;
+            PV[c] = fmaf(-rf.tau, w, pk);
+          }
         }
         if (lane == 0) {
           PV[j] = rf.beta;
