@@ -261,11 +261,12 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
 // The structure of the factor kernel: the job's tile of B (up to 16*CMAX columns of this
 // pass) is staged in shared memory, the pivot row of each reflector is staged from
 // global memory (prefetched one reflector ahead), and the reflector tail is prefetched
-// into registers (every half-warp reads the same rows, so the loads hit L1). Half-warp hw
-// owns columns cs + hw + 16 t; each warp issues exactly its own slots. The half-warp
-// ranks rotate with the reflector: a CTA's warp w always runs on SM sub-partition w mod 4,
-// and with a fixed order the lowest warps, which take the extra slots of uneven steps,
-// would load the same sub-partition's FP64 pipe in every CTA on the SM.
+// into registers (every half-warp reads the same rows, so the loads hit L1). The
+// half-warp of rank h owns columns cs + h + 16 t; each warp issues exactly its own slots.
+// The ranks rotate with the reflector (warp w has rank (w + s) mod 8 at reflector step s):
+// a CTA's warp w always runs on SM sub-partition w mod 4, and with a fixed order the
+// lowest warps, which take the extra slots of uneven steps, would load the same
+// sub-partition's FP64 pipe in every CTA on the SM. Warp 0 runs each step's scalar phase.
 constexpr int kTileThreads = 256;
 
 

@@ -541,7 +541,7 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
       __syncthreads();
       // (C) warp 0: the reflector's scalars, the update coefficients and the new pivot row.
       //     Up to 64 columns all loads go first (the columns are independent, and stores
-      //     between loads would serialize them: 5-10% faster chains at n <= 64); at 128
+      //     between loads would serialize them: about 6% faster chains at n <= 64); at 128
       //     columns the extra live registers cost more than that.
       if (warp == 0) {
         const Refl<float> rf = reflector<float>(PV[j], PC[j]);

@@ -218,8 +218,8 @@ struct ApplyParamsT {
 using ApplyParams = ApplyParamsT<double>;
 
 // cols_per_cta caps the columns of B one CTA of the tile kernel handles (16, 32 or 64): a
-// launch with few jobs (a tree level) spreads a job's columns over more CTAs; columns are
-// independent, so each one's arithmetic does not change.
+// launch with few jobs (a tree level) spreads a job's columns over more CTAs. Columns are
+// independent; only the summation order of a column's dot products changes with the cap.
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2,
                          int cols_per_cta = 64);
 
