@@ -44,6 +44,27 @@ def test_apply_qt_unique_part(cuda_lib, m, n, h, arity, two, k):
     F.free()
 
 
+@pytest.mark.parametrize("m,n,h,two", [(200_003, 16, 64, False), (131_077, 8, 32, True)])
+def test_apply_one_rhs_over_many_jobs(cuda_lib, m, n, h, two):
+    """A single right-hand side over a chain launch of thousands of jobs (one warp per job),
+    with the remainder rows in the last leaf, so the jobs differ in tile count and height."""
+    import paper_0912_2572_gb300 as ts
+    info = ts.plan_describe(m, n, h, 2, two)
+    assert info["jobs"] >= 1024
+    A = inputs.gaussian(m, n, seed=13)
+    b = inputs.gaussian(m, 1, seed=14)
+    F = ts.factor(to_dev(A), leaf_h=h, arity=2, two_level=two)
+    bd = to_dev(b)
+    F.apply_qt(bd)
+    c = to_host(bd)
+    top, tail = oracle.qt_b(A, b)
+    assert rel(c[:n], top) <= 1e-12
+    assert rel(np.linalg.norm(c[n:], axis=0), tail) <= 1e-12
+    F.apply_q(bd)
+    assert rel(to_host(bd), b) <= 1e-13
+    F.free()
+
+
 @pytest.mark.parametrize("m,n,h,arity,two", SHAPES)
 def test_apply_q_of_thin_coordinates(cuda_lib, m, n, h, arity, two):
     """Q [c; 0] = Q_thin c, the only part of Q B fixed by the factorization."""
