@@ -38,6 +38,10 @@ FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20
 # capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum at m = 1,048,576,
 # n = 64, 144-row tiles: 1.050 GB); traffic grows with the rows, so it is scaled by m.
 # Valid for n = 64 and that kernel build.
+# end-to-end pipeline: steps rotate over this many streams, each with its own device
+# buffers, so one step's input copy, another's result copy and a third's kernels overlap
+# (measured at 4M x 64: 87.0 ms per step with three, 89.6 with two, 101.8 with one)
+E2E_SLOTS = 3
 CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.427328e6 + 502.893824e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
@@ -728,15 +732,15 @@ def bench_ours(args):
     peak = peak_measured if peak_measured > 0 else peak_derived
     factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
 
-    # --- end to end: pinned host buffers, copies inside the timed region. Steps alternate
-    # between two streams with their own device buffers, so step i+1's input copy and step
-    # i's result copy overlap the other stream's kernels (every copy stays in the region).
+    # --- end to end: pinned host buffers, copies inside the timed region. Steps rotate
+    # over E2E_SLOTS streams with their own device buffers, so input and result copies
+    # overlap other steps' kernels (every copy stays in the region).
     e2e = None
     if not args.no_e2e:
         Ah = host_pinned_colmajor(A)
         bh = host_pinned_colmajor(b)
         slots = []
-        for q in range(2):
+        for q in range(E2E_SLOTS):
             sl = {"s": torch.cuda.Stream(),
                   "Qh": torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
                   "Rh": torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
@@ -750,28 +754,30 @@ def bench_ours(args):
             slots.append(sl)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for sl in slots:
-            sl["s"].wait_event(e0)
-        for i in range(args.e2e_steps):
-            sl = slots[i % 2]
-            with torch.cuda.stream(sl["s"]):
-                sl["Ad"].copy_(Ah, non_blocking=True)
-                sl["b0"].copy_(bh, non_blocking=True)
-                F = run_step(ts, sl["Ad"], sl["bd"], sl["b0"], sl["Q"], sl["x"], leaf_h, args.arity, two)
-                sl["Qh"].copy_(sl["Q"], non_blocking=True)
-                sl["Rh"].copy_(F.R, non_blocking=True)
-                sl["xh"].copy_(sl["x"], non_blocking=True)
-                F.free()
-        for sl in slots:
-            stream.wait_stream(sl["s"])
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with ClockSampler(local) as e2e_clk:
+            e0.record(stream)
+            for sl in slots:
+                sl["s"].wait_event(e0)
+            for i in range(args.e2e_steps):
+                sl = slots[i % E2E_SLOTS]
+                with torch.cuda.stream(sl["s"]):
+                    sl["Ad"].copy_(Ah, non_blocking=True)
+                    sl["b0"].copy_(bh, non_blocking=True)
+                    F = run_step(ts, sl["Ad"], sl["bd"], sl["b0"], sl["Q"], sl["x"], leaf_h, args.arity, two)
+                    sl["Qh"].copy_(sl["Q"], non_blocking=True)
+                    sl["Rh"].copy_(F.R, non_blocking=True)
+                    sl["xh"].copy_(sl["x"], non_blocking=True)
+                    F.free()
+            for sl in slots:
+                stream.wait_stream(sl["s"])
+            e1.record(stream)
+            torch.cuda.synchronize()
         te = rank_max(e0.elapsed_time(e1), world, "cuda")
         e2e = {"value": whole_job_rate(fl_step * args.e2e_steps, world, te) / 1e9, "unit": "Gflop/s",
                "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
-               "ms_per_step": te / args.e2e_steps, "pipelined_streams": 2}
-        xe = slots[(args.e2e_steps - 1) % 2]["xh"].numpy()[:, 0]
+               "ms_per_step": te / args.e2e_steps, "pipelined_streams": E2E_SLOTS,
+               "clocks": e2e_clk.summary()}
+        xe = slots[(args.e2e_steps - 1) % E2E_SLOTS]["xh"].numpy()[:, 0]
         xd = x.cpu().numpy()[:, 0]
         e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
         del Ah, slots
