@@ -211,13 +211,25 @@ def host_pinned_colmajor(a):
     return t.t()
 
 
+_SIDE_STREAMS = {}
+
+
 def run_step(ts, Ad, bd, b0, Q, x, leaf_h, arity, two_level):
-    """One pass of the FP64 path; returns the factor set (caller frees)."""
+    """One pass of the FP64 path; returns the factor set (caller frees). The thin Q and
+    Q^T b + the solve both need only the factorization, so Q^T b runs on a second stream
+    beside the thin Q (its latency-bound tree levels fill SMs the thin Q leaves idle); the
+    calling stream waits for both before returning."""
+    import torch
+    cur = torch.cuda.current_stream()
+    side = _SIDE_STREAMS.setdefault(cur.cuda_stream, torch.cuda.Stream())
     F = ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two_level)
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        bd.copy_(b0)
+        F.apply_qt(bd)
+        F.solve_r(bd, X=x)
     F.form_q(Q)
-    bd.copy_(b0)
-    F.apply_qt(bd)
-    F.solve_r(bd, X=x)
+    cur.wait_stream(side)
     return F
 
 
