@@ -52,3 +52,17 @@ def test_factor_autotune_configuration_matches_oracle(cuda_lib):
     R = to_host(F.R)
     F.free()
     assert rel(R, oracle.r_factor(A)) <= 1e-12
+
+
+def test_factor_autotune_small_matrix(cuda_lib):
+    """A matrix of at most one tile per SM also tries the flat tree (one chain)."""
+    import paper_0912_2572_gb300 as ts
+    m, n = 20_000, 16
+    A = inputs.gaussian(m, n, 77)
+    Ad = to_dev(A)
+    cfg = ts.factor_autotune(Ad)
+    assert cfg["ms"] > 0 and cfg["arity"] in (0, 2, 4)
+    F = ts.factor(Ad, leaf_h=cfg["leaf_h"], arity=cfg["arity"], two_level=cfg["two_level"])
+    R = to_host(F.R)
+    F.free()
+    assert rel(R, oracle.r_factor(A)) <= 1e-12

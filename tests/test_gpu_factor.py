@@ -62,3 +62,23 @@ def test_fp64_peak_probe_is_plausible(cuda_lib):
     import paper_0912_2572_gb300 as ts
     tf = ts.probe_fp64_peak()
     assert 0.3 < tf < 3.0
+
+
+@pytest.mark.parametrize("n", [1, 8, 16, 24, 32, 48, 64])
+def test_three_cta_plan_widths(cuda_lib, n):
+    """The default tile of the widths that take three CTAs per SM (tiles of at least 2n
+    rows), on a ragged m: R and the thin Q against the oracle, and the plan is the
+    three-CTA one."""
+    import paper_0912_2572_gb300 as ts
+    m = 60_013
+    info = ts.plan_describe(m, n, 1 << 20)
+    assert info["ctas_per_sm"] == 3 and info["tile_rows"] >= 2 * n
+    A = inputs.gaussian(m, n, 900 + n)
+    F = ts.factor(to_dev(A), leaf_h=info["tile_rows"], arity=2, two_level=True)
+    Q = to_host(F.form_q())
+    R = to_host(F.R)
+    F.free()
+    Qo, Ro, _ = oracle.qr(A)
+    assert _rel(R, Ro) <= R_TOL
+    assert _rel(Q, Qo) <= R_TOL
+    assert oracle.orth_error(Q) <= BE_TOL
