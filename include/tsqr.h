@@ -122,7 +122,7 @@ tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *str
  *              chains of 128-row tiles, the FP64 tree with `arity` (0 = binary), and
  *              corrected semi-normal-equation refinement in FP64 from X = 0 (r = B - A X,
  *              R^T R dX = A^T r), at most max_refine + 1 steps, stopping once the predicted
- *              remaining ||dX||_F/||X||_F is below 1e-12 or the corrections stop
+ *              remaining ||dX||_F/||X||_F is below 1e-10 or the corrections stop
  *              shrinking; leaf_h and flags do not apply. k <= 64, refined in groups of 8.
  *              Synchronizes the stream.
  *   info       host array of length max_refine + 1 or NULL: info[s] = ||dX||_F/||X||_F
@@ -228,7 +228,7 @@ typedef struct tsqr_batch_item {
                        TSQR_MIXED: FP32 leaf chains + FP64 tree for R; with k > 0, X by
                        corrected semi-normal-equation refinement in FP64 from X = 0
                        (r = B - A X, R^T R dX = A^T r), at most 10 steps, stopping once the
-                       predicted remaining ||dX||_F/||X||_F is below 1e-12 or the
+                       predicted remaining ||dX||_F/||X||_F is below 1e-10 or the
                        corrections stop shrinking; R-only MIXED items carry FP32 accuracy.
                        TSQR_AUTO: one of the two by a cost model (R-only items: FP64). */
 } tsqr_batch_item;
