@@ -477,7 +477,7 @@ constexpr double kBatchRefineTol = 1e-10;
 constexpr double kFp64Factor = 0.76, kFp64FactorNarrow = 0.5;
 constexpr double kFp32FactorPerCol = 0.1, kFp32FactorMax = 6.0;
 constexpr double kRefineTflops = 0.75, kRefineTflopsNarrow = 0.6;
-constexpr double kRefineStepsEst = 2.6;
+constexpr double kRefineStepsEst = 2.3;
 
 // ---------------------------------------------------------------- batched solve
 namespace {
