@@ -811,6 +811,16 @@ def bench_ours(args):
         xe = slots[(args.e2e_steps - 1) % E2E_SLOTS]["xh"].numpy()[:, 0]
         xd = x.cpu().numpy()[:, 0]
         e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
+        # this box's pinned-copy bandwidth, after the timed region (the e2e figure depends on it)
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        slots[0]["Ad"].copy_(Ah, non_blocking=True)
+        c1.record(stream)
+        slots[0]["Qh"].copy_(slots[0]["Q"], non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        e2e["copy_gbs"] = {"h2d": 8.0 * m * n / (c0.elapsed_time(c1) * 1e-3) / 1e9,
+                           "d2h": 8.0 * m * n / (c1.elapsed_time(c2) * 1e-3) / 1e9}
         del Ah, slots
 
     # the library's factorization autotuner on the same matrix (leaf height x arity x tree
