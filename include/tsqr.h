@@ -99,6 +99,22 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
 tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k,
                           void *stream);
 
+/*
+ * tsqr_factor_qt — tsqr_factor and then B <- Q^T B as tsqr_apply_qt, in one call that
+ * overlaps them: the apply's launch over the leaves' reflectors runs as soon as the leaves
+ * are factored, while the reduction tree's levels (which keep few SMs busy) run, and each
+ * of the apply's tree levels follows the same level of the factorization. The overlap uses
+ * a helper stream of the library (one per device) joined back to `stream` with events; all
+ * of the call's work is ordered before work enqueued later on `stream`, and B's result is
+ * bitwise that of tsqr_factor + tsqr_apply_qt.
+ *   B, ldb, k  as tsqr_apply_qt (device, m-by-k, ldb >= m, k >= 1), overwritten.
+ *   Other arguments as tsqr_factor; TSQR_INPLACE is not supported (TSQR_ERR_ARG).
+ *   Errors: as tsqr_factor, plus TSQR_ERR_ARG for null B, k < 1 or ldb < m.
+ */
+tsqr_status tsqr_factor_qt(const double *A, int64_t m, int32_t n, int64_t lda, double *B, int64_t ldb,
+                           int32_t k, int32_t leaf_h, int32_t arity, int32_t prec, int32_t flags,
+                           void *stream, tsqr_factors **F, double *R, int64_t ldr);
+
 /* tsqr_apply_q — B <- Q B (the inverse of tsqr_apply_qt). Same arguments. */
 tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t k,
                          void *stream);

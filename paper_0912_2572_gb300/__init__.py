@@ -125,12 +125,14 @@ class Factors:
 
 
 def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace: bool = False,
-           R=None, stream=None) -> Factors:
+           R=None, stream=None, qt=None) -> Factors:
     """TSQR factorization of a column-major m-by-n float64 CUDA tensor A (paper §2.3).
 
     leaf_h: rows per leaf; arity: 2..16 (k-ary tree) or 0 (flat); two_level: a flat chain
     inside each CTA followed by the arity-k tree across CTAs. Returns a Factors object
-    whose ``R`` (n-by-n, diag >= 0) is valid once the stream reaches this point.
+    whose ``R`` (n-by-n, diag >= 0) is valid once the stream reaches this point. With
+    ``qt`` (an m-by-k column-major tensor), also qt <- Q^T qt, overlapped with the
+    factorization's tree (tsqr_factor_qt; not with ``inplace``).
     """
     import torch
     lib = _lib.load()
@@ -141,9 +143,15 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
     ldr = _check_mat(R, "R", rows=n, cols=n)
     flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0)
     h = ctypes.c_void_p()
-    st = lib.tsqr_factor(A.data_ptr(), m, n, lda, leaf_h, arity, FP64, flags, _stream(stream),
-                         ctypes.byref(h), R.data_ptr(), ldr)
-    _lib.check(st, "tsqr_factor")
+    if qt is None:
+        st = lib.tsqr_factor(A.data_ptr(), m, n, lda, leaf_h, arity, FP64, flags, _stream(stream),
+                             ctypes.byref(h), R.data_ptr(), ldr)
+        _lib.check(st, "tsqr_factor")
+    else:
+        ldq = _check_mat(qt, "qt", rows=m)
+        st = lib.tsqr_factor_qt(A.data_ptr(), m, n, lda, qt.data_ptr(), ldq, qt.shape[1], leaf_h, arity, FP64,
+                                flags, _stream(stream), ctypes.byref(h), R.data_ptr(), ldr)
+        _lib.check(st, "tsqr_factor_qt")
     return Factors(h, m, n, R, A if inplace else None, stream)
 
 

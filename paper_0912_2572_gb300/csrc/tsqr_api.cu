@@ -84,6 +84,20 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
   return cudaMallocAsync(p, bytes, s);
 }
 
+// One non-blocking helper stream per device, for work the library overlaps with the
+// caller's stream (joined back with events before the call's later work).
+cudaStream_t helper_stream(int dev) {
+  static std::mutex mu;
+  static std::vector<std::pair<int, cudaStream_t>> streams;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto &ds : streams)
+    if (ds.first == dev) return ds.second;
+  cudaStream_t hs = nullptr;
+  if (cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess) hs = nullptr;
+  streams.push_back({dev, hs});
+  return hs;
+}
+
 // ------------------------------------------------------------------- profiler
 // Opt-in: a pair of CUDA events recorded on the launching stream around every kernel
 // launch the library makes, read back by tsqr_profile_stop.
@@ -392,8 +406,10 @@ static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, dou
   return TSQR_OK;
 }
 
-static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
-                             cudaStream_t s) {
+// Launch li of the plan applied to B's columns [c0, c0 + kg) (kg <= 64; the warp kernel
+// for kg <= 8): Q^T in forward launch order, Q in reverse.
+static tsqr_status apply_launch(const tsqr_factors *F, double *B, int64_t ldb, int c0, int kg, int trans, int formq,
+                                int li, cudaStream_t s) {
   const Plan &pl = F->plan();
   ApplyParams p{};
   p.V = F->V;
@@ -408,24 +424,31 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
   p.ldt = pl.tile_h;
   p.trans = trans;
   p.formq = formq;
-  const int nl = (int)pl.launches.size();
+  p.col0 = c0;
+  p.k = kg;
+  const LaunchDesc &ld = pl.launches[li];
+  p.job0 = ld.job_begin;
   const int sms = device_info(F->device).sms;
-  // B is processed in groups of at most 64 columns (8 for the warp kernel path)
-  const int group = (k <= 8) ? 8 : 64;
-  for (int c0 = 0; c0 < k; c0 += group) {
-    p.col0 = c0;
-    p.k = std::min(group, k - c0);
+  ProfScope ps(formq ? TSQR_PROF_FORM_Q : (trans ? TSQR_PROF_APPLY_QT : TSQR_PROF_APPLY_Q), s);
+  // a tree level whose nodes, four CTAs each, still fit one wave of two CTAs per SM runs
+  // 16 columns per CTA: each node's reflector steps get shorter
+  const bool narrow = li > 0 && (int64_t)ld.job_count * 4 <= (int64_t)sms * 2;
+  CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2, narrow ? 16 : 64));
+  return TSQR_OK;
+}
+
+// B is processed in groups of at most 64 columns (8 for the warp kernel path)
+static int apply_group(int k) { return (k <= 8) ? 8 : 64; }
+
+static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
+                             cudaStream_t s) {
+  const int nl = (int)F->plan().launches.size();
+  const int group = apply_group(k);
+  for (int c0 = 0; c0 < k; c0 += group)
     for (int q = 0; q < nl; ++q) {
-      const int li = trans ? q : nl - 1 - q;  // launch 0 holds the chains
-      const LaunchDesc &ld = pl.launches[li];
-      p.job0 = ld.job_begin;
-      ProfScope ps(formq ? TSQR_PROF_FORM_Q : (trans ? TSQR_PROF_APPLY_QT : TSQR_PROF_APPLY_Q), s);
-      // a tree level whose nodes, four CTAs each, still fit one wave of two CTAs per SM
-      // runs 16 columns per CTA: each node's reflector steps get shorter
-      const bool narrow = li > 0 && (int64_t)ld.job_count * 4 <= (int64_t)sms * 2;
-      CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2, narrow ? 16 : 64));
+      tsqr_status st = apply_launch(F, B, ldb, c0, std::min(group, k - c0), trans, formq, trans ? q : nl - 1 - q, s);
+      if (st != TSQR_OK) return st;
     }
-  }
   return TSQR_OK;
 }
 
@@ -1079,9 +1102,15 @@ const char *tsqr_strerror(tsqr_status s) {
 
 const char *tsqr_last_error(void) { return g_last_error.c_str(); }
 
-tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h, int32_t arity,
-                        int32_t prec, int32_t flags, void *stream, tsqr_factors **F, double *R, int64_t ldr) {
-  g_last_error.clear();
+}  // extern "C"
+
+// The factorization's launches on s; with QB, also Q^T QB on a helper stream of the
+// device: launch q of the apply waits (event) for launch q of the factorization, so the
+// apply's chain launch runs while the factorization's latency-bound tree levels leave SMs
+// idle. s waits for the helper stream before the sign fix of QB.
+static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h, int32_t arity,
+                                 int32_t prec, int32_t flags, cudaStream_t s, tsqr_factors **F, double *R,
+                                 int64_t ldr, double *QB, int64_t ldqb, int32_t kqb) {
   tsqr_status st = check_factor_args(A, m, n, lda, leaf_h, arity);
   if (st != TSQR_OK) return st;
   if (!F) return fail(TSQR_ERR_ARG, "F is NULL");
@@ -1090,7 +1119,6 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
   if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "tsqr_factor: TSQR_MIXED is served by tsqr_lstsq");
   if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   *F = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
   tsqr_factors *f = new (std::nothrow) tsqr_factors();
   if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
   f->stream = s;
@@ -1108,10 +1136,64 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
       f->ldv = m;
     }
   }
-  if (st == TSQR_OK) st = run_factor(f, A, lda, nullptr, 0, s);
+  if (st == TSQR_OK && !QB) st = run_factor(f, A, lda, nullptr, 0, s);
+  if (st == TSQR_OK && QB) {
+    cudaStream_t hs = helper_stream(f->device);
+    if (!hs) st = fail(TSQR_ERR_CUDA, "no helper stream");
+    const Plan &pl = f->plan();
+    const int nl = (int)pl.launches.size();
+    std::vector<cudaEvent_t> ev(nl + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q <= nl && e == cudaSuccess && st == TSQR_OK; ++q)
+      e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "event creation: %s", cudaGetErrorString(e));
+    // the helper stream starts after everything already enqueued on s (QB's producers)
+    if (st == TSQR_OK) {
+      e = cudaEventRecord(ev[nl], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ev[nl], 0);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "helper stream fork: %s", cudaGetErrorString(e));
+    }
+    FactorParams p{};
+    p.A = A;
+    p.lda = lda;
+    p.V = f->V;
+    p.ldv = f->ldv;
+    p.jobs = f->dp->jobs;
+    p.tiles = f->dp->tiles;
+    p.tau = f->tau;
+    p.scl = f->scl;
+    p.n = pl.n;
+    p.nc = pl.n;
+    p.ldt = pl.tile_h;
+    const int group = apply_group(kqb);
+    for (int q = 0; q < nl && st == TSQR_OK; ++q) {
+      const LaunchDesc &ld = pl.launches[q];
+      p.job0 = ld.job_begin;
+      {
+        ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
+        e = launch_factor(p, ld.job_count, s, q == 0 ? pl.ctas_per_sm : 2);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev[q], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ev[q], 0);
+      if (e != cudaSuccess) {
+        st = fail(TSQR_ERR_CUDA, "factor launch %d: %s", q, cudaGetErrorString(e));
+        break;
+      }
+      for (int c0 = 0; c0 < kqb && st == TSQR_OK; c0 += group)
+        st = apply_launch(f, QB, ldqb, c0, std::min(group, kqb - c0), 1, 0, q, hs);
+    }
+    if (st == TSQR_OK) {
+      e = cudaEventRecord(ev[nl], hs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[nl], 0);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "helper stream join: %s", cudaGetErrorString(e));
+    }
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+  }
   if (st == TSQR_OK) {
     ProfScope ps(TSQR_PROF_SMALL, s);
     cudaError_t e = launch_extract_r(f->V, f->ldv, n, R, ldr, f->d, s);
+    if (e == cudaSuccess && QB) e = launch_scale_rows(QB, ldqb, n, kqb, f->d, s);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "extract_r: %s", cudaGetErrorString(e));
   }
   if (st != TSQR_OK) {
@@ -1120,6 +1202,23 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
   }
   *F = f;
   return TSQR_OK;
+}
+
+extern "C" {
+
+tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h, int32_t arity,
+                        int32_t prec, int32_t flags, void *stream, tsqr_factors **F, double *R, int64_t ldr) {
+  g_last_error.clear();
+  return factor_common(A, m, n, lda, leaf_h, arity, prec, flags, (cudaStream_t)stream, F, R, ldr, nullptr, 0, 0);
+}
+
+tsqr_status tsqr_factor_qt(const double *A, int64_t m, int32_t n, int64_t lda, double *B, int64_t ldb, int32_t k,
+                           int32_t leaf_h, int32_t arity, int32_t prec, int32_t flags, void *stream,
+                           tsqr_factors **F, double *R, int64_t ldr) {
+  g_last_error.clear();
+  if (!B || k < 1 || ldb < m) return fail(TSQR_ERR_ARG, "bad B, k=%d or ldb=%lld", k, (long long)ldb);
+  if (flags & TSQR_INPLACE) return fail(TSQR_ERR_ARG, "tsqr_factor_qt: TSQR_INPLACE is not supported");
+  return factor_common(A, m, n, lda, leaf_h, arity, prec, flags, (cudaStream_t)stream, F, R, ldr, B, ldb, k);
 }
 
 tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {

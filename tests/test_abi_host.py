@@ -198,6 +198,17 @@ def test_server_entry_points_reject_bad_arguments(lib):
     assert lib.tsqr_server_destroy(None) == 0
 
 
+def test_factor_qt_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    ptr = ctypes.c_void_p(256)
+    assert lib.tsqr_factor_qt(ptr, 100, 4, 100, None, 100, 1, 16, 2, 0, 0, None, ctypes.byref(h), None, 4) == 1
+    assert lib.tsqr_factor_qt(ptr, 100, 4, 100, ptr, 100, 0, 16, 2, 0, 0, None, ctypes.byref(h), None, 4) == 1
+    assert lib.tsqr_factor_qt(ptr, 100, 4, 100, ptr, 99, 1, 16, 2, 0, 0, None, ctypes.byref(h), None, 4) == 1
+    assert lib.tsqr_factor_qt(ptr, 100, 4, 100, ptr, 100, 1, 16, 2, 0, 1, None, ctypes.byref(h), None, 4) == 1
+    assert lib.tsqr_factor_qt(None, 100, 4, 100, ptr, 100, 1, 16, 2, 0, 0, None, ctypes.byref(h), None, 4) == 1
+    assert not h.value
+
+
 def test_autotuners_reject_bad_arguments(lib):
     L, a, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     item = _lib.BatchItem()                   # A = NULL: an invalid item

@@ -44,6 +44,29 @@ def test_apply_qt_unique_part(cuda_lib, m, n, h, arity, two, k):
     F.free()
 
 
+@pytest.mark.parametrize("m,n,h,arity,two,k", [(300_011, 64, 144, 2, True, 1), (50_003, 32, 100, 4, False, 12),
+                                               (20_000, 16, 256, 0, False, 3), (9_001, 7, 50, 3, True, 70)])
+def test_factor_qt_equals_factor_then_apply(cuda_lib, m, n, h, arity, two, k):
+    """tsqr_factor_qt overlaps Q^T B with the factorization's tree on a helper stream; its
+    R, B and factor set are bitwise those of tsqr_factor + tsqr_apply_qt."""
+    import paper_0912_2572_gb300 as ts
+    A = inputs.gaussian(m, n, 51)
+    B = inputs.gaussian(m, k, 52)
+    Ad = to_dev(A)
+    B1 = to_dev(B)
+    F1 = ts.factor(Ad, leaf_h=h, arity=arity, two_level=two)
+    F1.apply_qt(B1)
+    B2 = to_dev(B)
+    F2 = ts.factor(Ad, leaf_h=h, arity=arity, two_level=two, qt=B2)
+    assert np.array_equal(to_host(F2.R), to_host(F1.R))
+    assert np.array_equal(to_host(B2), to_host(B1))
+    top, _ = oracle.qt_b(A, B)
+    assert rel(to_host(B2)[:n], top) <= 1e-12
+    assert np.array_equal(to_host(F2.form_q()), to_host(F1.form_q()))
+    F1.free()
+    F2.free()
+
+
 @pytest.mark.parametrize("m,n,h,two", [(200_003, 16, 64, False), (131_077, 8, 32, True)])
 def test_apply_one_rhs_over_many_jobs(cuda_lib, m, n, h, two):
     """A single right-hand side over a chain launch of thousands of jobs (one warp per job),
