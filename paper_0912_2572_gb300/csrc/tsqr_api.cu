@@ -1148,10 +1148,12 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
       e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
     if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "event creation: %s", cudaGetErrorString(e));
     // the helper stream starts after everything already enqueued on s (QB's producers)
+    bool forked = false;
     if (st == TSQR_OK) {
       e = cudaEventRecord(ev[nl], s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ev[nl], 0);
       if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "helper stream fork: %s", cudaGetErrorString(e));
+      forked = e == cudaSuccess;
     }
     FactorParams p{};
     p.A = A;
@@ -1182,10 +1184,13 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
       for (int c0 = 0; c0 < kqb && st == TSQR_OK; c0 += group)
         st = apply_launch(f, QB, ldqb, c0, std::min(group, kqb - c0), 1, 0, q, hs);
     }
-    if (st == TSQR_OK) {
+    // joined even after a failed launch: the factor set's buffers are freed in the order
+    // of s, after whatever the helper stream still reads
+    if (forked) {
       e = cudaEventRecord(ev[nl], hs);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[nl], 0);
-      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "helper stream join: %s", cudaGetErrorString(e));
+      if (e != cudaSuccess && st == TSQR_OK)
+        st = fail(TSQR_ERR_CUDA, "helper stream join: %s", cudaGetErrorString(e));
     }
     for (cudaEvent_t x : ev)
       if (x) cudaEventDestroy(x);
