@@ -96,6 +96,7 @@ def parse(argv=None):
     p.add_argument("--sweep", default="", help="write a leaf-height x tree sweep (factor only) to this file")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
+    p.add_argument("--no-orth", action="store_true", help="skip the block-orthogonalization (Q-only TSQR) workload")
     p.add_argument("--batch-count", type=int, default=10000)
     p.add_argument("--no-serve", action="store_true", help="skip the served least-squares workload")
     p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
@@ -309,6 +310,42 @@ def bench_mixed_lsq(ts):
             "fp64_err_vs_oracle": float(np.linalg.norm(X64.cpu().numpy() - Xo) / nrm),
             "err_vs_oracle_per_step": per_step, "dx_over_x_per_step": steps,
             "fp64_gflops": fl / (t_64 * 1e-3) / 1e9}
+
+
+def bench_block_orth(ts, peak_tflops, elems=1 << 28, widths=(8, 16, 32, 64), reps=3):
+    """Q-only TSQR (tsqr_orthonormalize), the orthogonalization step of block iterative
+    methods: blocks of 2^28 FP64 entries (2 GiB) at n = 8, 16, 32, 64 columns, iid N(0,1)
+    drawn on the device from a seeded generator, orthonormalized out of place. Flops:
+    2 (2mn^2 - 2n^3/3) (factor + thin Q). The orthogonality ||Q^T Q - I||_F is checked
+    after the timed runs."""
+    import torch
+    out = {}
+    for n in widths:
+        m = elems // n
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9000 + n)
+        A = torch.randn((n, m), generator=g, dtype=torch.float64, device="cuda").t()
+        Q = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+        R = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+        leaf_h = ts.plan_describe(m, n, 4096, 2, True)["tile_rows"]
+        ts.orthonormalize(A, Q=Q, R=R, leaf_h=leaf_h, arity=2, two_level=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ts.orthonormalize(A, Q=Q, R=R, leaf_h=leaf_h, arity=2, two_level=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        fl = 2.0 * (2.0 * m * n * n - 2.0 * n ** 3 / 3.0)
+        orth = float(torch.linalg.norm(Q.t() @ Q - torch.eye(n, dtype=torch.float64, device="cuda")))
+        out[f"n{n}"] = {"m": m, "leaf_h": leaf_h, "ms": ms, "gflops": fl / (ms * 1e-3) / 1e9,
+                        "frac_of_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak_tflops, "orth_err": orth}
+        del A, Q, R
+        torch.cuda.empty_cache()
+    out["workload"] = ("Q-only TSQR of 2^28-entry FP64 blocks (m = 2^28 / n), iid N(0,1) from a seeded device "
+                       "generator, out of place, binary two-level tree on the on-chip tile; flops 2(2mn^2 - 2n^3/3)")
+    return out
 
 
 def bench_batched(ts, count):
@@ -838,6 +875,8 @@ def bench_ours(args):
     del Q
     mixed = None if args.no_mixed or rank != 0 else bench_mixed_lsq(ts)
     torch.cuda.empty_cache()
+    block_orth = None if args.no_orth or rank != 0 else bench_block_orth(ts, peak)
+    torch.cuda.empty_cache()
     batched = None if args.no_batch or rank != 0 else bench_batched(ts, args.batch_count)
     torch.cuda.empty_cache()
     served = None if args.no_serve or rank != 0 else bench_served(ts)
@@ -870,7 +909,8 @@ def bench_ours(args):
                                       "measured-peaks file has no FP64 entry",
                          "frac_of_derived": achieved / peak_derived},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
-            "factor_autotune": tuned, "mixed_lsq": mixed, "batched": batched, "served": served,
+            "factor_autotune": tuned, "mixed_lsq": mixed, "block_orth": block_orth, "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -127,6 +127,25 @@ tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t 
 tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *stream);
 
 /*
+ * tsqr_orthonormalize — Q-only TSQR: an orthonormal basis Q (m-by-n) of the columns of A,
+ * with A = Q R and diag(R) >= 0, as tsqr_factor followed by tsqr_form_q and tsqr_free in
+ * one call. This is the orthogonalization step of block iterative methods (block
+ * eigensolvers, block Krylov), the use the paper gives TSQR beside CAQR's panel (§2.5, §6).
+ *   A, m, n, lda, leaf_h, arity, flags  as tsqr_factor; TSQR_INPLACE is not supported.
+ *   prec       TSQR_FP64 only (TSQR_MIXED: TSQR_ERR_UNSUPPORTED).
+ *   Q          device, m-by-n column-major, ldq >= m, out. Q may alias A (Q == A and
+ *              ldq == lda orthonormalizes the block in place): A is fully read before Q is
+ *              written.
+ *   R          device n-by-n (ldr >= n), out, or NULL.
+ *   Stream-ordered; the factor set's scratch (m-by-n reflectors plus O(leaves * n)
+ *   scalars) is freed in stream order at the end of the call.
+ *   Errors: as tsqr_factor, plus TSQR_ERR_ARG for null Q or ldq < m.
+ */
+tsqr_status tsqr_orthonormalize(const double *A, int64_t m, int32_t n, int64_t lda, double *Q,
+                                int64_t ldq, double *R, int64_t ldr, int32_t leaf_h, int32_t arity,
+                                int32_t prec, int32_t flags, void *stream);
+
+/*
  * tsqr_lstsq — X = argmin ||A X - B||_F column by column: X = R^{-1} (Q^T B)[0:n].
  *   A          device m-by-n (lda >= m), not modified.
  *   B          device m-by-k (ldb >= m, 1 <= k <= 64), not modified.

@@ -18,7 +18,7 @@ from . import _lib
 
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
            "TSQRError", "profile_collect", "plan_describe", "batch_solve", "batch_autotune", "factor_autotune",
-           "AUTO", "BatchPlan", "Server", "probe_fp64_peak"]
+           "AUTO", "BatchPlan", "Server", "probe_fp64_peak", "orthonormalize"]
 
 FP64 = 0
 MIXED = 1
@@ -153,6 +153,28 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
                                 flags, _stream(stream), ctypes.byref(h), R.data_ptr(), ldr)
         _lib.check(st, "tsqr_factor_qt")
     return Factors(h, m, n, R, A if inplace else None, stream)
+
+
+def orthonormalize(A, Q=None, R=None, leaf_h: int = 256, arity: int = 2, two_level: bool = True,
+                   stream=None):
+    """Q-only TSQR (tsqr_orthonormalize): an orthonormal basis of the columns of the
+    column-major m-by-n float64 CUDA tensor A, A = Q R with diag(R) >= 0, the
+    orthogonalization step of block iterative methods (paper §2.5, §6). ``Q=A``
+    orthonormalizes A in place. Returns (Q, R)."""
+    import torch
+    lib = _lib.load()
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    if Q is None:
+        Q = torch.empty((n, m), dtype=torch.float64, device=A.device).t()
+    ldq = _check_mat(Q, "Q", rows=m, cols=n)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    ldr = _check_mat(R, "R", rows=n, cols=n)
+    flags = TWO_LEVEL if two_level else 0
+    _lib.check(lib.tsqr_orthonormalize(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(), ldr, leaf_h,
+                                       arity, FP64, flags, _stream(stream)), "tsqr_orthonormalize")
+    return Q, R
 
 
 PROFILE_KINDS = {0: "factor_chains", 1: "factor_tree", 2: "apply_qt", 3: "apply_q", 4: "form_q",

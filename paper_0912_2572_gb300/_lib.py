@@ -35,6 +35,7 @@ SIGNATURES = {
     "tsqr_apply_qt": (_i32, [_vp, _dp, _i64, _i32, _vp]),
     "tsqr_apply_q": (_i32, [_vp, _dp, _i64, _i32, _vp]),
     "tsqr_form_q": (_i32, [_vp, _dp, _i64, _vp]),
+    "tsqr_orthonormalize": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _dp, _i64, _i32, _i32, _i32, _i32, _vp]),
     "tsqr_lstsq": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _dp, _i64, _i32, _i32, _i32, _i32,
                           _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tsqr_solve_r": (_i32, [_vp, _dp, _i64, _i32, _dp, _i64, _dp, _vp]),

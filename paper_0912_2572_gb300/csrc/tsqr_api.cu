@@ -1262,6 +1262,23 @@ tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *str
   return run_apply(F, Q, ldq, F->plan().n, 0, 1, s);
 }
 
+tsqr_status tsqr_orthonormalize(const double *A, int64_t m, int32_t n, int64_t lda, double *Q, int64_t ldq,
+                                double *R, int64_t ldr, int32_t leaf_h, int32_t arity, int32_t prec,
+                                int32_t flags, void *stream) {
+  g_last_error.clear();
+  if (!Q || ldq < m) return fail(TSQR_ERR_ARG, "NULL Q or ldq=%lld < m=%lld", (long long)ldq, (long long)m);
+  if (flags & TSQR_INPLACE) return fail(TSQR_ERR_ARG, "tsqr_orthonormalize: TSQR_INPLACE is not supported");
+  cudaStream_t s = (cudaStream_t)stream;
+  tsqr_factors *F = nullptr;
+  tsqr_status st = factor_common(A, m, n, lda, leaf_h, arity, prec, flags, s, &F, R, ldr, nullptr, 0, 0);
+  if (st != TSQR_OK) return st;
+  // the factorization has read all of A before the first write to Q (stream order), and
+  // V is the factor set's own copy, so Q may alias A
+  st = tsqr_form_q(F, Q, ldq, stream);
+  factors_release(F);
+  return st;
+}
+
 tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, int32_t k, double *X, int64_t ldx,
                          int32_t *status, void *stream) {
   g_last_error.clear();

@@ -209,6 +209,18 @@ def test_factor_qt_rejects_bad_arguments(lib):
     assert not h.value
 
 
+def test_orthonormalize_rejects_bad_arguments(lib):
+    ptr = ctypes.c_void_p(256)
+    f = lib.tsqr_orthonormalize
+    assert f(ptr, 100, 4, 100, None, 100, None, 4, 16, 2, 0, 0, None) == 1     # Q NULL
+    assert f(ptr, 100, 4, 100, ptr, 99, None, 4, 16, 2, 0, 0, None) == 1       # ldq < m
+    assert f(ptr, 100, 4, 100, ptr, 100, None, 4, 16, 2, 0, 1, None) == 1      # INPLACE
+    assert f(None, 100, 4, 100, ptr, 100, None, 4, 16, 2, 0, 0, None) == 1     # A NULL
+    assert f(ptr, 100, 4, 100, ptr, 100, ptr, 3, 16, 2, 0, 0, None) == 1       # ldr < n
+    assert f(ptr, 3, 4, 3, ptr, 3, None, 4, 16, 2, 0, 0, None) == 1            # m < n
+    assert f(ptr, 100, 4, 100, ptr, 100, None, 4, 16, 2, 1, 0, None) == 6      # MIXED
+
+
 def test_autotuners_reject_bad_arguments(lib):
     L, a, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     item = _lib.BatchItem()                   # A = NULL: an invalid item
