@@ -339,8 +339,15 @@ def bench_block_orth(ts, peak_tflops, elems=1 << 28, widths=(8, 16, 32, 64), rep
         ms = e0.elapsed_time(e1) / reps
         fl = 2.0 * (2.0 * m * n * n - 2.0 * n ** 3 / 3.0)
         orth = float(torch.linalg.norm(Q.t() @ Q - torch.eye(n, dtype=torch.float64, device="cuda")))
+        _, prof = ts.profile_collect(lambda: ts.orthonormalize(A, Q=Q, R=R, leaf_h=leaf_h, arity=2,
+                                                               two_level=True))
+        torch.cuda.synchronize()
+        phases = {}
+        for kind, t in prof:
+            phases[kind] = phases.get(kind, 0.0) + t
         out[f"n{n}"] = {"m": m, "leaf_h": leaf_h, "ms": ms, "gflops": fl / (ms * 1e-3) / 1e9,
-                        "frac_of_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak_tflops, "orth_err": orth}
+                        "frac_of_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak_tflops, "orth_err": orth,
+                        "phases_ms": phases, "factor_autotune": ts.factor_autotune(A)}
         del A, Q, R
         torch.cuda.empty_cache()
     out["workload"] = ("Q-only TSQR of 2^28-entry FP64 blocks (m = 2^28 / n), iid N(0,1) from a seeded device "

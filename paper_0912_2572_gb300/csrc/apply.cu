@@ -7,9 +7,11 @@
 // everything in reverse.
 //
 // Two kernels:
-//   * k_apply_warp: one warp per job, for B with at most 8 columns. Each reflector is a
-//     dot product over the tile rows, one warp-level transpose-reduce, and an update; no
-//     block barrier is needed, so many jobs run per SM and hide the reduction latency.
+//   * k_apply_warp: one warp per job, for B with at most 8 columns, and for forming a
+//     thin Q of up to 16 columns in passes of 4. Each reflector is a dot product over the
+//     tile rows, one warp-level transpose-reduce, and an update; no block barrier is
+//     needed. One FP64 warp instruction per 64 cycles fills a sub-partition's FP64 pipe,
+//     so a warp per sub-partition keeps it busy without the block barriers of k_apply_tile.
 //   * k_apply_tile: one CTA per job and per pass of up to 64 columns, the structure of
 //     the factor kernel. Used for many right-hand sides and for forming Q. When forming
 //     Q every pivot-row block stays upper triangular (the root starts from
@@ -132,6 +134,55 @@ __host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2
   }
 
 // ------------------------------------------------------------- one warp per job
+// One reflector (pivot row j, tail xv over rows [lo, hi), tau, scale) applied to the NA
+// columns c0 .. c0 + NA - 1 of the warp's staged tile: dot products, one transpose-
+// reduce, the pivot-row update, then the tail update. NA is exact, so no column that the
+// reflector leaves unchanged issues an FMA (forming Q: reflector j touches columns >= j).
+template <int NA, int RW, typename R>
+__device__ __forceinline__ void warp_reflector(R *Bt, R *PR, int ldt, int n, int c0, bool ge, int j, int lo,
+                                               int hi, int lane, const R (&xv)[RW], R tau, R sc) {
+  constexpr int KP = pow2ceil(NA);
+  R part[KP];
+#pragma unroll
+  for (int a = 0; a < KP; ++a) part[a] = R(0);
+  R *Bc = Bt + (size_t)c0 * ldt;
+  const int ra = (hi - lo + 31) >> 5;
+#define TSQR_WDOT(r)                                                                        \
+  {                                                                                         \
+    const int i = lo + lane + 32 * (r);                                                     \
+    if (i < hi) {                                                                           \
+      _Pragma("unroll") for (int a = 0; a < NA; ++a) part[a] = fma(xv[r], Bc[a * ldt + i], part[a]); \
+    }                                                                                       \
+  }
+  TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
+#undef TSQR_WDOT
+  int idx;
+  const R tot = treduce32<KP, R>(part, lane, idx);
+  R cfv = R(0);
+  if ((lane & (32 / KP - 1)) == 0 && idx < NA) {
+    const int c = c0 + idx;
+    R *pp = ge ? &Bt[c * ldt + j] : &PR[c * n + j];
+    const R piv = *pp;
+    const R w = fma(sc, tot, piv);
+    *pp = fma(-tau, w, piv);
+    cfv = tau * sc * w;
+  }
+  R cf[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) cf[a] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(a));
+  __syncwarp();
+#define TSQR_WUPD(r)                                                                        \
+  {                                                                                         \
+    const int i = lo + lane + 32 * (r);                                                     \
+    if (i < hi) {                                                                           \
+      _Pragma("unroll") for (int a = 0; a < NA; ++a) Bc[a * ldt + i] = fma(-cf[a], xv[r], Bc[a * ldt + i]); \
+    }                                                                                       \
+  }
+  TSQR_ROW_SLOTS(ra, RW, TSQR_WUPD)
+#undef TSQR_WUPD
+  __syncwarp();
+}
+
 // Lane l handles rows lo + l + 32 r of each reflector's tail (RW slots at most, entered
 // through TSQR_ROW_SLOTS so only the needed slots issue); the K columns of B are exact.
 template <int K, int RW, typename R>
@@ -186,10 +237,13 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
       tau_d = __ldg(p.tau + td.refl + j);
       scl_d = __ldg(p.scl + td.refl + j);
     };
+    // forming Q (reverse order), the reflectors j >= col0 + K change none of the pass's
+    // columns: the pass starts after them
+    const int s_beg = (p.formq && !p.trans) ? max(0, n - (p.col0 + K)) : 0;
 #pragma unroll
     for (int d = 0; d < D; ++d)
-      if (d < n) load_refl(xb[d], tb[d], sb[d], d);
-    for (int s0 = 0; s0 < n; s0 += D) {
+      if (s_beg + d < n) load_refl(xb[d], tb[d], sb[d], s_beg + d);
+    for (int s0 = s_beg; s0 < n; s0 += D) {
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int s = s0 + d;
@@ -199,44 +253,19 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
         refl_rows(kind, j, ht, lo, hi, td.off);
         const R(&xv)[RW] = xb[d];
         const R tau = tb[d], sc = sb[d];
-        constexpr int KP = pow2ceil(K);
-        R part[KP];
-#pragma unroll
-        for (int c = 0; c < KP; ++c) part[c] = R(0);
-        const int ra = (hi - lo + 31) >> 5;
-#define TSQR_WDOT(r)                                                                        \
-  {                                                                                         \
-    const int i = lo + lane + 32 * (r);                                                     \
-    if (i < hi) {                                                                           \
-      _Pragma("unroll") for (int c = 0; c < K; ++c) part[c] = fma(xv[r], Bt[c * ldt + i], part[c]); \
-    }                                                                                       \
-  }
-        TSQR_ROW_SLOTS(ra, RW, TSQR_WDOT)
-#undef TSQR_WDOT
-        int idx;
-        const R tot = treduce32<KP, R>(part, lane, idx);
-        R cfv = R(0);
-        if ((lane & (32 / KP - 1)) == 0 && idx < K) {
-          R *pp = ge ? &Bt[idx * ldt + j] : &PR[idx * n + j];
-          const R piv = *pp;
-          const R w = fma(sc, tot, piv);
-          *pp = fma(-tau, w, piv);
-          cfv = tau * sc * w;
+        // forming Q, reflector j leaves the pass's columns below j unchanged
+        const int c0 = p.formq ? max(0, j - p.col0) : 0;
+        switch (K - c0) {
+          case 8: if (K >= 8) warp_reflector<(K >= 8 ? 8 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 7: if (K >= 7) warp_reflector<(K >= 7 ? 7 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 6: if (K >= 6) warp_reflector<(K >= 6 ? 6 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 5: if (K >= 5) warp_reflector<(K >= 5 ? 5 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 4: if (K >= 4) warp_reflector<(K >= 4 ? 4 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 3: if (K >= 3) warp_reflector<(K >= 3 ? 3 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 2: if (K >= 2) warp_reflector<(K >= 2 ? 2 : 1), RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          case 1: warp_reflector<1, RW, R>(Bt, PR, ldt, n, c0, ge, j, lo, hi, lane, xv, tau, sc); break;
+          default: break;
         }
-        R cf[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) cf[c] = __shfl_sync(kFull, cfv, treduce32_lane<KP>(c));
-        __syncwarp();
-#define TSQR_WUPD(r)                                                                        \
-  {                                                                                         \
-    const int i = lo + lane + 32 * (r);                                                     \
-    if (i < hi) {                                                                           \
-      _Pragma("unroll") for (int c = 0; c < K; ++c) Bt[c * ldt + i] = fma(-cf[c], xv[r], Bt[c * ldt + i]); \
-    }                                                                                       \
-  }
-        TSQR_ROW_SLOTS(ra, RW, TSQR_WUPD)
-#undef TSQR_WUPD
-        __syncwarp();
         if (s + D < n) load_refl(xb[d], tb[d], sb[d], s + D);
       }
     }
@@ -529,7 +558,7 @@ cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_s
                              cudaStream_t s) {
   if (njobs <= 0 || p.k <= 0) return cudaSuccess;
   if (p.ldt > 512) return cudaErrorInvalidValue;
-  if (p.k <= 8 && !p.formq) {
+  if (p.k <= 8) {
     switch (p.k) {
       case 1: return launch_warp_k<1, R>(p, njobs, s);
       case 2: return launch_warp_k<2, R>(p, njobs, s);
