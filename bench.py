@@ -97,6 +97,9 @@ def parse(argv=None):
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
     p.add_argument("--no-orth", action="store_true", help="skip the block-orthogonalization (Q-only TSQR) workload")
+    p.add_argument("--orth-only", action="store_true", help="run only the block-orthogonalization workload")
+    p.add_argument("--orth-elems", type=int, default=1 << 28, help="FP64 entries per block (m = elems / n)")
+    p.add_argument("--orth-widths", default="8,16,32,64", help="block widths n, comma-separated")
     p.add_argument("--batch-count", type=int, default=10000)
     p.add_argument("--no-serve", action="store_true", help="skip the served least-squares workload")
     p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
@@ -716,6 +719,12 @@ def bench_ours(args):
         if rank == 0:
             print(json.dumps({"served": bench_served(ts)}), flush=True)
         return 0
+    if args.orth_only:
+        if rank == 0:
+            widths = tuple(int(w) for w in args.orth_widths.split(","))
+            print(json.dumps({"block_orth": bench_block_orth(ts, ts.probe_fp64_peak(), args.orth_elems, widths)}),
+                  flush=True)
+        return 0
     if args.profile_batch:
         pool = make_served_pool(32, 11)
         items = [{"A": r["A"], "B": r["B"], "want_r": False, "prec": ts.MIXED} for r in pool]
@@ -882,7 +891,8 @@ def bench_ours(args):
     del Q
     mixed = None if args.no_mixed or rank != 0 else bench_mixed_lsq(ts)
     torch.cuda.empty_cache()
-    block_orth = None if args.no_orth or rank != 0 else bench_block_orth(ts, peak)
+    block_orth = None if args.no_orth or rank != 0 else bench_block_orth(
+        ts, peak, args.orth_elems, tuple(int(w) for w in args.orth_widths.split(",")))
     torch.cuda.empty_cache()
     batched = None if args.no_batch or rank != 0 else bench_batched(ts, args.batch_count)
     torch.cuda.empty_cache()

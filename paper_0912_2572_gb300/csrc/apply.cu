@@ -8,10 +8,11 @@
 //
 // Two kernels:
 //   * k_apply_warp: one warp per job, for B with at most 8 columns, and for forming a
-//     thin Q of up to 16 columns in passes of 4. Each reflector is a dot product over the
+//     thin Q of up to 32 columns in passes of 4. Each reflector is a dot product over the
 //     tile rows, one warp-level transpose-reduce, and an update; no block barrier is
-//     needed. One FP64 warp instruction per 64 cycles fills a sub-partition's FP64 pipe,
-//     so a warp per sub-partition keeps it busy without the block barriers of k_apply_tile.
+//     needed. With 4 columns a job stages 16.6 KB of a 512-row tile, so three CTAs of four
+//     jobs fit per SM, and the independent jobs of a sub-partition's three warps hide one
+//     another's reduction and shared-memory latency.
 //   * k_apply_tile: one CTA per job and per pass of up to 64 columns, the structure of
 //     the factor kernel. Used for many right-hand sides and for forming Q. When forming
 //     Q every pivot-row block stays upper triangular (the root starts from

@@ -440,11 +440,11 @@ static tsqr_status apply_launch(const tsqr_factors *F, double *B, int64_t ldb, i
 // B is processed in groups of at most 64 columns (8 for the warp kernel path)
 static int apply_group(int k) { return (k <= 8) ? 8 : 64; }
 
-// The thin Q of up to 16 columns is formed in passes of 4 columns by the warp kernel: at
+// The thin Q of up to 32 columns is formed in passes of 4 columns by the warp kernel: at
 // these widths the CTA kernel leaves most of its half-warps idle (reflector j touches
 // columns >= j only) between block barriers, and 4 columns per warp keep a job's staged
 // tile small enough for two or three CTAs of four jobs per SM.
-static int formq_group(int n) { return (n <= 16) ? 4 : 64; }
+static int formq_group(int n) { return (n <= 32) ? 4 : 64; }
 
 static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
                              cudaStream_t s) {
