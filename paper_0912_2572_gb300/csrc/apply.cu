@@ -20,79 +20,12 @@
 //     touches columns >= j and forming Q costs as many flops as the factorization, not
 //     twice as many.
 #include "tsqr_internal.h"
+#include "warp_reduce.cuh"
 
 namespace tsqr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// Transpose-reduce over a full warp (C a power of two <= 32); see treduce16 in the
-// factor kernel. The lane ends with the warp total of value idx.
-template <int C, typename R>
-__device__ __forceinline__ R treduce32(R (&v)[C], int lane, int &idx) {
-  idx = 0;
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int m = 16 >> s;
-    const int cs = (C >> s) > 1 ? (C >> s) : 1;
-    if (cs > 1) {
-      const int half = cs >> 1;
-      const bool up = (lane & m) != 0;
-#pragma unroll
-      for (int i = 0; i < C / 2; ++i) {
-        if (i < half) {
-          const R send = up ? v[i] : v[i + half];
-          const R keep = up ? v[i + half] : v[i];
-          v[i] = keep + __shfl_xor_sync(kFull, send, m);
-        }
-      }
-      if (up) idx += half;
-    } else {
-      v[0] += __shfl_xor_sync(kFull, v[0], m);
-    }
-  }
-  return v[0];
-}
-
-// Lowest lane that holds the total of value c after treduce32<C>.
-template <int C>
-__device__ __forceinline__ int treduce32_lane(int c) {
-  int lane = 0;
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int half = (C >> s) >> 1;
-    if (half >= 1 && (c & half)) lane |= (16 >> s);
-  }
-  return lane;
-}
-
-template <int C, typename R>
-__device__ __forceinline__ R treduce16(R (&v)[C], int hl, int &idx) {
-  idx = 0;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int m = 8 >> s;
-    const int cs = (C >> s) > 1 ? (C >> s) : 1;
-    if (cs > 1) {
-      const int half = cs >> 1;
-      const bool up = (hl & m) != 0;
-#pragma unroll
-      for (int i = 0; i < C / 2; ++i) {
-        if (i < half) {
-          const R send = up ? v[i] : v[i + half];
-          const R keep = up ? v[i + half] : v[i];
-          v[i] = keep + __shfl_xor_sync(kFull, send, m);
-        }
-      }
-      if (up) idx += half;
-    } else {
-      v[0] += __shfl_xor_sync(kFull, v[0], m);
-    }
-  }
-  return v[0];
-}
-
-__host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
 
 // Runs BODY(r) for r = ra-1 down to 0 (ra <= 32, warp-uniform) through a fall-through
 // switch: only the row slots the reflector needs are issued (a predicated-off FP64

@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "tsqr_internal.h"
+#include "warp_reduce.cuh"
 
 namespace tsqr {
 namespace {
@@ -48,38 +49,6 @@ __device__ __forceinline__ void warp_copy(double *dst, const double *src, int cn
     for (int i = lane; i < cnt; i += 32) dst[i] = ld1(src + i);
   }
 }
-
-// Transpose-reduce over the 16 lanes of a half-warp: each lane holds C partial sums
-// (C a power of two <= 16). Stage s exchanges half of the values with the lane whose
-// bit (8 >> s) differs and adds, until one value is left, then plain butterflies
-// finish the sum. The lane ends with the half-warp total of value `idx`.
-template <int C, typename R>
-__device__ __forceinline__ R treduce16(R (&v)[C], int hl, int &idx) {
-  idx = 0;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int m = 8 >> s;
-    const int cs = (C >> s) > 1 ? (C >> s) : 1;
-    if (cs > 1) {
-      const int half = cs >> 1;
-      const bool up = (hl & m) != 0;
-#pragma unroll
-      for (int i = 0; i < C / 2; ++i) {
-        if (i < half) {
-          const R send = up ? v[i] : v[i + half];
-          const R keep = up ? v[i + half] : v[i];
-          v[i] = keep + __shfl_xor_sync(kFull, send, m);
-        }
-      }
-      if (up) idx += half;
-    } else {
-      v[0] += __shfl_xor_sync(kFull, v[0], m);
-    }
-  }
-  return v[0];
-}
-
-__host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
 
 // Column slots. The FP64 job's column work is dealt to 14 worker half-warps (warps 0..6;
 // warp 7 is the scalar warp): worker rank v (0..13) owns columns cs + v + 14 t. The rank
@@ -641,7 +610,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_factor(const FactorParamsT<d
   extern __shared__ __align__(16) unsigned char smraw[];
   run_job<CMAX, true>(p, p.jobs[p.job0 + blockIdx.x], smraw);
 }
-
 
 // ----------------------------------------------------------- batched persistent kernel
 // Finishing an instance: R out with diag >= 0, and X = R^{-1} (Q^T B)[0:n] when the
