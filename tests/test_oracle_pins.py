@@ -204,6 +204,24 @@ def test_sign_of_zero_and_zero_column():
     assert oracle.backward_error(A, Q, R) <= 1e-15
 
 
+def test_thin_q_reflector_j_leaves_columns_below_j():
+    """Forming the thin Q applies H_{n-1} first: the reflectors j..n-1 leave column c < j of
+    [I_n; 0] exactly unchanged, since v_k is zero above row k (§4, Property 1: the thin Q
+    costs the factorization's flops, not twice them). Both thin-Q kernels skip those
+    columns."""
+    m, n = 200, 9
+    A = inputs.gaussian(m, n, 6)
+    VR, tau = oracle.householder(A)
+    E = np.zeros((m, n))
+    E[:n, :n] = np.eye(n)
+    for j in range(1, n):
+        t = tau.copy()
+        t[:j] = 0.0                                  # only H_j .. H_{n-1}
+        C = oracle.apply_q(VR, t, E)
+        assert np.array_equal(C[:, :j], E[:, :j])
+        assert not np.array_equal(C[:, j], E[:, j])  # column j is the first one touched
+
+
 def test_apply_roundtrip_and_thin_part():
     m, n, k = 300, 12, 3
     A = inputs.gaussian(m, n, 4)
