@@ -13,8 +13,9 @@ Definitions followed (see the C file's header for the detail):
   * TSQR reaches the same R and thin Q by an associative reduction (paper §2.3), so
     the oracle is the plain QR of the whole matrix.
   * Q^T b, Q b and the thin Q (paper §4, Table 2 and Property 1).
-  * Least squares through QR, and Bjorck augmented-system refinement around an
-    FP32 QR for the mixed-precision path (no counterpart in the paper).
+  * Least squares through QR, and two refinements around an FP32 QR for the
+    mixed-precision path (no counterpart in the paper): Bjorck's augmented system and
+    Bjorck's corrected semi-normal equations (the one the library runs).
 """
 from __future__ import annotations
 
@@ -73,6 +74,10 @@ def _load():
             "oracle_lstsq_refine_mixed": (ctypes.c_int, [_i64, _i64, _dp, _i64, _dp, _i32,
                                                          ctypes.c_double, _dp, _dp, _dp]),
             "oracle_lstsq_refine_x_only": (ctypes.c_int, [_i64, _i64, _dp, _i64, _dp, _i32, _dp, _dp]),
+            "oracle_lstsq_refine_csne": (ctypes.c_int, [_i64, _i64, _dp, _i64, _dp, _i32, ctypes.c_double,
+                                                        _dp, _dp]),
+            "oracle_apply_qt_f32": (None, [_i64, _i64, _fp, _i64, _fp, _fp]),
+            "oracle_apply_q_f32": (None, [_i64, _i64, _fp, _i64, _fp, _fp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -220,10 +225,21 @@ def lstsq(A, B):
 
 
 def trsv_upper(R, c):
+    """x with R x = c for upper-triangular R (back substitution)."""
     lib = _load()
     R = _f64(R)
     x = np.array(c, dtype=np.float64, copy=True)
     if lib.oracle_trsv_upper(R.shape[0], _p(R), R.shape[0], _p(x)):
+        raise np.linalg.LinAlgError("singular R")
+    return x
+
+
+def trsv_upper_t(R, g):
+    """x with R^T x = g for upper-triangular R (forward substitution)."""
+    lib = _load()
+    R = _f64(R)
+    x = np.array(g, dtype=np.float64, copy=True)
+    if lib.oracle_trsv_upper_t(R.shape[0], _p(R), R.shape[0], _p(x)):
         raise np.linalg.LinAlgError("singular R")
     return x
 
@@ -242,6 +258,22 @@ def lstsq_refine_mixed(A, b, max_steps: int = 10, tol: float = 1e-14):
     if steps < 0:
         raise np.linalg.LinAlgError("singular R in the FP32 factorization")
     return x, r, hist[:steps]
+
+
+def lstsq_refine_csne(A, b, max_steps: int = 10, tol: float = 1e-10):
+    """Corrected semi-normal equations iterated from x = 0 around the R of an FP32
+    Householder QR (Bjorck 1987), with the library's stopping rule.
+    Returns (x, hist) where hist[s] = ||dx||/||x|| after step s."""
+    lib = _load()
+    Aw = _f64(A)
+    m, n = Aw.shape
+    bw = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n)
+    hist = np.zeros(max(max_steps, 1))
+    steps = lib.oracle_lstsq_refine_csne(m, n, _p(Aw), m, _p(bw), max_steps, tol, _p(x), _p(hist))
+    if steps < 0:
+        raise np.linalg.LinAlgError("singular R in the FP32 factorization")
+    return x, hist[:steps]
 
 
 def lstsq_refine_x_only(A, b, max_steps: int = 10):
@@ -284,6 +316,28 @@ def geqr2_f32(A):
     tau = np.zeros(n, dtype=np.float32)
     lib.oracle_geqr2_f32(m, n, VR.ctypes.data_as(_fp), m, tau.ctypes.data_as(_fp))
     return VR, tau
+
+
+def apply_qt_f32(VR, tau, b):
+    """Q^T b in FP32 for the reflectors (VR, tau) of geqr2_f32 (one vector b)."""
+    lib = _load()
+    VR = np.array(VR, dtype=np.float32, order="F", copy=True)
+    tau = np.ascontiguousarray(tau, dtype=np.float32)
+    w = np.array(b, dtype=np.float32, copy=True)
+    m, n = VR.shape
+    lib.oracle_apply_qt_f32(m, n, VR.ctypes.data_as(_fp), m, tau.ctypes.data_as(_fp), w.ctypes.data_as(_fp))
+    return w
+
+
+def apply_q_f32(VR, tau, b):
+    """Q b in FP32 for the reflectors (VR, tau) of geqr2_f32 (one vector b)."""
+    lib = _load()
+    VR = np.array(VR, dtype=np.float32, order="F", copy=True)
+    tau = np.ascontiguousarray(tau, dtype=np.float32)
+    w = np.array(b, dtype=np.float32, copy=True)
+    m, n = VR.shape
+    lib.oracle_apply_q_f32(m, n, VR.ctypes.data_as(_fp), m, tau.ctypes.data_as(_fp), w.ctypes.data_as(_fp))
+    return w
 
 
 def normalised_r_from(VR) -> np.ndarray:

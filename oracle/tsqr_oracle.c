@@ -21,8 +21,9 @@
  *   - Mixed-precision least squares: an FP32 Householder QR used inside Bjorck's
  *     augmented-system iterative refinement with FP64 residuals and corrections
  *     (Bjorck 1967; Higham, "Accuracy and Stability of Numerical Algorithms",
- *     §20.5). The paper has no mixed-precision algorithm; this is the reading the
- *     library documents.
+ *     §20.5), and Bjorck's corrected semi-normal equations iterated around the R
+ *     of the same FP32 QR (Bjorck 1987), the refinement the library runs. The paper
+ *     has no mixed-precision algorithm; these are the readings the library documents.
  *   - Error measures ||A - QR||_F / ||A||_F and ||Q^T Q - I||_F, accumulated with
  *     Neumaier's compensated summation (Neumaier 1974).
  *
@@ -409,5 +410,71 @@ int oracle_lstsq_refine_x_only(int64_t m, int64_t n, const double *A, int64_t ld
     steps = s + 1;
   }
   free(A32); free(tau); free(w32); free(R); free(dx);
+  return steps;
+}
+
+/*
+ * Mixed-precision least squares by corrected semi-normal equations, iterated
+ * (Bjorck, "Stability analysis of the method of seminormal equations for linear least
+ * squares problems", 1987; Higham, "Accuracy and Stability", §20.6). This is the
+ * refinement the library runs; the paper has no mixed-precision algorithm. R is the R
+ * factor of an FP32 Householder QR of A (promoted to FP64, any diagonal signs); every
+ * other operation is FP64. From x = 0:
+ *   r = b - A x,  g = A^T r,  R^T y = g,  R d = y,  x <- x + d.
+ * Stopping rule (the library's reading): stop after the step whose ||d|| / ||x|| is
+ * <= 1e-15; or, from the second step on, once ||d|| / ||x|| times rho / (1 - rho) is
+ * <= tol with rho < 1/2, rho the largest ratio of successive corrections seen so far;
+ * or, from the third step on, once a correction exceeds half the previous one; or after
+ * max_steps steps. One right-hand side b (length m); x (n) is the output and hist[s]
+ * (length max_steps, may be NULL) receives ||d|| / ||x|| of step s. Returns the number
+ * of steps taken, or -4 if R is singular.
+ */
+int oracle_lstsq_refine_csne(int64_t m, int64_t n, const double *A, int64_t lda, const double *b,
+                             int32_t max_steps, double tol, double *x, double *hist) {
+  float *A32 = (float *)malloc(sizeof(float) * (size_t)(m * n));
+  float *tau = (float *)malloc(sizeof(float) * (size_t)n);
+  double *R = (double *)malloc(sizeof(double) * (size_t)(n * n));
+  double *r = (double *)malloc(sizeof(double) * (size_t)m);
+  double *y = (double *)malloc(sizeof(double) * (size_t)n);
+  double *h = (double *)malloc(sizeof(double) * (size_t)(max_steps > 0 ? max_steps : 1));
+  int steps = 0;
+  for (int64_t j = 0; j < n; j++)
+    for (int64_t i = 0; i < m; i++) A32[i + j * m] = (float)AT(A, i, j, lda);
+  oracle_geqr2_f32(m, n, A32, m, tau);
+  for (int64_t j = 0; j < n; j++)
+    for (int64_t i = 0; i < n; i++) R[i + j * n] = (i <= j) ? (double)A32[i + j * m] : 0.0;
+  for (int64_t i = 0; i < n; i++) x[i] = 0.0;
+  for (int32_t s = 0; s < max_steps; s++) {
+    for (int64_t i = 0; i < m; i++) {          /* r = b - A x */
+      double t = b[i];
+      for (int64_t j = 0; j < n; j++) t -= AT(A, i, j, lda) * x[j];
+      r[i] = t;
+    }
+    for (int64_t j = 0; j < n; j++) {          /* g = A^T r */
+      double t = 0.0;
+      for (int64_t i = 0; i < m; i++) t += AT(A, i, j, lda) * r[i];
+      y[j] = t;
+    }
+    if (oracle_trsv_upper_t(n, R, n, y) || oracle_trsv_upper(n, R, n, y)) { steps = -4; break; }
+    double nx = 0.0, nd = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+      x[i] += y[i];
+      nx += x[i] * x[i];
+      nd += y[i] * y[i];
+    }
+    const double ratio = nx > 0.0 ? sqrt(nd / nx) : (nd > 0.0 ? 1.0 : 0.0);
+    h[s] = ratio;
+    if (hist) hist[s] = ratio;
+    steps = s + 1;
+    if (ratio <= 1e-15) break;
+    if (s >= 1) {
+      double rho = 0.0;
+      for (int32_t q = 1; q <= s; q++)
+        if (h[q - 1] > 0.0) rho = fmax(rho, h[q] / h[q - 1]);
+      if (s >= 2 && ratio > 0.5 * h[s - 1]) break;
+      if (rho < 0.5 && ratio * rho / (1.0 - rho) <= tol) break;
+    }
+  }
+  free(A32); free(tau); free(R); free(r); free(y); free(h);
   return steps;
 }

@@ -280,6 +280,156 @@ def test_mixed_refinement_reaches_fp64_and_x_only_stalls():
     assert rel(x2, xo) > 1e-9
 
 
+# --------------------------------------------------------- error measures, pinned
+def exact_orth_error(Q):
+    """||Q^T Q - I||_F of a matrix with dyadic entries: the Gram matrix in exact
+    rationals (Fraction(float) is exact), one rounding in the final square root."""
+    m, n = Q.shape
+    Qf = [[Fraction(float(Q[i, j])) for j in range(n)] for i in range(m)]
+    s = Fraction(0)
+    for a in range(n):
+        for b in range(n):
+            g = sum(Qf[i][a] * Qf[i][b] for i in range(m)) - (1 if a == b else 0)
+            s += g * g
+    return math.sqrt(float(s))
+
+
+def test_orth_error_closed_forms():
+    """Q = c [I_n; 0] gives Q^T Q - I = (c^2 - 1) I, an error of sqrt(n) |c^2 - 1|; two
+    unit columns at inner product eps give sqrt(2) |eps| (the off-diagonal entry counts
+    twice); a Q with orthonormal columns gives 0."""
+    for n, c in ((5, 1.5), (8, 0.75), (3, 2.0)):
+        Q = np.zeros((20, n))
+        Q[:n, :n] = c * np.eye(n)
+        expect = math.sqrt(n) * abs(c * c - 1.0)
+        assert abs(oracle.orth_error(Q) - expect) <= 1e-15 * expect
+    eps = 2.0 ** -12
+    Q = np.zeros((4, 2))
+    Q[0, 0] = 1.0
+    Q[0, 1], Q[1, 1] = eps, math.sqrt(1.0 - eps * eps)
+    assert abs(oracle.orth_error(Q) - math.sqrt(2.0) * eps) <= 1e-9 * eps
+    E = np.zeros((10, 4))
+    E[[2, 5, 7, 9], [0, 1, 2, 3]] = [1.0, -1.0, 1.0, 1.0]
+    assert oracle.orth_error(E) == 0.0
+
+
+def test_orth_error_exact_rational():
+    """A dyadic 9-by-4 matrix: every term of ||Q^T Q - I||_F, diagonal and off-diagonal,
+    against the exact rational Gram matrix."""
+    Q = inputs.integer_matrix(9, 4, seed=12) / 8.0
+    assert abs(oracle.orth_error(Q) - exact_orth_error(Q)) <= 1e-14 * exact_orth_error(Q)
+    Q2 = np.eye(6, 3) + inputs.integer_matrix(6, 3, seed=13) / 64.0
+    assert abs(oracle.orth_error(Q2) - exact_orth_error(Q2)) <= 1e-14 * exact_orth_error(Q2)
+
+
+def test_trsv_upper_t_exact_rational():
+    """R^T x = g (forward substitution) against the exact rational solution for integer R
+    with a nonzero diagonal, and x = e_0 / r_00 for g = e_0 (only the first unknown is
+    then nonzero when R is diagonal)."""
+    n = 7
+    R = np.triu(inputs.integer_matrix(n, n, seed=14)).astype(np.float64)
+    R[np.arange(n), np.arange(n)] = np.where(np.diag(R) == 0, 3.0, np.diag(R))
+    g = inputs.integer_matrix(n, 1, seed=15)[:, 0].astype(np.float64)
+    Rf = [[Fraction(int(R[i, j])) for j in range(n)] for i in range(n)]
+    x = [Fraction(0)] * n
+    for i in range(n):  # column i of R holds row i of R^T
+        x[i] = (Fraction(int(g[i])) - sum(Rf[l][i] * x[l] for l in range(i))) / Rf[i][i]
+    xe = np.array([float(v) for v in x])
+    assert rel(oracle.trsv_upper_t(R, g), xe) <= 1e-14
+    D = np.diag(np.arange(1.0, n + 1))
+    assert np.array_equal(oracle.trsv_upper_t(D, np.eye(n)[0]), np.eye(n)[0])
+    with pytest.raises(np.linalg.LinAlgError):
+        Z = R.copy()
+        Z[3, 3] = 0.0
+        oracle.trsv_upper_t(Z, g)
+
+
+def test_raw_diagonal_sign_convention():
+    """Before sign normalisation, r_00 = -sign(a_00) ||a_0|| in both precisions (the
+    reflector's sign choice that avoids cancellation, sign(0) = +1)."""
+    A = inputs.gaussian(30, 3, 16)
+    for a00 in (2.5, -2.5, 0.0):
+        A[0, 0] = a00
+        nrm = float(np.linalg.norm(A[:, 0]))
+        expect = -(-1.0 if a00 < 0 else 1.0) * nrm
+        VR, _ = oracle.householder(A)
+        assert abs(VR[0, 0] - expect) <= 1e-15 * nrm
+        V32, _ = oracle.geqr2_f32(A)
+        assert abs(float(V32[0, 0]) - expect) <= 1e-6 * nrm
+
+
+# ------------------------------------------------------- the FP32 Householder QR
+U32 = 2.0 ** -24
+
+
+def test_geqr2_f32_against_fp64_and_exact():
+    """The FP32 QR of an input exact in FP32 (integers): R within the FP32 backward bound
+    of the exact rational R, and not at FP64 accuracy (every operation is FP32)."""
+    for shape, seed in (((12, 6), 3), ((40, 8), 17)):
+        A = inputs.integer_matrix(*shape, seed=seed).astype(np.float64)
+        if np.linalg.matrix_rank(A) < shape[1]:
+            continue
+        V32, _ = oracle.geqr2_f32(A)
+        err = rel(oracle.normalised_r_from(V32), exact_r(A))
+        assert 1e-11 < err <= 20 * shape[1] * U32
+
+
+def test_geqr2_f32_closed_form_and_reflectors():
+    """A = Q0 diag(d) (Q0 orthonormal, rounded to FP32) gives |R| = diag(|d|) to FP32
+    accuracy; Q^T A from the FP32 reflectors is [R; 0] and Q Q^T b = b, both within the
+    FP32 bound."""
+    Q0 = np.linalg.qr(inputs.gaussian(200, 8, 18))[0].astype(np.float32).astype(np.float64)
+    d = np.array([4.0, -2.0, 1.0, 0.5, -0.25, 3.0, -1.5, 2.0])
+    A = (Q0 * d[None, :]).astype(np.float32).astype(np.float64)
+    V32, tau = oracle.geqr2_f32(A)
+    R = oracle.normalised_r_from(V32)
+    assert rel(R, np.diag(np.abs(d))) <= 50 * 8 * U32
+    Rraw = np.triu(np.asarray(V32[:8], dtype=np.float64))
+    for j in range(8):
+        c = oracle.apply_qt_f32(V32, tau, A[:, j])
+        assert np.linalg.norm(c[:8] - Rraw[:, j]) <= 50 * U32 * np.linalg.norm(A[:, j])
+        assert np.linalg.norm(c[8:]) <= 50 * U32 * np.linalg.norm(A[:, j])
+    b = inputs.gaussian(200, 1, 19)[:, 0]
+    back = oracle.apply_q_f32(V32, tau, oracle.apply_qt_f32(V32, tau, b))
+    assert rel(back, b) <= 50 * U32
+
+
+def test_geqr2_f32_near_triangular_is_stable():
+    """The FP32 analogue of the near-triangular case: below-diagonal entries 1e-5 of the
+    diagonal, where the cancelling sign choice loses every digit of alpha - beta."""
+    n = 8
+    U = np.triu(inputs.gaussian(40, n, 3)[:n]) + 3 * np.eye(n)
+    A = np.vstack([U, np.zeros((32, n))]) + 1e-5 * np.tril(inputs.gaussian(40, n, 4), -1)
+    A = A.astype(np.float32).astype(np.float64)
+    V32, tau = oracle.geqr2_f32(A)
+    Rraw = np.triu(np.asarray(V32[:n], dtype=np.float64))
+    Q = np.column_stack([oracle.apply_q_f32(V32, tau, np.eye(40)[:, j]) for j in range(n)]).astype(np.float64)
+    assert np.all(np.isfinite(Rraw))
+    assert rel(Q @ Rraw, A) <= 50 * n * U32
+    assert oracle.orth_error(Q) <= 50 * n * U32
+
+
+# ---------------------------------- corrected semi-normal equations (the GPU's refinement)
+def test_csne_refinement_reaches_fp64_solution():
+    """CSNE iterated around the FP32 R reaches the FP64 least-squares solution for
+    kappa ~ 1e4 with a nonzero residual, each correction smaller than the last, within
+    a few steps; on a consistent well-conditioned system it returns x_true."""
+    A = inputs.graded(4000, 16, 4)
+    b, _ = inputs.lstsq_rhs(A, 1, 1e-6, 2)
+    xo = oracle.lstsq(A, b[:, 0])
+    x, hist = oracle.lstsq_refine_csne(A, b[:, 0], max_steps=10)
+    assert rel(x, xo) <= 1e-10
+    assert hist[0] == 1.0                     # from x = 0 the first correction is all of x
+    # the unblocked FP32 R (4000-term FP32 sums) perturbs the first step most; from the
+    # second correction on each one is smaller than the last
+    assert all(hist[s + 1] < hist[s] for s in range(1, len(hist) - 1))
+    assert hist[-1] <= 1e-13
+    A2 = inputs.graded(1500, 12, 2)
+    x_true = inputs.gaussian(12, 1, 20)[:, 0]
+    x2, _ = oracle.lstsq_refine_csne(A2, A2 @ x_true, max_steps=10)
+    assert rel(x2, x_true) <= 1e-12
+
+
 def test_thread_count_does_not_change_results():
     code = ("import numpy as np, oracle; from paper_0912_2572_gb300 import inputs;"
             "Q,R,_=oracle.qr(inputs.gaussian(3000,24,1)); print(repr(float(np.sum(R*np.arange(1,577).reshape(24,24)))))")
@@ -305,6 +455,21 @@ MUTANTS = {
                            "kahan_add(&qr, &cq, AT(Q, i, l, ldq) * AT(R, j, l, ldr));"),
     "apply_order": ("for (int64_t j = n - 1; j >= 0; j--) {\n#pragma omp parallel for schedule(static)\n    for (int64_t c = 0; c < k; c++) reflect_column(m, j, V, ldv, tau[j], &AT(B, 0, c, ldb));",
                     "for (int64_t j = 0; j < n; j++) {\n#pragma omp parallel for schedule(static)\n    for (int64_t c = 0; c < k; c++) reflect_column(m, j, V, ldv, tau[j], &AT(B, 0, c, ldb));"),
+    "orth_offdiag_weight": ("kahan_add(&s, &c, (a == b ? 1.0 : 2.0) * e * e);",
+                            "kahan_add(&s, &c, e * e);"),
+    "orth_diagonal_only": ("for (int64_t b = a; b < n; b++) {\n      double g = 0.0, cg = 0.0;",
+                           "for (int64_t b = a; b <= a; b++) {\n      double g = 0.0, cg = 0.0;"),
+    "orth_identity_dropped": ("double e = (g + cg) - (a == b ? 1.0 : 0.0);", "double e = (g + cg);"),
+    "trsv_t_transposed": ("for (int64_t l = 0; l < i; l++) s -= AT(R, l, i, ldr) * x[l];",
+                          "for (int64_t l = 0; l < i; l++) s -= AT(R, i, l, ldr) * x[l];"),
+    "f32_beta_sign": ("float beta = -(alpha < 0.0f ? -1.0f : 1.0f) * hypotf(alpha, sigma);",
+                      "float beta = (alpha < 0.0f ? -1.0f : 1.0f) * hypotf(alpha, sigma);"),
+    "f32_tau_formula": ("hypotf(alpha, sigma);\n      tau[j] = (beta - alpha) / beta;",
+                        "hypotf(alpha, sigma);\n      tau[j] = (beta - alpha) / alpha;"),
+    "f32_dropped_pivot_term": ("float w = Bc[j];", "float w = 0.0f;"),
+    "f32_scale_denominator": ("float denom = alpha - beta;", "float denom = beta;"),
+    "csne_gradient_sign": ("for (int64_t i = 0; i < m; i++) t += AT(A, i, j, lda) * r[i];\n      y[j] = t;",
+                           "for (int64_t i = 0; i < m; i++) t -= AT(A, i, j, lda) * r[i];\n      y[j] = t;"),
     "scale_denominator": ("for (int64_t i = 1; i < m - j; i++) x[i] = x[i] / denom;",
                           "for (int64_t i = 1; i < m - j; i++) x[i] = x[i] / beta;"),
 }
@@ -329,6 +494,14 @@ run("near_triangular", t.test_near_triangular_input_is_stable)
 run("invariants", lambda: t.test_invariants(500, 16, 0))
 run("apply", t.test_apply_roundtrip_and_thin_part)
 run("lstsq", t.test_lstsq_consistent_system_and_lapack)
+run("orth_closed", t.test_orth_error_closed_forms)
+run("orth_exact", t.test_orth_error_exact_rational)
+run("trsv_t", t.test_trsv_upper_t_exact_rational)
+run("raw_sign", t.test_raw_diagonal_sign_convention)
+run("f32_exact", t.test_geqr2_f32_against_fp64_and_exact)
+run("f32_closed", t.test_geqr2_f32_closed_form_and_reflectors)
+run("f32_near_triangular", t.test_geqr2_f32_near_triangular_is_stable)
+run("csne", t.test_csne_refinement_reaches_fp64_solution)
 print("FAILED:" + ",".join(failed))
 """
 
