@@ -196,14 +196,17 @@ tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, in
  *      n >= 1, k >= 1, n + k <= 128. A and B are not modified.
  *   The scratch needed is about 8 * m * (n + k) bytes plus the plan: for n = 64, k = 1
  *   at most about 129,000 rows.
- *   The first call on a device looks up the array's address with that device current;
- *   make that first call before any stream capture. All calls share the array and it
- *   keeps the previous call's contents: calls that may overlap on the GPU (several
- *   streams or host threads) race and must be serialized by the caller. The call waits
- *   for its stream to finish (it reads back the singularity flag).
- *   Errors: TSQR_ERR_ARG (null pointers, bad sizes or leading dimensions),
- *           TSQR_ERR_UNSUPPORTED (the problem needs more scratch than the static array
- *           holds; nothing is enqueued), TSQR_ERR_SINGULAR, TSQR_ERR_CUDA.
+ *   The stream must belong to the current device. The first call on a device looks up the
+ *   array's address with that device current. Every call waits for its stream to finish
+ *   (it reads back the singularity flag), so no call, the first one included, may be made
+ *   on a stream that is being captured into a CUDA graph. All calls share the array and
+ *   it keeps the previous call's contents: calls that may overlap on the GPU (several
+ *   streams or host threads) race and must be serialized by the caller. A call that
+ *   fails after enqueuing work waits for its stream before it returns.
+ *   Errors (described by tsqr_last_error): TSQR_ERR_ARG (null pointers, bad sizes or
+ *           leading dimensions, a stream of another device), TSQR_ERR_UNSUPPORTED (the
+ *           problem needs more scratch than the static array holds; nothing is
+ *           enqueued), TSQR_ERR_SINGULAR, TSQR_ERR_CUDA.
  */
 tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, int64_t lda,
                               const double *B, int64_t ldb, int32_t k, double *X,

@@ -14,13 +14,18 @@
 // Costs and rules of use:
 //   * every GPU that loads the library holds the array (64 MiB) until the process exits;
 //   * the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current, so make the first call before any
-//     stream capture;
+//     (cudaGetSymbolAddress) with that device current; the stream passed must belong to
+//     the current device (checked);
+//   * every call waits for its stream (it reads back the singularity flag), so no call,
+//     the first included, can be made on a stream that is being captured into a graph;
 //   * every call shares the one array, which keeps the previous call's contents: calls
 //     that can overlap on the GPU (different streams, or several host threads) race on
-//     it and must be serialized by the caller; host-side use is serialized by a mutex;
+//     it and must be serialized by the caller; host-side use is serialized by a mutex,
+//     and a call that fails after enqueuing work waits for its stream before returning,
+//     so that work never overlaps the next call;
 //   * problems whose scratch exceeds the array, or whose plan exceeds the fixed host
-//     arrays, are rejected with TSQR_ERR_UNSUPPORTED before any work is enqueued.
+//     arrays, are rejected with TSQR_ERR_UNSUPPORTED before any work is enqueued;
+//   * errors are described by tsqr_last_error(), whose buffer is fixed (no allocation).
 #include <mutex>
 
 #include "../../include/tsqr.h"
@@ -99,18 +104,28 @@ bool build_plan(int64_t m, int n, int tile_h, int64_t chains_target, int &ntiles
 
 extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, int64_t lda, const double *B,
                                          int64_t ldb, int32_t k, double *X, int64_t ldx, void *stream) {
-  if (!A || !B || !X) return TSQR_ERR_ARG;
-  if (n < 1 || k < 1 || n + k > 128) return TSQR_ERR_ARG;
-  if (m < n || lda < m || ldb < m || ldx < n) return TSQR_ERR_ARG;
+  clear_last_error();
+  if (!A || !B || !X) return set_last_error(TSQR_ERR_ARG, "A, B or X is NULL");
+  if (n < 1 || k < 1 || n + k > 128) return set_last_error(TSQR_ERR_ARG, "n=%d, k=%d: need n, k >= 1 and n + k <= 128", n, k);
+  if (m < n || lda < m || ldb < m || ldx < n)
+    return set_last_error(TSQR_ERR_ARG, "bad sizes: m=%lld n=%d lda=%lld ldb=%lld ldx=%lld", (long long)m, n,
+                          (long long)lda, (long long)ldb, (long long)ldx);
   cudaStream_t s = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_mu);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return TSQR_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_last_error(TSQR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_last_error(TSQR_ERR_UNSUPPORTED, "device %d >= %d", dev, kMaxDevices);
+  int sdev = dev;
+  e = cudaStreamGetDevice(s, &sdev);
+  if (e != cudaSuccess) return set_last_error(TSQR_ERR_CUDA, "cudaStreamGetDevice: %s", cudaGetErrorString(e));
+  if (sdev != dev)
+    return set_last_error(TSQR_ERR_ARG, "the stream belongs to device %d, the current device is %d", sdev, dev);
   if (!g_dev_ptr[dev]) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) return TSQR_ERR_CUDA;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return set_last_error(TSQR_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
     g_dev_ptr[dev] = p;
   }
   int sms = 0, smem_sm = 0, reserved = 0, optin = 0;
@@ -118,13 +133,15 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return TSQR_ERR_CUDA;
+    return set_last_error(TSQR_ERR_CUDA, "device %d attributes", dev);
   const int nc = n + k;
   int cps = 0, tile_h = 0;
-  if (!factor_tile_choice(n, nc, 1 << 20, smem_sm, reserved, optin, 3, tile_h, cps)) return TSQR_ERR_UNSUPPORTED;
+  if (!factor_tile_choice(n, nc, 1 << 20, smem_sm, reserved, optin, 3, tile_h, cps))
+    return set_last_error(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for n + k = %d", nc);
   int ntiles = 0, njobs = 0, nlaunches = 0;
   if (!build_plan(m, n, tile_h, (int64_t)sms * cps * 4, ntiles, njobs, nlaunches))
-    return TSQR_ERR_UNSUPPORTED;
+    return set_last_error(TSQR_ERR_UNSUPPORTED, "m=%lld needs more than %d tiles or %d jobs", (long long)m, kMaxTiles,
+                          kMaxJobs);
   // scratch layout inside the static array
   const size_t o_status = 0;
   const size_t o_jobs = o_status + 256;
@@ -134,7 +151,9 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
   const size_t o_V = o_scl + up256(sizeof(double) * ntiles * n);
   const size_t o_W = o_V + up256(sizeof(double) * (size_t)m * n);
   const size_t need = o_W + up256(sizeof(double) * (size_t)m * k);
-  if (need > kStaticScratchBytes) return TSQR_ERR_UNSUPPORTED;
+  if (need > kStaticScratchBytes)
+    return set_last_error(TSQR_ERR_UNSUPPORTED, "scratch of %zu bytes exceeds the %zu-byte static array", need,
+                          kStaticScratchBytes);
   char *base = (char *)g_dev_ptr[dev];
   int32_t *status = (int32_t *)(base + o_status);
   JobDesc *djobs = (JobDesc *)(base + o_jobs);
@@ -142,9 +161,15 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
   double *tau = (double *)(base + o_tau), *scl = (double *)(base + o_scl);
   double *V = (double *)(base + o_V), *W = (double *)(base + o_W);
 
-#define STATIC_TRY(expr)                     \
-  do {                                       \
-    if ((expr) != cudaSuccess) return TSQR_ERR_CUDA; \
+  // once work is enqueued, a failing step waits for the stream before returning, so that
+  // nothing of this call still uses the shared array when the next call starts
+#define STATIC_TRY(expr)                                                                \
+  do {                                                                                  \
+    const cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                            \
+      cudaStreamSynchronize(s);                                                         \
+      return set_last_error(TSQR_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+    }                                                                                   \
   } while (0)
 
   // the previous call's contents stay in the array: clear the status word, and copy
@@ -177,6 +202,6 @@ extern "C" tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, 
   STATIC_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   STATIC_TRY(cudaStreamSynchronize(s));
 #undef STATIC_TRY
-  if (hstatus == 4) return TSQR_ERR_SINGULAR;
+  if (hstatus == 4) return set_last_error(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
   return TSQR_OK;
 }

@@ -19,15 +19,25 @@ using namespace tsqr;
 
 namespace {
 
-thread_local std::string g_last_error;
+// The calling thread's last error message, in a fixed buffer: setting or clearing it
+// never allocates (the allocation-free entry point reports through it too).
+struct ErrorText {
+  char buf[512];
+  void clear() { buf[0] = 0; }
+  const char *c_str() const { return buf; }
+  void vset(const char *fmt, va_list ap) {
+    char tmp[sizeof buf];  // the arguments may point into buf
+    vsnprintf(tmp, sizeof tmp, fmt, ap);
+    memcpy(buf, tmp, sizeof buf);
+  }
+};
+thread_local ErrorText g_last_error = {{0}};
 
 tsqr_status fail(tsqr_status s, const char *fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  g_last_error.vset(fmt, ap);
   va_end(ap);
-  g_last_error = buf;
   return s;
 }
 
@@ -1043,6 +1053,16 @@ size_t tsqr::batch_item_bytes(const tsqr_batch_item &it) {
 }
 
 const char *tsqr::last_error_text() { return g_last_error.c_str(); }
+
+tsqr_status tsqr::set_last_error(tsqr_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  g_last_error.vset(fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+void tsqr::clear_last_error() { g_last_error.clear(); }
 
 extern "C" {
 

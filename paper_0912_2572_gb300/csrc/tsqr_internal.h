@@ -194,6 +194,9 @@ tsqr_status check_batch_item(const tsqr_batch_item &it, int32_t q);
 size_t batch_item_bytes(const tsqr_batch_item &it);  // device workspace estimate for admission
 int32_t resolve_batch_prec(const tsqr_batch_item &it);  // TSQR_FP64 or TSQR_MIXED
 const char *last_error_text();
+// the calling thread's error message (tsqr_last_error) for entry points outside tsqr_api.cu
+tsqr_status set_last_error(tsqr_status s, const char *fmt, ...);
+void clear_last_error();
 
 // ------------------------------------------------------------------ apply kernels
 template <typename R>

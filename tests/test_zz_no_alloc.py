@@ -77,6 +77,30 @@ def test_static_matches_lstsq_on_two_calls(cuda_lib):
         assert np.array_equal(to_host(Bd), B)  # the caller's B is untouched
 
 
+def test_static_single_tile_and_singular(cuda_lib):
+    """A problem shorter than one on-chip tile (a one-job plan with no tree) against the
+    oracle, a square problem, then an A with a zero column: R then has an exactly zero
+    diagonal entry and the call reports TSQR_ERR_SINGULAR with a message."""
+    import torch
+    lib = cuda_lib
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for m, n, k, seed in ((100, 8, 2, 31), (24, 24, 1, 32)):
+        A = inputs.gaussian(m, n, seed)
+        B = inputs.gaussian(m, k, seed + 1)
+        Ad, Bd = to_dev(A), to_dev(B)
+        Xd = torch.full((k, n), float("nan"), dtype=torch.float64, device="cuda").t()
+        assert _static(lib, Ad, Bd, Xd, stream) == 0
+        torch.cuda.synchronize()
+        assert lib.tsqr_last_error() == b""
+        assert rel(to_host(Xd), oracle.lstsq(A, B)) <= (1e-10 if m == n else TOL)
+    A = inputs.gaussian(3000, 6, 33)
+    A[:, 2] = 0.0
+    B = inputs.gaussian(3000, 1, 34)
+    Xd = torch.zeros((1, 6), dtype=torch.float64, device="cuda").t()
+    assert _static(lib, to_dev(A), to_dev(B), Xd, stream) == 4
+    assert b"zero diagonal" in lib.tsqr_last_error()
+
+
 def test_static_refuses_oversized_problem(cuda_lib):
     import torch
     lib = cuda_lib
@@ -84,5 +108,7 @@ def test_static_refuses_oversized_problem(cuda_lib):
     # 2,000,000 x 64 needs about 1 GB of scratch: refused, nothing enqueued
     st = lib.tsqr_lstsq_static(4096, 2_000_000, 64, 2_000_000, 4096, 2_000_000, 1, 4096, 64, stream)
     assert st == 6
+    assert b"exceeds" in lib.tsqr_last_error()
     assert lib.tsqr_lstsq_static(None, 10, 2, 10, 4096, 10, 1, 4096, 2, stream) == 1
+    assert lib.tsqr_last_error() != b""
     assert lib.tsqr_lstsq_static(4096, 10, 100, 10, 4096, 10, 40, 4096, 100, stream) == 1
