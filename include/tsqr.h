@@ -90,6 +90,35 @@ tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int3
                         tsqr_factors **F, double *R, int64_t ldr);
 
 /*
+ * tsqr_caqr — QR factorization A = Q R of a wider m-by-n matrix (n up to 4096) by CAQR,
+ * the communication-avoiding QR whose panel factorization is TSQR (paper §2.4; the
+ * switch from TSQR to CAQR for large n, §6, and Property 5 of §4). The columns are split
+ * into panels of `panel` columns. Panel p (its columns, rows p*panel..m-1 of the updated
+ * matrix) is factored by TSQR as tsqr_factor does, and its Q_p^T is applied to the
+ * trailing columns (the trailing-matrix update, overlapped with the panel's reduction
+ * tree as in tsqr_factor_qt); the top `panel` rows of the updated trailing columns are
+ * rows of R, and the next panel is the trailing block below them. Q = Q_0 Q_1 ... with
+ * each Q_p acting on rows p*panel..m-1.
+ *   A       device, m-by-n column-major FP64, lda >= m. Read only, unless flags has
+ *           TSQR_INPLACE: A then receives every panel's reflectors and trailing updates.
+ *           Otherwise the factor set holds an m-by-n working copy.
+ *   m, n    1 <= n <= 4096, m >= n.
+ *   panel   columns per panel, 1..128; 0 = 64.
+ *   leaf_h, arity, flags (TSQR_INPLACE | TSQR_TWO_LEVEL)  as tsqr_factor, for every
+ *           panel; leaf_h >= min(panel, n).
+ *   F       out: a factor set that tsqr_apply_qt, tsqr_apply_q, tsqr_form_q,
+ *           tsqr_solve_r, tsqr_factors_info and tsqr_free take like a TSQR one
+ *           (tsqr_factors_info reports totals over the panels).
+ *   R       device, n-by-n (ldr >= n), out: R with diag(R) >= 0, zeros below. May be NULL.
+ *   Errors: TSQR_ERR_ARG (n outside [1, 4096], m < n, lda < m, panel outside [0, 128],
+ *           leaf_h below the panel width, bad arity or flags, null A or F), TSQR_ERR_OOM,
+ *           TSQR_ERR_CUDA.
+ */
+tsqr_status tsqr_caqr(const double *A, int64_t m, int32_t n, int64_t lda, int32_t panel, int32_t leaf_h,
+                      int32_t arity, int32_t flags, void *stream, tsqr_factors **F, double *R,
+                      int64_t ldr);
+
+/*
  * tsqr_apply_qt — B <- Q^T B for the m-by-m orthogonal Q of F (paper §4, Table 2).
  *   B  device, m-by-k column-major, ldb >= m, 1 <= k. Rows 0..n-1 of the result are
  *      Q_thin^T B with the sign convention diag(R) >= 0; the other rows hold B's
@@ -132,6 +161,7 @@ tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *str
  * one call. This is the orthogonalization step of block iterative methods (block
  * eigensolvers, block Krylov), the use the paper gives TSQR beside CAQR's panel (§2.5, §6).
  *   A, m, n, lda, leaf_h, arity, flags  as tsqr_factor; TSQR_INPLACE is not supported.
+ *              n > 128 (up to 4096) runs tsqr_caqr with the default panel width.
  *   prec       TSQR_FP64 only (TSQR_MIXED: TSQR_ERR_UNSUPPORTED).
  *   Q          device, m-by-n column-major, ldq >= m, out. Q may alias A (Q == A and
  *              ldq == lda orthonormalizes the block in place): A is fully read before Q is
@@ -147,7 +177,9 @@ tsqr_status tsqr_orthonormalize(const double *A, int64_t m, int32_t n, int64_t l
 
 /*
  * tsqr_lstsq — X = argmin ||A X - B||_F column by column: X = R^{-1} (Q^T B)[0:n].
- *   A          device m-by-n (lda >= m), not modified.
+ *   A          device m-by-n (lda >= m), not modified. n > 128 (up to 4096, TSQR_FP64
+ *              only; TSQR_MIXED: TSQR_ERR_UNSUPPORTED) is factored by tsqr_caqr with the
+ *              default panel width, then Q^T B and the back substitution.
  *   B          device m-by-k (ldb >= m, 1 <= k <= 64), not modified.
  *   X          device n-by-k (ldx >= n), out.
  *   leaf_h, arity, flags as in tsqr_factor (TSQR_INPLACE is ignored).

@@ -16,7 +16,7 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "lstsq", "colmajor",
+__all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "caqr", "lstsq", "colmajor",
            "TSQRError", "profile_collect", "plan_describe", "batch_solve", "batch_autotune", "factor_autotune",
            "AUTO", "BatchPlan", "Server", "probe_fp64_peak", "orthonormalize"]
 
@@ -152,6 +152,26 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
         st = lib.tsqr_factor_qt(A.data_ptr(), m, n, lda, qt.data_ptr(), ldq, qt.shape[1], leaf_h, arity, FP64,
                                 flags, _stream(stream), ctypes.byref(h), R.data_ptr(), ldr)
         _lib.check(st, "tsqr_factor_qt")
+    return Factors(h, m, n, R, A if inplace else None, stream)
+
+
+def caqr(A, panel: int = 0, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace: bool = False,
+         R=None, stream=None) -> Factors:
+    """CAQR factorization (tsqr_caqr, paper §2.4) of a column-major m-by-n float64 CUDA
+    tensor A with n up to 4096: TSQR of panels of ``panel`` columns (0 = 64), each panel's
+    Q^T applied to the trailing columns. Returns a Factors object (apply_qt, apply_q,
+    form_q, solve_r work as for ``factor``) whose ``R`` is n-by-n with diag >= 0."""
+    import torch
+    lib = _lib.load()
+    lda = _check_mat(A, "A")
+    m, n = A.shape
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
+    ldr = _check_mat(R, "R", rows=n, cols=n)
+    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0)
+    h = ctypes.c_void_p()
+    _lib.check(lib.tsqr_caqr(A.data_ptr(), m, n, lda, panel, leaf_h, arity, flags, _stream(stream), ctypes.byref(h),
+                             R.data_ptr(), ldr), "tsqr_caqr")
     return Factors(h, m, n, R, A if inplace else None, stream)
 
 

@@ -32,6 +32,7 @@ SIGNATURES = {
                            ctypes.POINTER(_vp), _dp, _i64]),
     "tsqr_factor_qt": (_i32, [_dp, _i64, _i32, _i64, _dp, _i64, _i32, _i32, _i32, _i32, _i32, _vp,
                               ctypes.POINTER(_vp), _dp, _i64]),
+    "tsqr_caqr": (_i32, [_dp, _i64, _i32, _i64, _i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp), _dp, _i64]),
     "tsqr_apply_qt": (_i32, [_vp, _dp, _i64, _i32, _vp]),
     "tsqr_apply_q": (_i32, [_vp, _dp, _i64, _i32, _vp]),
     "tsqr_form_q": (_i32, [_vp, _dp, _i64, _vp]),

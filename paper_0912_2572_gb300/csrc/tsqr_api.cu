@@ -366,7 +366,17 @@ struct tsqr_factors {
   bool owns_V = false;
   double *tau = nullptr, *scl = nullptr, *d = nullptr;
   void *block = nullptr;  // one allocation for tau, scl, d
+  // CAQR (tsqr_caqr): the TSQR factor sets of the panels in order; panel p covers columns
+  // p*panel.. and rows p*panel..m-1 of V, the m-by-ncols working copy that holds every
+  // panel's reflectors. Rfull is the ncols-by-ncols R with diag >= 0.
+  std::vector<tsqr_factors *> panels;
+  int32_t panel = 0, ncols = 0;
+  int64_t mrows = 0;
+  double *Rfull = nullptr;
+  bool caqr() const { return !panels.empty(); }
   const Plan &plan() const { return dp->plan; }
+  int64_t rows() const { return caqr() ? mrows : dp->plan.m; }
+  int32_t cols() const { return caqr() ? ncols : dp->plan.n; }
 };
 
 static tsqr_status factors_alloc(tsqr_factors *F, cudaStream_t s) {
@@ -384,6 +394,8 @@ static tsqr_status factors_alloc(tsqr_factors *F, cudaStream_t s) {
 
 static void factors_release(tsqr_factors *F) {
   if (!F) return;
+  for (tsqr_factors *P : F->panels) factors_release(P);
+  if (F->Rfull) cudaFreeAsync(F->Rfull, F->stream);
   if (F->block) cudaFreeAsync(F->block, F->stream);
   if (F->owns_V && F->V) cudaFreeAsync(F->V, F->stream);
   delete F;
@@ -471,7 +483,7 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
 static tsqr_status check_factor_args(const void *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h,
                                      int32_t arity) {
   if (!A) return fail(TSQR_ERR_ARG, "A is NULL");
-  if (n < 1 || n > 128) return fail(TSQR_ERR_ARG, "n=%d outside [1, 128]", n);
+  if (n < 1 || n > 128) return fail(TSQR_ERR_ARG, "n=%d outside [1, 128] (tsqr_caqr factors wider matrices)", n);
   if (m < n) return fail(TSQR_ERR_ARG, "m=%lld < n=%d", (long long)m, n);
   if (lda < m) return fail(TSQR_ERR_ARG, "lda=%lld < m=%lld", (long long)lda, (long long)m);
   if (leaf_h < n) return fail(TSQR_ERR_ARG, "leaf_h=%d < n=%d", leaf_h, n);
@@ -1235,6 +1247,206 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
   return TSQR_OK;
 }
 
+// B <- Q^T B (trans) or B <- Q B of F: the TSQR launches with the sign fix D, or, for a
+// CAQR factor set, its panels in order (Q^T: panel 0 first; each panel acts on rows
+// p*panel..m-1 of B).
+static tsqr_status apply_impl(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, int trans,
+                              cudaStream_t s) {
+  if (F->caqr()) {
+    const int np = (int)F->panels.size();
+    for (int i = 0; i < np; ++i) {
+      const int p = trans ? i : np - 1 - i;
+      tsqr_status st = apply_impl(F->panels[p], B + (int64_t)p * F->panel, ldb, k, trans, s);
+      if (st != TSQR_OK) return st;
+    }
+    return TSQR_OK;
+  }
+  if (trans) {
+    tsqr_status st = run_apply(F, B, ldb, k, 1, 0, s);
+    if (st != TSQR_OK) return st;
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
+    return TSQR_OK;
+  }
+  {
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
+  }
+  return run_apply(F, B, ldb, k, 0, 0, s);
+}
+
+// The thin Q of F. For CAQR, Q [I_n; 0] = Q_0 Q_1 ... Q_{P-1} [I_n; 0] is built from the
+// last panel back: panel p forms its own thin Q in its columns (rows p*panel..m-1; later
+// panels never touch these columns) and applies Q_p to the later panels' columns, whose
+// rows p*panel..(p+1)*panel-1 are still zero. Rows above each panel's block are zero.
+static tsqr_status form_q_impl(const tsqr_factors *F, double *Q, int64_t ldq, cudaStream_t s) {
+  if (F->caqr()) {
+    const int np = (int)F->panels.size();
+    const int64_t b = F->panel;
+    for (int p = 1; p < np; ++p) {
+      const int64_t c0 = p * b;
+      CUDA_TRY(cudaMemset2DAsync(Q + c0 * ldq, sizeof(double) * ldq, 0, sizeof(double) * c0,
+                                 (size_t)F->panels[p]->plan().n, s));
+    }
+    for (int p = np - 1; p >= 0; --p) {
+      const int64_t c0 = p * b;
+      const int32_t bp = F->panels[p]->plan().n;
+      const int32_t kt = F->ncols - (int32_t)c0 - bp;
+      double *Qp = Q + c0 + c0 * ldq;
+      if (kt > 0) {
+        tsqr_status st = apply_impl(F->panels[p], Qp + (int64_t)bp * ldq, ldq, kt, 0, s);
+        if (st != TSQR_OK) return st;
+      }
+      tsqr_status st = form_q_impl(F->panels[p], Qp, ldq, s);
+      if (st != TSQR_OK) return st;
+    }
+    return TSQR_OK;
+  }
+  {
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    CUDA_TRY(launch_formq_init(Q, ldq, F->plan().n, F->d, s));
+  }
+  return run_apply(F, Q, ldq, F->plan().n, 0, 1, s);
+}
+
+// ------------------------------------------------------------------------ CAQR
+// Communication-avoiding QR of a wider matrix (paper §2.4; the switch from TSQR to CAQR
+// for large n of §6 and Property 5 of §4): the columns are split into panels, each panel
+// is factored by TSQR and its Q^T is applied to the trailing columns, whose top rows are
+// rows of R; the next panel is the updated trailing block below them.
+constexpr int32_t kCaqrMaxCols = 4096;  // the back substitution keeps a column of X in shared memory
+constexpr int32_t kCaqrPanel = 64;      // default panel width: the TSQR kernels' widest efficient tile
+
+static tsqr_status check_caqr_args(const double *A, int64_t m, int32_t n, int64_t lda, int32_t panel,
+                                   int32_t leaf_h, int32_t arity) {
+  if (!A) return fail(TSQR_ERR_ARG, "A is NULL");
+  if (n < 1 || n > kCaqrMaxCols) return fail(TSQR_ERR_ARG, "n=%d outside [1, %d]", n, kCaqrMaxCols);
+  if (m < n) return fail(TSQR_ERR_ARG, "m=%lld < n=%d", (long long)m, n);
+  if (lda < m) return fail(TSQR_ERR_ARG, "lda=%lld < m=%lld", (long long)lda, (long long)m);
+  if (panel < 0 || panel > 128) return fail(TSQR_ERR_ARG, "panel=%d outside [0, 128]", panel);
+  const int32_t b = std::min(n, panel > 0 ? panel : kCaqrPanel);
+  if (leaf_h < b) return fail(TSQR_ERR_ARG, "leaf_h=%d < panel width %d", leaf_h, b);
+  if (!(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "arity=%d not in {0, 2..16}", arity);
+  return TSQR_OK;
+}
+
+static tsqr_status caqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t panel, int32_t leaf_h,
+                               int32_t arity, int32_t flags, cudaStream_t s, tsqr_factors **F, double *R,
+                               int64_t ldr) {
+  tsqr_status st = check_caqr_args(A, m, n, lda, panel, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if (!F) return fail(TSQR_ERR_ARG, "F is NULL");
+  if (R && ldr < n) return fail(TSQR_ERR_ARG, "ldr=%lld < n=%d", (long long)ldr, n);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  *F = nullptr;
+  const int32_t b = panel > 0 ? panel : kCaqrPanel;
+  tsqr_factors *f = new (std::nothrow) tsqr_factors();
+  if (!f) return fail(TSQR_ERR_OOM, "host allocation failed");
+  f->stream = s;
+  cudaGetDevice(&f->device);
+  f->panel = b;
+  f->ncols = n;
+  f->mrows = m;
+  try {
+    f->panels.reserve((size_t)((n + b - 1) / b));
+  } catch (const std::bad_alloc &) {
+    delete f;
+    return fail(TSQR_ERR_OOM, "host allocation failed");
+  }
+  // the working copy holds every panel's reflectors and the trailing updates
+  cudaError_t e = cudaSuccess;
+  if (flags & TSQR_INPLACE) {
+    f->V = const_cast<double *>(A);
+    f->ldv = lda;
+  } else {
+    e = pool_alloc((void **)&f->V, sizeof(double) * (size_t)m * n, s);
+    if (e == cudaSuccess) {
+      f->owns_V = true;
+      f->ldv = m;
+      e = cudaMemcpy2DAsync(f->V, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                            cudaMemcpyDeviceToDevice, s);
+    }
+  }
+  if (e == cudaSuccess) e = pool_alloc((void **)&f->Rfull, sizeof(double) * (size_t)n * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->Rfull, 0, sizeof(double) * (size_t)n * n, s);
+  if (e != cudaSuccess) st = fail(TSQR_ERR_OOM, "CAQR workspace: %s", cudaGetErrorString(e));
+  for (int32_t c0 = 0; c0 < n && st == TSQR_OK; c0 += b) {
+    const int32_t bp = std::min(b, n - c0);
+    const int32_t kt = n - c0 - bp;  // trailing columns
+    double *Wp = f->V + c0 + (int64_t)c0 * f->ldv;
+    double *Tp = kt > 0 ? Wp + (int64_t)bp * f->ldv : nullptr;
+    tsqr_factors *fp = nullptr;
+    // the panel in place in the working copy; Q_p^T of the trailing columns overlaps the
+    // panel's reduction tree (tsqr_factor_qt's launch pairing)
+    st = factor_common(Wp, m - c0, bp, f->ldv, leaf_h, arity, TSQR_FP64, (flags & TSQR_TWO_LEVEL) | TSQR_INPLACE, s,
+                       &fp, f->Rfull + c0 + (int64_t)c0 * n, n, Tp, f->ldv, kt);
+    if (st != TSQR_OK) break;
+    f->panels.push_back(fp);
+    if (kt > 0) {  // rows c0..c0+bp-1 of the updated trailing columns are rows of R (diag(R) >= 0 signs)
+      e = cudaMemcpy2DAsync(f->Rfull + c0 + (int64_t)(c0 + bp) * n, sizeof(double) * n, Tp,
+                            sizeof(double) * f->ldv, sizeof(double) * bp, kt, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "R row copy: %s", cudaGetErrorString(e));
+    }
+  }
+  if (st == TSQR_OK && R) {
+    e = cudaMemcpy2DAsync(R, sizeof(double) * ldr, f->Rfull, sizeof(double) * n, sizeof(double) * n, n,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "R copy: %s", cudaGetErrorString(e));
+  }
+  if (st != TSQR_OK) {
+    factors_release(f);
+    return st;
+  }
+  *F = f;
+  return TSQR_OK;
+}
+
+// Least squares through CAQR (n > 128): X = R^{-1} (Q^T B)[0:n], FP64 only.
+static tsqr_status caqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const double *B, int64_t ldb,
+                              int32_t k, double *X, int64_t ldx, int32_t leaf_h, int32_t arity, int32_t prec,
+                              int32_t flags, cudaStream_t s, double *info) {
+  tsqr_status st = check_caqr_args(A, m, n, lda, 0, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if (!B || !X) return fail(TSQR_ERR_ARG, "B or X is NULL");
+  if (k < 1 || k > 64) return fail(TSQR_ERR_ARG, "k=%d outside [1, 64]", k);
+  if (ldb < m || ldx < n) return fail(TSQR_ERR_ARG, "bad ldb/ldx");
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_MIXED least squares takes n <= 128");
+  if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
+  tsqr_factors *F = nullptr;
+  st = caqr_factor(A, m, n, lda, 0, leaf_h, arity, flags & TSQR_TWO_LEVEL, s, &F, nullptr, 0);
+  if (st != TSQR_OK) return st;
+  double *W = nullptr;  // Q^T B workspace (m-by-k)
+  int32_t *status = nullptr;
+  cudaError_t e = pool_alloc((void **)&W, sizeof(double) * (size_t)m * k, s);
+  if (e == cudaSuccess) e = pool_alloc((void **)&status, sizeof(int32_t), s);
+  if (e != cudaSuccess) st = fail(TSQR_ERR_OOM, "workspace allocation failed");
+  if (st == TSQR_OK) {
+    e = cudaMemcpy2DAsync(W, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, k,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "workspace init: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK) st = apply_impl(F, W, m, k, 1, s);
+  if (st == TSQR_OK) {
+    ProfScope ps(TSQR_PROF_SMALL, s);
+    e = launch_trsv(F->Rfull, n, n, W, m, k, X, ldx, nullptr, status, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "trsv: %s", cudaGetErrorString(e));
+  }
+  int32_t hstatus = 0;
+  if (st == TSQR_OK) {
+    e = cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "status readback: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK && info) info[0] = 0.0;
+  if (W) cudaFreeAsync(W, s);
+  if (status) cudaFreeAsync(status, s);
+  factors_release(F);
+  if (st == TSQR_OK && hstatus == 4) return fail(TSQR_ERR_SINGULAR, "R has a zero diagonal entry");
+  return st;
+}
+
 extern "C" {
 
 tsqr_status tsqr_factor(const double *A, int64_t m, int32_t n, int64_t lda, int32_t leaf_h, int32_t arity,
@@ -1255,37 +1467,28 @@ tsqr_status tsqr_factor_qt(const double *A, int64_t m, int32_t n, int64_t lda, d
 tsqr_status tsqr_apply_qt(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
   g_last_error.clear();
   if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
-  if (k < 1 || ldb < F->plan().m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
-  cudaStream_t s = (cudaStream_t)stream;
-  tsqr_status st = run_apply(F, B, ldb, k, 1, 0, s);
-  if (st != TSQR_OK) return st;
-  ProfScope ps(TSQR_PROF_SMALL, s);
-  CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
-  return TSQR_OK;
+  if (k < 1 || ldb < F->rows()) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  return apply_impl(F, B, ldb, k, 1, (cudaStream_t)stream);
 }
 
 tsqr_status tsqr_apply_q(const tsqr_factors *F, double *B, int64_t ldb, int32_t k, void *stream) {
   g_last_error.clear();
   if (!F || !B) return fail(TSQR_ERR_ARG, "NULL factor set or B");
-  if (k < 1 || ldb < F->plan().m) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
-  cudaStream_t s = (cudaStream_t)stream;
-  {
-    ProfScope ps(TSQR_PROF_SMALL, s);
-    CUDA_TRY(launch_scale_rows(B, ldb, F->plan().n, k, F->d, s));
-  }
-  return run_apply(F, B, ldb, k, 0, 0, s);
+  if (k < 1 || ldb < F->rows()) return fail(TSQR_ERR_ARG, "bad k=%d or ldb=%lld", k, (long long)ldb);
+  return apply_impl(F, B, ldb, k, 0, (cudaStream_t)stream);
 }
 
 tsqr_status tsqr_form_q(const tsqr_factors *F, double *Q, int64_t ldq, void *stream) {
   g_last_error.clear();
   if (!F || !Q) return fail(TSQR_ERR_ARG, "NULL factor set or Q");
-  if (ldq < F->plan().m) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
-  cudaStream_t s = (cudaStream_t)stream;
-  {
-    ProfScope ps(TSQR_PROF_SMALL, s);
-    CUDA_TRY(launch_formq_init(Q, ldq, F->plan().n, F->d, s));
-  }
-  return run_apply(F, Q, ldq, F->plan().n, 0, 1, s);
+  if (ldq < F->rows()) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
+  return form_q_impl(F, Q, ldq, (cudaStream_t)stream);
+}
+
+tsqr_status tsqr_caqr(const double *A, int64_t m, int32_t n, int64_t lda, int32_t panel, int32_t leaf_h,
+                      int32_t arity, int32_t flags, void *stream, tsqr_factors **F, double *R, int64_t ldr) {
+  g_last_error.clear();
+  return caqr_factor(A, m, n, lda, panel, leaf_h, arity, flags, (cudaStream_t)stream, F, R, ldr);
 }
 
 tsqr_status tsqr_orthonormalize(const double *A, int64_t m, int32_t n, int64_t lda, double *Q, int64_t ldq,
@@ -1296,11 +1499,17 @@ tsqr_status tsqr_orthonormalize(const double *A, int64_t m, int32_t n, int64_t l
   if (flags & TSQR_INPLACE) return fail(TSQR_ERR_ARG, "tsqr_orthonormalize: TSQR_INPLACE is not supported");
   cudaStream_t s = (cudaStream_t)stream;
   tsqr_factors *F = nullptr;
-  tsqr_status st = factor_common(A, m, n, lda, leaf_h, arity, prec, flags, s, &F, R, ldr, nullptr, 0, 0);
+  tsqr_status st;
+  if (n > 128) {  // CAQR with the default panel width
+    if (prec != TSQR_FP64) return fail(prec == TSQR_MIXED ? TSQR_ERR_UNSUPPORTED : TSQR_ERR_ARG, "prec %d", prec);
+    st = caqr_factor(A, m, n, lda, 0, leaf_h, arity, flags, s, &F, R, ldr);
+  } else {
+    st = factor_common(A, m, n, lda, leaf_h, arity, prec, flags, s, &F, R, ldr, nullptr, 0, 0);
+  }
   if (st != TSQR_OK) return st;
   // the factorization has read all of A before the first write to Q (stream order), and
   // V is the factor set's own copy, so Q may alias A
-  st = tsqr_form_q(F, Q, ldq, stream);
+  st = form_q_impl(F, Q, ldq, s);
   factors_release(F);
   return st;
 }
@@ -1309,11 +1518,14 @@ tsqr_status tsqr_solve_r(const tsqr_factors *F, const double *C, int64_t ldc, in
                          int32_t *status, void *stream) {
   g_last_error.clear();
   if (!F || !C || !X) return fail(TSQR_ERR_ARG, "NULL factor set, C or X");
-  const int n = F->plan().n;
+  const int n = F->cols();
   if (k < 1 || ldc < n || ldx < n) return fail(TSQR_ERR_ARG, "bad k=%d, ldc or ldx", k);
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope ps(TSQR_PROF_SMALL, s);
-  CUDA_TRY(launch_trsv(F->V, F->ldv, n, C, ldc, k, X, ldx, F->d, status, s));
+  if (F->caqr())
+    CUDA_TRY(launch_trsv(F->Rfull, n, n, C, ldc, k, X, ldx, nullptr, status, s));
+  else
+    CUDA_TRY(launch_trsv(F->V, F->ldv, n, C, ldc, k, X, ldx, F->d, status, s));
   return TSQR_OK;
 }
 
@@ -1321,6 +1533,8 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
                        int32_t k, double *X, int64_t ldx, int32_t leaf_h, int32_t arity, int32_t prec,
                        int32_t flags, int32_t max_refine, void *stream, double *info) {
   g_last_error.clear();
+  if (n > 128)
+    return caqr_lstsq(A, m, n, lda, B, ldb, k, X, ldx, leaf_h, arity, prec, flags, (cudaStream_t)stream, info);
   tsqr_status st = check_factor_args(A, m, n, lda, leaf_h, arity);
   if (st != TSQR_OK) return st;
   if (!B || !X) return fail(TSQR_ERR_ARG, "B or X is NULL");
@@ -1670,7 +1884,26 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
 
 tsqr_status tsqr_factors_info(const tsqr_factors *F, int64_t *out) {
   if (!F || !out) return fail(TSQR_ERR_ARG, "NULL argument");
-  plan_info(F->plan(), out);
+  if (!F->caqr()) {
+    plan_info(F->plan(), out);
+    return TSQR_OK;
+  }
+  // CAQR: totals over the panels (rows and columns of the whole matrix; the first
+  // panel's tile rows and CTAs per SM)
+  int64_t sum[8] = {0}, one[8];
+  for (const tsqr_factors *P : F->panels) {
+    plan_info(P->plan(), one);
+    for (int i : {2, 4, 5, 6}) sum[i] += one[i];
+  }
+  plan_info(F->panels[0]->plan(), one);
+  out[0] = F->mrows;
+  out[1] = F->ncols;
+  out[2] = sum[2];
+  out[3] = one[3];
+  out[4] = sum[4];
+  out[5] = sum[5];
+  out[6] = sum[6];
+  out[7] = one[7];
   return TSQR_OK;
 }
 

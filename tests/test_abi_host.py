@@ -61,6 +61,39 @@ def test_factor_argument_errors(lib, kw, why):
     assert not h.value
 
 
+@pytest.mark.parametrize("kw,why", [
+    (dict(A=0), "A is NULL"),
+    (dict(n=4097, m=5000, lda=5000), "n=4097"),
+    (dict(m=100, n=101, lda=101), "m=100 < n"),
+    (dict(lda=99), "lda=99"),
+    (dict(panel=129), "panel=129"),
+    (dict(panel=-1), "panel=-1"),
+    (dict(leaf_h=63), "leaf_h=63 < panel"),
+    (dict(arity=17), "arity=17"),
+    (dict(F=False), "F is NULL"),
+    (dict(ldr=199), "ldr=199"),
+    (dict(flags=8), "unknown flags"),
+])
+def test_caqr_argument_errors(lib, kw, why):
+    """tsqr_caqr (CAQR for wide matrices, paper §2.4) rejects bad arguments on the host."""
+    a = dict(A=FAKE, m=1000, n=200, lda=1000, panel=0, leaf_h=64, arity=2, flags=0, F=True, ldr=200)
+    a.update(kw)
+    h = ctypes.c_void_p()
+    st = lib.tsqr_caqr(a["A"], a["m"], a["n"], a["lda"], a["panel"], a["leaf_h"], a["arity"], a["flags"], None,
+                       ctypes.byref(h) if a["F"] else None, FAKE, a["ldr"])
+    assert st == 1
+    assert why.split()[0] in lib.tsqr_last_error().decode()
+    assert not h.value
+
+
+def test_wide_least_squares_arguments(lib):
+    """tsqr_lstsq with n > 128 goes through CAQR: FP64 only, same argument checks."""
+    assert lib.tsqr_lstsq(FAKE, 1000, 200, 1000, FAKE, 1000, 1, FAKE, 200, 256, 2, 1, 0, 0, None, None) == 6
+    assert lib.tsqr_lstsq(FAKE, 1000, 200, 1000, FAKE, 1000, 0, FAKE, 200, 256, 2, 0, 0, 0, None, None) == 1
+    assert lib.tsqr_lstsq(FAKE, 1000, 200, 1000, FAKE, 1000, 1, FAKE, 199, 256, 2, 0, 0, 0, None, None) == 1
+    assert lib.tsqr_lstsq(FAKE, 1000, 200, 1000, FAKE, 1000, 1, FAKE, 200, 32, 2, 0, 0, 0, None, None) == 1
+
+
 def test_factor_mixed_is_unsupported(lib):
     h = ctypes.c_void_p()
     st = lib.tsqr_factor(FAKE, 100, 16, 100, 32, 2, 1, 0, None, ctypes.byref(h), FAKE, 16)
