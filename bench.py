@@ -97,6 +97,9 @@ def parse(argv=None):
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision least-squares workload")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
     p.add_argument("--no-orth", action="store_true", help="skip the block-orthogonalization (Q-only TSQR) workload")
+    p.add_argument("--no-caqr", action="store_true", help="skip the CAQR (wide matrix) workload")
+    p.add_argument("--no-config2", action="store_true", help="skip the leaf-height x tree sweep and apply timings")
+    p.add_argument("--caqr-only", action="store_true", help="run only the CAQR workload")
     p.add_argument("--orth-only", action="store_true", help="run only the block-orthogonalization workload")
     p.add_argument("--orth-elems", type=int, default=1 << 28, help="FP64 entries per block (m = elems / n)")
     p.add_argument("--orth-widths", default="8,16,32,64", help="block widths n, comma-separated")
@@ -356,6 +359,116 @@ def bench_block_orth(ts, peak_tflops, elems=1 << 28, widths=(8, 16, 32, 64), rep
     out["workload"] = ("Q-only TSQR of 2^28-entry FP64 blocks (m = 2^28 / n), iid N(0,1) from a seeded device "
                        "generator, out of place, binary two-level tree on the on-chip tile; flops 2(2mn^2 - 2n^3/3)")
     return out
+
+
+def bench_caqr(ts, peak_tflops, shapes=((1 << 19, 256), (1 << 19, 512)), panels=(32, 64, 128), reps=3):
+    """CAQR (tsqr_caqr, paper §2.4) of wide blocks: m = 524,288 rows, n = 256 and 512, iid
+    N(0,1) from a seeded device generator; panels of 64 columns (32 and 128 timed beside
+    it). Flops 2mn^2 - 2n^3/3 for the factorization and the same for the thin Q. The
+    backward and orthogonality errors are checked on the device after the timed runs
+    (a cuBLAS product, check only)."""
+    import torch
+    out = {}
+    for m, n in shapes:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9100 + n)
+        A = torch.randn((n, m), generator=g, dtype=torch.float64, device="cuda").t()
+        leaf_h = ts.plan_describe(m, 64, 4096, 2, True)["tile_rows"]
+        fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+        row = {"m": m, "n": n, "leaf_h": leaf_h}
+        for panel in panels:
+            ts.caqr(A, panel=panel, leaf_h=leaf_h).free()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ts.caqr(A, panel=panel, leaf_h=leaf_h).free()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[f"panel{panel}"] = {"factor_ms": ms, "gflops": fl / (ms * 1e-3) / 1e9,
+                                    "frac_of_fp64_peak": fl / (ms * 1e-3) / 1e12 / peak_tflops}
+        F = ts.caqr(A, panel=64, leaf_h=leaf_h)
+        Q = F.form_q()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            F.form_q(Q)
+        e1.record()
+        torch.cuda.synchronize()
+        qms = e0.elapsed_time(e1) / reps
+        row["form_q_ms"] = qms
+        row["form_q_gflops"] = fl / (qms * 1e-3) / 1e9
+        _, prof = ts.profile_collect(lambda: ts.caqr(A, panel=64, leaf_h=leaf_h).free())
+        torch.cuda.synchronize()
+        phases = {}
+        for kind, t in prof:
+            phases[kind] = phases.get(kind, 0.0) + t
+        row["factor_phases_ms"] = phases
+        eye = torch.eye(n, dtype=torch.float64, device="cuda")
+        row["orth_err"] = float(torch.linalg.norm(Q.t() @ Q - eye))
+        row["backward_err"] = float(torch.linalg.norm(A - Q @ F.R) / torch.linalg.norm(A))
+        F.free()
+        out[f"{m}x{n}"] = row
+        del A, Q
+        torch.cuda.empty_cache()
+    out["workload"] = ("CAQR of iid N(0,1) FP64 blocks from a seeded device generator: TSQR panels (binary "
+                       "two-level tree on the on-chip tile), each panel's Q^T applied to the trailing columns; "
+                       "flops 2mn^2 - 2n^3/3 (factor), the same for the thin Q")
+    return out
+
+
+def bench_config2(ts, Ad, m, n, leaf_h, arity, two, reps=2):
+    """The leaf-height x tree sweep of the 4,194,304 x 64 matrix (factor only; the pure
+    k-ary trees over leaves of h rows and the GPU two-level form, binary, 4-ary and flat),
+    Q^T B at k = 1 and 4 and the thin Q for the headline configuration, and the ratio
+    time(Q and R) / time(R) (paper §4, Property 1: about 2). A pure flat tree over 4M rows
+    is one sequential chain on one CTA (about 17 s), so the flat tree is timed in its
+    two-level form only (flat chains inside each CTA, then one flat chain over them)."""
+    import torch
+
+    def timed(fn, r=reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(r):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / r
+
+    f_fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+    rows = []
+    for tree in ("pure", "two-level"):
+        for ar in (2, 4, 0):
+            if tree == "pure" and ar == 0:
+                continue
+            for h in (64, 128, 256, 512, 1024):
+                t = timed(lambda: ts.factor(Ad, leaf_h=h, arity=ar, two_level=tree == "two-level").free(),
+                          1 if ar == 0 else reps)
+                rows.append({"tree": tree, "arity": ar, "leaf_h": h, "factor_ms": t,
+                             "gflops": f_fl / (t * 1e-3) / 1e9})
+    F = ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two)
+    Q = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+    res = {}
+    for k in (1, 4):
+        B0 = torch.randn((k, m), dtype=torch.float64, device="cuda").t()
+        B = B0.clone()
+        t = timed(lambda: F.apply_qt(B))
+        res[f"apply_qt_k{k}_ms"] = t
+        res[f"apply_qt_k{k}_gflops"] = (4.0 * m * n * k - 2.0 * n * n * k) / (t * 1e-3) / 1e9
+    t_q = timed(lambda: F.form_q(Q))
+    t_r = timed(lambda: ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two).free())
+    t_qr = timed(lambda: ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two).form_q(Q))
+    F.free()
+    del Q
+    torch.cuda.empty_cache()
+    res.update({"form_q_ms": t_q, "factor_ms": t_r, "factor_and_form_q_ms": t_qr,
+                "property1_ratio_q_and_r_over_r": t_qr / t_r, "sweep": rows,
+                "best": min(rows, key=lambda r: r["factor_ms"])})
+    return res
 
 
 def bench_batched(ts, count):
@@ -725,6 +838,10 @@ def bench_ours(args):
             print(json.dumps({"block_orth": bench_block_orth(ts, ts.probe_fp64_peak(), args.orth_elems, widths)}),
                   flush=True)
         return 0
+    if args.caqr_only:
+        if rank == 0:
+            print(json.dumps({"caqr": bench_caqr(ts, ts.probe_fp64_peak())}), flush=True)
+        return 0
     if args.profile_batch:
         pool = make_served_pool(32, 11)
         items = [{"A": r["A"], "B": r["B"], "want_r": False, "prec": ts.MIXED} for r in pool]
@@ -889,6 +1006,10 @@ def bench_ours(args):
             os.sched_setaffinity(0, all_cpus)  # the oracle baseline uses every host core
         cpu = cpu_baseline(m, n, args.decades)
     del Q
+    config2 = None if args.no_config2 or rank != 0 else bench_config2(ts, Ad, m, n, leaf_h, args.arity, two)
+    torch.cuda.empty_cache()
+    caqr = None if args.no_caqr or rank != 0 else bench_caqr(ts, peak)
+    torch.cuda.empty_cache()
     mixed = None if args.no_mixed or rank != 0 else bench_mixed_lsq(ts)
     torch.cuda.empty_cache()
     block_orth = None if args.no_orth or rank != 0 else bench_block_orth(
@@ -926,7 +1047,8 @@ def bench_ours(args):
                                       "measured-peaks file has no FP64 entry",
                          "frac_of_derived": achieved / peak_derived},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
-            "factor_autotune": tuned, "mixed_lsq": mixed, "block_orth": block_orth, "batched": batched,
+            "factor_autotune": tuned, "config2": config2, "caqr": caqr, "mixed_lsq": mixed,
+            "block_orth": block_orth, "batched": batched,
             "served": served,
         }
         print(json.dumps(line), flush=True)

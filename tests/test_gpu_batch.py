@@ -238,3 +238,33 @@ def test_batch_degenerate_shapes(cuda_lib, m, n, k, prec):
     assert rel(R, oracle.r_factor(A)) <= tolr
     if k:
         assert rel(X, oracle.lstsq(A, B)) <= 1e-10
+
+
+def test_batch_of_ten_thousand_sampled_against_oracle(cuda_lib):
+    """The batched workload at full size: 10,000 instances, m log-uniform in [256, 65,536],
+    n from {8, 16, 32, 64}, iid N(0,1) from a seeded device generator, alternately FP64 and
+    FP32-mixed, in one launch (chain length 16, binary tree). A seeded sample of 100 items
+    is checked against the oracle (FP64 items to 1e-12, mixed R-only items to FP32 leaf
+    accuracy, 1e-5), and every item's status is 0."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    count = 10_000
+    g = inputs.rng(17)
+    ms = np.exp(g.uniform(np.log(256), np.log(65536), size=count)).astype(np.int64)
+    ns = g.choice([8, 16, 32, 64], size=count)
+    ms = np.maximum(ms, ns)
+    offs = np.concatenate([[0], np.cumsum(ms * ns)])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    buf = torch.randn(int(offs[-1]), dtype=torch.float64, device="cuda", generator=gen)
+    items = [{"A": buf[offs[q]:offs[q + 1]].view(int(ns[q]), int(ms[q])).t(), "prec": q & 1} for q in range(count)]
+    outs, st = ts.batch_solve(items, chain_tiles=16, arity=2, status=True)
+    assert st == [0] * count
+    sample = inputs.rng(18).choice(count, size=100, replace=False)
+    for q in sample:
+        A = to_host(items[q]["A"])
+        R = to_host(outs[q][0])
+        assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+        assert rel(R, oracle.r_factor(A)) <= (1e-12 if q % 2 == 0 else 1e-5), f"item {q}"
+    del buf, items, outs
+    torch.cuda.empty_cache()

@@ -150,3 +150,54 @@ def test_concurrent_submitters(cuda_lib):
         assert np.array_equal(to_host(R), R1)
         if B is not None:
             assert np.array_equal(to_host(X), X1)
+
+
+def mixed_requests(count, seed, mlo=1000, mhi=200_000, ns=(16, 32, 64, 128)):
+    """Served least-squares requests shaped like the served workload: m log-uniform, n from
+    {16, 32, 64, 128}, k from 1..8 (n = 128 included), kappa log-uniform in [1, 1e4],
+    b = A x_true + 1e-6 N(0, 1)."""
+    g = inputs.rng(seed)
+    out = []
+    for q in range(count):
+        n = int(ns[q % len(ns)])
+        m = max(int(np.exp(g.uniform(np.log(mlo), np.log(mhi)))), n)
+        k = int(g.integers(1, 9))
+        dec = float(g.uniform(0.0, 4.0))
+        A = inputs.graded(m, n, dec, seed_g=seed * 1000 + q, seed_v=seed * 1000 + q + 1)
+        B, _ = inputs.lstsq_rhs(A, k, 1e-6, seed * 1000 + q + 500)
+        out.append((A, B))
+    return out
+
+
+@pytest.mark.parametrize("prec_name", ["MIXED", "AUTO"])
+def test_served_mixed_and_auto_match_oracle(cuda_lib, prec_name):
+    """The served mixed-precision path (FP32 leaves, FP64 tree, FP64 refinement) and the
+    AUTO policy, through the server's multi-stream batches and refinement launches: every
+    X is bitwise the request solved alone with the same precision, and within 1e-10 of the
+    FP64 oracle, for kappa up to 1e4, n up to 128 with right-hand sides, and one request of
+    a million rows."""
+    import paper_0912_2572_gb300 as ts
+    prec = getattr(ts, prec_name)
+    reqs = mixed_requests(48, 7 if prec_name == "MIXED" else 8)
+    A1 = inputs.graded(1_000_000, 32, 4.0, seed_g=70, seed_v=71)
+    B1, _ = inputs.lstsq_rhs(A1, 2, 1e-6, 72)
+    reqs.append((A1, B1))
+    dev = [({"A": to_dev(A), "B": to_dev(B), "prec": prec, "want_r": False}) for A, B in reqs]
+    outs = {}
+    with ts.Server(max_batch=16, streams=2, chain_tiles=8) as srv:
+        for i, it in enumerate(dev):
+            t, out = srv.submit(it)
+            outs[t] = (i, out)
+        srv.drain()
+        done = srv.poll()
+        stats = srv.stats()
+    assert len(done) == len(reqs) and all(st == 0 for _, _, st in done)
+    assert stats["batches"] >= 3
+    for t, (i, (_, X)) in outs.items():
+        A, B = reqs[i]
+        Xs = to_host(X)
+        (_, Xa), = ts.batch_solve([{"A": dev[i]["A"], "B": dev[i]["B"], "prec": prec, "want_r": False}],
+                                  chain_tiles=8)
+        assert np.array_equal(Xs, to_host(Xa)), f"request {i}: served != alone"
+        err = rel(Xs, oracle.lstsq(A, B))
+        assert err <= 1e-10, f"request {i} (m={A.shape[0]}, n={A.shape[1]}, k={B.shape[1]}): {err:.2e}"
