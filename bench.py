@@ -88,6 +88,8 @@ def parse(argv=None):
     p.add_argument("--leaf-h", type=int, default=0, help="rows per leaf; 0 = the on-chip tile height")
     p.add_argument("--arity", type=int, default=2)
     p.add_argument("--tree", default="two-level", choices=["two-level", "pure"])
+    p.add_argument("--cluster", type=int, default=1,
+                   help="1: the binary tree's latency-bound levels in thread-block clusters (TSQR_CLUSTER)")
     p.add_argument("--decades", type=float, default=6.0)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -221,7 +223,7 @@ def host_pinned_colmajor(a):
 _SIDE_STREAMS = {}
 
 
-def run_step(ts, Ad, bd, b0, Q, x, leaf_h, arity, two_level):
+def run_step(ts, Ad, bd, b0, Q, x, leaf_h, arity, two_level, cluster=False):
     """One pass of the FP64 path; returns the factor set (caller frees). The thin Q and
     Q^T b + the solve both need only the factorization, so Q^T b runs on a second stream
     beside the thin Q (its latency-bound tree levels fill SMs the thin Q leaves idle); the
@@ -229,7 +231,7 @@ def run_step(ts, Ad, bd, b0, Q, x, leaf_h, arity, two_level):
     import torch
     cur = torch.cuda.current_stream()
     side = _SIDE_STREAMS.setdefault(cur.cuda_stream, torch.cuda.Stream())
-    F = ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two_level)
+    F = ts.factor(Ad, leaf_h=leaf_h, arity=arity, two_level=two_level, cluster=cluster)
     side.wait_stream(cur)
     with torch.cuda.stream(side):
         bd.copy_(b0)
@@ -856,6 +858,7 @@ def bench_ours(args):
 
     m, n = args.m, args.n
     two = args.tree == "two-level"
+    cl = bool(args.cluster) and args.arity == 2
     leaf_h = args.leaf_h or ts.plan_describe(m, n, 4096, args.arity, two)["tile_rows"]
     A, b = make_workload(m, n, args.decades)
     Ad = dev_colmajor(A)
@@ -870,9 +873,9 @@ def bench_ours(args):
         sweep(args, ts, Ad, args.sweep)
 
     for _ in range(args.warmup):
-        run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two).free()
+        run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
     torch.cuda.synchronize()
-    info = ts.factor(Ad, leaf_h=leaf_h, arity=args.arity, two_level=two)
+    info = ts.factor(Ad, leaf_h=leaf_h, arity=args.arity, two_level=two, cluster=cl)
     plan = info.info()
     info.free()
     torch.cuda.synchronize()
@@ -887,7 +890,7 @@ def bench_ours(args):
         def timed():
             ev0.record(stream)
             for _ in range(args.steps):
-                run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two).free()
+                run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
             ev1.record(stream)
             torch.cuda.synchronize()
         _, prof = ts.profile_collect(timed)
@@ -917,46 +920,33 @@ def bench_ours(args):
     peak = peak_measured if peak_measured > 0 else peak_derived
     factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
 
-    # --- end to end: pinned host buffers, copies inside the timed region. Steps rotate
-    # over E2E_SLOTS streams with their own device buffers, so input and result copies
-    # overlap other steps' kernels (every copy stays in the region).
+    # --- end to end through the library's host-buffer call (tsqr_qr_solve_host): every
+    # step copies A and b from pinned host memory to the device, runs the whole path, and
+    # copies Q, R and x back, all inside the timed region. Steps rotate over E2E_SLOTS
+    # streams; each call's kernels wait (its `after` event) for the previous call's kernels,
+    # so one step's copies overlap the neighbouring steps' kernels.
     e2e = None
     if not args.no_e2e:
         Ah = host_pinned_colmajor(A)
         bh = host_pinned_colmajor(b)
         slots = []
         for q in range(E2E_SLOTS):
-            sl = {"s": torch.cuda.Stream(),
-                  "Qh": torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
-                  "Rh": torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
-                  "xh": torch.empty((1, n), dtype=torch.float64, pin_memory=True).t()}
-            if q == 0:
-                sl.update(Ad=Ad, b0=b0, bd=bd, Q=Q, x=x)
-            else:
-                with torch.cuda.stream(sl["s"]):
-                    sl.update(Ad=torch.empty_like(Ad), b0=torch.empty_like(b0), bd=torch.empty_like(bd),
-                              Q=torch.empty_like(Q), x=torch.empty_like(x))
-            slots.append(sl)
-        # the steps' kernels run one step after another (an event chain across the
-        # streams): kernels of concurrent steps would interleave and finish together, and
-        # their copies would then queue while the GPU idles. Input copies run ahead; a
-        # step's result copies overlap the next step's kernels.
+            ev = torch.cuda.Event()
+            ev.record(stream)  # materialise the event handle
+            slots.append({"s": torch.cuda.Stream(), "ev": ev,
+                          "Qh": torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
+                          "Rh": torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
+                          "xh": torch.empty((1, n), dtype=torch.float64, pin_memory=True).t(),
+                          "st": torch.zeros(1, dtype=torch.int32).pin_memory()})
+        torch.cuda.synchronize()
         done = [None]
 
         def e2e_step(i):
             sl = slots[i % E2E_SLOTS]
-            with torch.cuda.stream(sl["s"]):
-                sl["Ad"].copy_(Ah, non_blocking=True)
-                sl["b0"].copy_(bh, non_blocking=True)
-                if done[0] is not None:
-                    sl["s"].wait_event(done[0])
-                F = run_step(ts, sl["Ad"], sl["bd"], sl["b0"], sl["Q"], sl["x"], leaf_h, args.arity, two)
-                done[0] = torch.cuda.Event()
-                done[0].record(sl["s"])
-                sl["Qh"].copy_(sl["Q"], non_blocking=True)
-                sl["Rh"].copy_(F.R, non_blocking=True)
-                sl["xh"].copy_(sl["x"], non_blocking=True)
-                F.free()
+            ts.qr_solve_host(Ah, bh, Q=sl["Qh"], R=sl["Rh"], X=sl["xh"], status=sl["st"], leaf_h=leaf_h,
+                             arity=args.arity, two_level=two, cluster=cl, stream=sl["s"], after=done[0],
+                             done=sl["ev"])
+            done[0] = sl["ev"]
 
         # one untimed pass per stream (each stream's first allocations grow the pool)
         for i in range(E2E_SLOTS):
@@ -977,21 +967,26 @@ def bench_ours(args):
         e2e = {"value": whole_job_rate(fl_step * args.e2e_steps, world, te) / 1e9, "unit": "Gflop/s",
                "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
                "ms_per_step": te / args.e2e_steps, "pipelined_streams": E2E_SLOTS,
+               "api": "tsqr_qr_solve_host (host buffers, copies inside the call)",
                "clocks": e2e_clk.summary()}
-        xe = slots[(args.e2e_steps - 1) % E2E_SLOTS]["xh"].numpy()[:, 0]
+        last = slots[(args.e2e_steps - 1) % E2E_SLOTS]
+        xe = last["xh"].numpy()[:, 0]
         xd = x.cpu().numpy()[:, 0]
         e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
+        e2e["status"] = int(last["st"][0])
         # this box's pinned-copy bandwidth, after the timed region (the e2e figure depends on it)
+        Qd = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+        Ad2 = torch.empty_like(Ad)
         c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         c0.record(stream)
-        slots[0]["Ad"].copy_(Ah, non_blocking=True)
+        Ad2.copy_(Ah, non_blocking=True)
         c1.record(stream)
-        slots[0]["Qh"].copy_(slots[0]["Q"], non_blocking=True)
+        last["Qh"].copy_(Qd, non_blocking=True)
         c2.record(stream)
         torch.cuda.synchronize()
         e2e["copy_gbs"] = {"h2d": 8.0 * m * n / (c0.elapsed_time(c1) * 1e-3) / 1e9,
                            "d2h": 8.0 * m * n / (c1.elapsed_time(c2) * 1e-3) / 1e9}
-        del Ah, slots
+        del Ah, slots, Qd, Ad2
 
     # the library's factorization autotuner on the same matrix (leaf height x arity x tree
     # form, factor only); reported beside the headline's fixed configuration
@@ -1027,6 +1022,7 @@ def bench_ours(args):
             "config": {"workload": f"tsqr_fp64 {m}x{n} A=G*diag(sigma)*V^T, sigma 1..1e-{args.decades:g}; "
                                    "step = factor + thin Q + Q^T b + solve",
                        "m": m, "n": n, "leaf_h": leaf_h, "arity": args.arity, "tree": args.tree,
+                       "cluster_tier": cl,
                        "tile_rows": plan["tile_rows"], "chains": n_chains, "ctas_per_sm": plan["ctas_per_sm"],
                        "l2": "inputs (2.1 GB) larger than L2, no flush", "parallelism": f"replicas x{world}",
                        "host_numa_node": numa},

@@ -55,9 +55,17 @@ typedef enum {
 /* flags for tsqr_factor */
 enum {
   TSQR_INPLACE = 1,   /* the reflectors overwrite A (A is then not const) */
-  TSQR_TWO_LEVEL = 2  /* two-level tree: a flat chain over the leaves inside each
+  TSQR_TWO_LEVEL = 2, /* two-level tree: a flat chain over the leaves inside each
                          CTA, then the arity-k tree across CTAs (the GPU form of the
                          paper's topology-aware tree, §2.3 and §3) */
+  TSQR_CLUSTER = 4    /* with arity 2: the binary tree's levels run three at a time in
+                         thread-block clusters of 8 CTAs, whose combines exchange their
+                         triangles row by row through distributed shared memory and run
+                         as a pipeline (the cluster tier of a hierarchical tree, §2.3 and
+                         §3: CTA -> cluster -> grid). Ignored for other arities or when a
+                         combine's triangles do not fit one CTA's shared memory
+                         (n + extra columns beyond about 80). Same R and reflectors as
+                         the plain binary tree. */
 };
 
 typedef struct tsqr_factors tsqr_factors; /* opaque factor set */
@@ -76,7 +84,7 @@ typedef struct tsqr_factors tsqr_factors; /* opaque factor set */
  *           0 = flat tree (one left-to-right chain). A trailing group of size one
  *           passes up unchanged.
  *   prec    TSQR_FP64 only (TSQR_MIXED is accepted by tsqr_lstsq).
- *   flags   TSQR_INPLACE | TSQR_TWO_LEVEL.
+ *   flags   TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER.
  *   stream  cudaStream_t.
  *   F       out: the new factor set (host pointer to an opaque handle).
  *   R       device, n-by-n column-major, ldr >= n, out: the R factor with
@@ -244,6 +252,33 @@ tsqr_status tsqr_lstsq_static(const double *A, int64_t m, int32_t n, int64_t lda
                               const double *B, int64_t ldb, int32_t k, double *X,
                               int64_t ldx, void *stream);
 
+/*
+ * tsqr_qr_solve_host — the whole FP64 path on HOST buffers in one stream-ordered call:
+ * A (and B) are copied to the device, A is factored by TSQR (paper §2.3), the thin Q
+ * (§4, Property 1), R (diag >= 0) and X = R^{-1} (Q^T B)[0:n] are computed (Q^T B and the
+ * back substitution on the library's helper stream, beside the thin Q), and Q, R and X are
+ * copied back. Device memory comes from the library's stream-ordered pool and is released
+ * in stream order. With page-locked (pinned) host buffers every copy is asynchronous:
+ * results are valid once `stream` reaches the end of the call; pageable buffers work but
+ * the driver stages their copies.
+ *   A       host m-by-n (lda >= m), 1 <= n <= 128, m >= n.
+ *   B, X    host m-by-k (ldb >= m) and n-by-k (ldx >= n), k >= 1, or both NULL.
+ *   Q       host m-by-n (ldq >= m) or NULL.   R  host n-by-n (ldr >= n) or NULL.
+ *   status  host int32 or NULL: receives TSQR_ERR_SINGULAR (4) or 0 with the outputs
+ *           (valid once the stream reaches the end of the call).
+ *   leaf_h, arity, flags  as tsqr_factor (TSQR_TWO_LEVEL | TSQR_CLUSTER).
+ *   after   cudaEvent_t or NULL: the call's first kernel waits for it (after the input
+ *           copies are enqueued), so consecutive calls on two streams can run their kernels
+ *           one after another while each call's copies overlap the other's kernels.
+ *   done    cudaEvent_t or NULL: recorded after the call's last kernel, before the output
+ *           copies.
+ *   Errors: as tsqr_factor, plus TSQR_ERR_ARG for bad B/X/Q/R arguments.
+ */
+tsqr_status tsqr_qr_solve_host(const double *A, int64_t m, int32_t n, int64_t lda, const double *B, int64_t ldb,
+                               int32_t k, double *Q, int64_t ldq, double *R, int64_t ldr, double *X, int64_t ldx,
+                               int32_t *status, int32_t leaf_h, int32_t arity, int32_t flags, void *stream,
+                               void *after, void *done);
+
 /* tsqr_free — releases F (stream-ordered on the stream F was created on). NULL is
  * accepted. */
 tsqr_status tsqr_free(tsqr_factors *F);
@@ -272,6 +307,22 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
                                int64_t smem_reserved, int64_t smem_optin, int64_t *out,
                                int64_t *tiles, int64_t max_tiles, int64_t *jobs,
                                int64_t max_jobs);
+
+/*
+ * tsqr_plan_clusters — host only, touches no GPU: the cluster schedule tsqr_factor builds
+ * with TSQR_CLUSTER (arity 2) for the same arguments as tsqr_plan_describe.
+ *   out        host int64[2]: {cluster launches, slots}; 0 slots when the combines do not
+ *              fit one CTA's shared memory (the flag is then ignored).
+ *   launches   host int32[4 * max_launches] or NULL: {first slot, clusters, first and last
+ *              binary tree level (launch index of tsqr_plan_describe) of the launch}.
+ *   slots      host int32[3 * max_slots] or NULL, 8 per cluster: {job (index of
+ *              tsqr_plan_describe's jobs) or -1, cluster rank of the pivot child, of the
+ *              tile child} (-1: a triangle complete before the launch).
+ * Errors: as tsqr_plan_describe.
+ */
+tsqr_status tsqr_plan_clusters(int64_t m, int32_t n, int32_t nc, int32_t leaf_h, int32_t flags, int32_t sms,
+                               int64_t smem_per_sm, int64_t smem_reserved, int64_t smem_optin, int64_t *out,
+                               int32_t *launches, int64_t max_launches, int32_t *slots, int64_t max_slots);
 
 /*
  * Batched factorization / least squares: many independent problems in ONE persistent
@@ -319,6 +370,21 @@ typedef struct tsqr_batch_item {
  */
 tsqr_status tsqr_batch_solve(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
                              int32_t arity, void *stream, int32_t *status, double *info);
+
+/*
+ * tsqr_batch_describe — host only, touches no GPU and no item data: the job table the
+ * batched kernel would run for these items on a device with `sms` SMs and the given
+ * shared-memory sizes (as tsqr_plan_describe).
+ *   out   host int64[4]: {chain jobs, jobs, tiles, CTAs of the persistent launch}.
+ *   jobs  host int64[7 * max_jobs] or NULL, chain jobs first (queue order) then tree nodes:
+ *         {item, parent job or -1 at an item's root, children a node waits for, pivot
+ *         row, row of its triangle in the tree storage, first tile, tiles}.
+ * Errors: TSQR_ERR_ARG (as tsqr_batch_solve, a bad device description, or max_jobs too
+ * small while jobs is non-NULL; out is filled first).
+ */
+tsqr_status tsqr_batch_describe(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                                int32_t sms, int64_t smem_per_sm, int64_t smem_reserved, int64_t smem_optin,
+                                int64_t *out, int64_t *jobs, int64_t max_jobs);
 
 /*
  * Autotuners: each times its candidates on the caller's own data with CUDA events on the
@@ -381,9 +447,11 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
  * the same chain_tiles (the batched kernel is deterministic per item).
  *
  * tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctas_per_sm, &srv)
- *   max_bytes    device-memory budget for in-flight requests' workspaces (bytes);
- *                <= 0 = half the device memory free at creation. A request larger than
- *                the whole budget runs alone once nothing else is in flight.
+ *   max_bytes    optional device-memory budget for in-flight requests' workspaces
+ *                (bytes); <= 0 = none. Every admission also requires the batch to fit the
+ *                device memory free at that moment (cudaMemGetInfo plus the unused reserve
+ *                of the library's stream-ordered pool) less 5%. A request larger than
+ *                either runs alone once nothing else is in flight.
  *   max_batch    >= 1, requests per launch.   streams  1..16 batches in flight.
  *   chain_tiles  as for tsqr_batch_solve (0 = automatic).
  *   ctas_per_sm  CTAs per SM of the persistent kernel: 0 = as many as fit (2), 1 = one,
@@ -399,7 +467,8 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
  *   TSQR_ERR_SINGULAR, or the error that made its batch fail). Never blocks.
  * tsqr_server_drain(srv)       blocks until every submitted request has completed.
  * tsqr_server_stats(srv, out)  out[6] (host): submitted, completed, batches launched,
- *                              largest batch, budget bytes, bytes in flight.
+ *                              largest batch, budget bytes (or, without a budget, the free
+ *                              device memory seen at the last admission), bytes in flight.
  * tsqr_server_destroy(srv)     finishes every queued request, then frees the server.
  */
 typedef struct tsqr_server tsqr_server;
@@ -411,6 +480,15 @@ tsqr_status tsqr_server_poll(tsqr_server *srv, int32_t max, int64_t *tickets, do
 tsqr_status tsqr_server_drain(tsqr_server *srv);
 tsqr_status tsqr_server_stats(tsqr_server *srv, int64_t *out);
 tsqr_status tsqr_server_destroy(tsqr_server *srv);
+
+/*
+ * tsqr_debug_fail_allocations — failure injection for tests: the next `count` device
+ * allocations the library makes fail as if the device were out of memory (the calls
+ * return TSQR_ERR_OOM; a server batch whose workspace allocation fails reports
+ * TSQR_ERR_OOM for each of its requests and the server goes on serving). 0 clears it.
+ * Touches no GPU. No paper counterpart.
+ */
+tsqr_status tsqr_debug_fail_allocations(int32_t count);
 
 /* launch classes reported by the profiler */
 enum {
@@ -442,6 +520,16 @@ tsqr_status tsqr_profile_stop(int64_t max_records, int32_t *kind, float *ms, int
  * kernels' roofline denominator; synchronizes the stream. No paper counterpart.
  */
 tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz);
+
+/*
+ * tsqr_error_word — reads and clears the current device's error word after waiting for
+ * `stream`: bit 1 is set when a bounded device-side wait gave up (the TSQR_CLUSTER tree's
+ * waits for a child's progress; the results of that launch are then undefined), bit 2
+ * when an index check of a build compiled with TSQR_CHECK failed. *word (host) receives
+ * the bits. Returns TSQR_ERR_TIMEOUT when bit 1 was set, else TSQR_OK (TSQR_ERR_CUDA on a
+ * failed copy). No paper counterpart.
+ */
+tsqr_status tsqr_error_word(void *stream, int32_t *word);
 
 /* tsqr_strerror — static description of a status code. */
 const char *tsqr_strerror(tsqr_status s);

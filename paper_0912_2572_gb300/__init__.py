@@ -18,13 +18,15 @@ from . import _lib
 
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "caqr", "lstsq", "colmajor",
            "TSQRError", "profile_collect", "plan_describe", "batch_solve", "batch_autotune", "factor_autotune",
-           "AUTO", "BatchPlan", "Server", "probe_fp64_peak", "orthonormalize"]
+           "AUTO", "BatchPlan", "Server", "probe_fp64_peak", "orthonormalize", "CLUSTER", "error_word",
+           "qr_solve_host"]
 
 FP64 = 0
 MIXED = 1
 AUTO = 2
 INPLACE = 1
 TWO_LEVEL = 2
+CLUSTER = 4
 TSQRError = _lib.TSQRError
 
 
@@ -125,14 +127,16 @@ class Factors:
 
 
 def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace: bool = False,
-           R=None, stream=None, qt=None) -> Factors:
+           R=None, stream=None, qt=None, cluster: bool = False) -> Factors:
     """TSQR factorization of a column-major m-by-n float64 CUDA tensor A (paper §2.3).
 
     leaf_h: rows per leaf; arity: 2..16 (k-ary tree) or 0 (flat); two_level: a flat chain
     inside each CTA followed by the arity-k tree across CTAs. Returns a Factors object
     whose ``R`` (n-by-n, diag >= 0) is valid once the stream reaches this point. With
     ``qt`` (an m-by-k column-major tensor), also qt <- Q^T qt, overlapped with the
-    factorization's tree (tsqr_factor_qt; not with ``inplace``).
+    factorization's tree (tsqr_factor_qt; not with ``inplace``). ``cluster`` (binary
+    trees) runs the tree's levels three at a time in thread-block clusters, pipelined
+    through distributed shared memory (TSQR_CLUSTER).
     """
     import torch
     lib = _lib.load()
@@ -141,7 +145,7 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
     if R is None:
         R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
     ldr = _check_mat(R, "R", rows=n, cols=n)
-    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0)
+    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0) | (CLUSTER if cluster else 0)
     h = ctypes.c_void_p()
     if qt is None:
         st = lib.tsqr_factor(A.data_ptr(), m, n, lda, leaf_h, arity, FP64, flags, _stream(stream),
@@ -156,7 +160,7 @@ def factor(A, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace
 
 
 def caqr(A, panel: int = 0, leaf_h: int = 256, arity: int = 2, two_level: bool = True, inplace: bool = False,
-         R=None, stream=None) -> Factors:
+         R=None, stream=None, cluster: bool = False) -> Factors:
     """CAQR factorization (tsqr_caqr, paper §2.4) of a column-major m-by-n float64 CUDA
     tensor A with n up to 4096: TSQR of panels of ``panel`` columns (0 = 64), each panel's
     Q^T applied to the trailing columns. Returns a Factors object (apply_qt, apply_q,
@@ -168,7 +172,7 @@ def caqr(A, panel: int = 0, leaf_h: int = 256, arity: int = 2, two_level: bool =
     if R is None:
         R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
     ldr = _check_mat(R, "R", rows=n, cols=n)
-    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0)
+    flags = (INPLACE if inplace else 0) | (TWO_LEVEL if two_level else 0) | (CLUSTER if cluster else 0)
     h = ctypes.c_void_p()
     _lib.check(lib.tsqr_caqr(A.data_ptr(), m, n, lda, panel, leaf_h, arity, flags, _stream(stream), ctypes.byref(h),
                              R.data_ptr(), ldr), "tsqr_caqr")
@@ -176,7 +180,7 @@ def caqr(A, panel: int = 0, leaf_h: int = 256, arity: int = 2, two_level: bool =
 
 
 def orthonormalize(A, Q=None, R=None, leaf_h: int = 256, arity: int = 2, two_level: bool = True,
-                   stream=None):
+                   stream=None, cluster: bool = False):
     """Q-only TSQR (tsqr_orthonormalize): an orthonormal basis of the columns of the
     column-major m-by-n float64 CUDA tensor A, A = Q R with diag(R) >= 0, the
     orthogonalization step of block iterative methods (paper §2.5, §6). ``Q=A``
@@ -191,7 +195,7 @@ def orthonormalize(A, Q=None, R=None, leaf_h: int = 256, arity: int = 2, two_lev
     if R is None:
         R = torch.empty((n, n), dtype=torch.float64, device=A.device).t()
     ldr = _check_mat(R, "R", rows=n, cols=n)
-    flags = TWO_LEVEL if two_level else 0
+    flags = (TWO_LEVEL if two_level else 0) | (CLUSTER if cluster else 0)
     _lib.check(lib.tsqr_orthonormalize(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(), ldr, leaf_h,
                                        arity, FP64, flags, _stream(stream)), "tsqr_orthonormalize")
     return Q, R
@@ -417,6 +421,54 @@ def probe_fp64_peak(stream=None, clock: bool = False):
     return (out.value, mhz.value) if clock else out.value
 
 
+def _check_host(t, name, rows=None, cols=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 CPU tensor")
+    if t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); use colmajor()")
+    if rows is not None and t.shape[0] != rows:
+        raise ValueError(f"{name} has {t.shape[0]} rows, expected {rows}")
+    if cols is not None and t.shape[1] != cols:
+        raise ValueError(f"{name} has {t.shape[1]} columns, expected {cols}")
+    return max(t.stride(1), max(1, t.shape[0]))
+
+
+def qr_solve_host(A, B=None, Q=None, R=None, X=None, leaf_h: int = 256, arity: int = 2, two_level: bool = True,
+                  cluster: bool = False, stream=None, after=None, done=None, status=None):
+    """The whole FP64 path on host (CPU) tensors through tsqr_qr_solve_host: copies A (and
+    B) in, factors, forms the thin Q, R and X = R^{-1} (Q^T B)[0:n], copies them back into
+    the given column-major float64 CPU tensors (pinned ones make every copy asynchronous;
+    the outputs are valid once the stream reaches the call's end). ``after`` / ``done``:
+    optional torch.cuda.Event the call's kernels wait for / that is recorded after them.
+    ``status``: optional pinned int32 CPU tensor receiving 4 for a singular R."""
+    lib = _lib.load()
+    lda = _check_host(A, "A")
+    m, n = A.shape
+    ldb = _check_host(B, "B", rows=m) if B is not None else m
+    k = B.shape[1] if B is not None else 0
+    ldx = _check_host(X, "X", rows=n, cols=k) if X is not None else n
+    ldq = _check_host(Q, "Q", rows=m, cols=n) if Q is not None else m
+    ldr = _check_host(R, "R", rows=n, cols=n) if R is not None else n
+    flags = (TWO_LEVEL if two_level else 0) | (CLUSTER if cluster else 0)
+    ptr = (lambda t: t.data_ptr() if t is not None else None)
+    ev = (lambda e: ctypes.c_void_p(e.cuda_event) if e is not None else None)
+    _lib.check(lib.tsqr_qr_solve_host(A.data_ptr(), m, n, lda, ptr(B), ldb, k, ptr(Q), ldq, ptr(R), ldr, ptr(X), ldx,
+                                      ptr(status), leaf_h, arity, flags, _stream(stream), ev(after), ev(done)),
+               "tsqr_qr_solve_host")
+    return Q, R, X
+
+
+def error_word(stream=None) -> int:
+    """Reads and clears the device error word (tsqr_error_word; waits for the stream):
+    bit 1 = a bounded device wait gave up, bit 2 = an index check of a TSQR_CHECK build."""
+    w = ctypes.c_int32(0)
+    st = _lib.load().tsqr_error_word(_stream(stream), ctypes.byref(w))
+    if st not in (0, 5):
+        _lib.check(st, "tsqr_error_word")
+    return w.value
+
+
 def profile_collect(fn):
     """Runs fn() with launch profiling on and returns (fn's result, [(class, ms), ...])."""
     lib = _lib.load()
@@ -452,7 +504,7 @@ def plan_describe(m, n, leaf_h, arity=2, two_level=True, nc=None, sms=None):
 
 
 def lstsq(A, B, leaf_h: int = 256, arity: int = 2, two_level: bool = True, prec: int = FP64,
-          max_refine: int = 10, X=None, stream=None, info: bool = False):
+          max_refine: int = 10, X=None, stream=None, info: bool = False, cluster: bool = False):
     """X = argmin ||A X - B|| for column-major float64 CUDA tensors (A m-by-n, B m-by-k).
 
     prec FP64: TSQR of [A | B] with Q^T B fused, then back substitution. MIXED: FP32
@@ -469,7 +521,7 @@ def lstsq(A, B, leaf_h: int = 256, arity: int = 2, two_level: bool = True, prec:
         X = torch.empty((k, n), dtype=torch.float64, device=A.device).t()
     ldx = _check_mat(X, "X", rows=n, cols=k)
     hist = (ctypes.c_double * (max_refine + 1))()
-    flags = TWO_LEVEL if two_level else 0
+    flags = (TWO_LEVEL if two_level else 0) | (CLUSTER if cluster else 0)
     st = lib.tsqr_lstsq(A.data_ptr(), m, n, lda, B.data_ptr(), ldb, k, X.data_ptr(), ldx, leaf_h, arity,
                         prec, flags, max_refine, _stream(stream), hist if info else None)
     _lib.check(st, "tsqr_lstsq")

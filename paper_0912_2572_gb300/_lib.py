@@ -48,6 +48,14 @@ SIGNATURES = {
     "tsqr_factor_autotune": (_i32, [_dp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                      ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)]),
     "tsqr_free": (_i32, [_vp]),
+    "tsqr_error_word": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "tsqr_qr_solve_host": (_i32, [_vp, _i64, _i32, _i64, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                                  _i32, _i32, _i32, _vp, _vp, _vp]),
+    "tsqr_debug_fail_allocations": (_i32, [_i32]),
+    "tsqr_batch_describe": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _i64, _i64, _i64,
+                                   ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i64]),
+    "tsqr_plan_clusters": (_i32, [_i64, _i32, _i32, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.POINTER(_i64),
+                                  ctypes.POINTER(_i32), _i64, ctypes.POINTER(_i32), _i64]),
     "tsqr_probe_fp64_peak": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "tsqr_batch_plan_create": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "tsqr_batch_plan_run": (_i32, [_vp, _vp]),
@@ -99,6 +107,21 @@ def load() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def load_checked() -> ctypes.CDLL:
+    """Load the bounds-checked build libtsqr_check.so (its own handle, its own device error
+    word) with the same signatures; built by ``build.build(check=True)``."""
+    path = os.path.join(HERE, "libtsqr_check.so")
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_0912_2572_gb300.build --check`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name, None)
+        if fn is not None:
+            fn.restype = res
+            fn.argtypes = args
+    return lib
 
 
 def check(status: int, where: str) -> None:

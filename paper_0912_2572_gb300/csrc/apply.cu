@@ -129,9 +129,13 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
   const int n = p.n, ldt = p.ldt;
   R *Bt = sm + (size_t)warp * ((size_t)ldt + n) * K;  // tile rows, column-major
   R *PR = Bt + (size_t)ldt * K;                        // pivot rows, PR[c*n + j]
+  TSQR_CHECK_OR_SKIP(p.njobs == 0 || p.job0 + jid < p.njobs, p.err)
   const JobDesc job = p.jobs[p.job0 + jid];
   const int64_t pr = job.piv_row;
   auto bcol = [&](int c) -> R * { return p.B + (int64_t)(p.col0 + c) * p.ldb; };
+  TSQR_CHECK_OR_SKIP(pr >= 0 && (p.rows == 0 || pr + n <= p.rows) &&
+                         (p.ntiles == 0 || job.tile_begin + job.tile_count <= p.ntiles),
+                     p.err)
 
 #pragma unroll
   for (int c = 0; c < K; ++c)
@@ -145,6 +149,9 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
     const int ht = td.nrows, kind = td.kind;
     const bool ge = (kind == GEQRT);
     const int64_t r0 = td.row0;
+    TSQR_CHECK_OR_SKIP(r0 >= 0 && ht >= 1 && ht <= ldt && (p.rows == 0 || r0 + ht <= p.rows) && td.refl >= 0 &&
+                           (p.nrefl == 0 || td.refl + n <= p.nrefl),
+                       p.err)
 #pragma unroll
     for (int c = 0; c < K; ++c) {
       const R *src = bcol(c) + r0;
@@ -334,10 +341,14 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
   R *PV = PC + KC;                   // staged pivot row (TSQRT / TTQRT)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
+  TSQR_CHECK_OR_SKIP(p.njobs == 0 || p.job0 + (int)blockIdx.x < p.njobs, p.err)
   const JobDesc job = p.jobs[p.job0 + blockIdx.x];
   const int64_t pr = job.piv_row;
   auto bp = [&](int64_t row, int c) -> R * { return p.B + row + (int64_t)(col0 + c) * p.ldb; };
   constexpr int PFN = (KC + 31) / 32;
+  TSQR_CHECK_OR_SKIP(pr >= 0 && (p.rows == 0 || pr + n <= p.rows) &&
+                         (p.ntiles == 0 || job.tile_begin + job.tile_count <= p.ntiles),
+                     p.err)
 
   const int nt = job.tile_count;
   for (int q = 0; q < nt; ++q) {
@@ -346,6 +357,9 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
     const int ht = td.nrows, kind = td.kind;
     const bool ge = (kind == GEQRT);
     const int64_t r0 = td.row0;
+    TSQR_CHECK_OR_SKIP(r0 >= 0 && ht >= 1 && ht <= ldt && (p.rows == 0 || r0 + ht <= p.rows) && td.refl >= 0 &&
+                           (p.nrefl == 0 || td.refl + n <= p.nrefl),
+                       p.err)
     const R *Vt = p.V + r0;
     // stage the tile: when forming Q every row below the pivot block starts at zero
     for (int c = warp; c < kc; c += kTileThreads / 32) {

@@ -236,11 +236,18 @@ __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const Jo
     return (c < n) ? p.V + pr + j + (int64_t)c * p.ldv : p.B + pr + j + (int64_t)(c - n) * p.ldb;
   };
   constexpr int PCN = (job_nc_max(CMAX) + 31) / 32;  // columns after the pivot, per lane
+  TSQR_CHECK_OR_SKIP(pr >= 0 && (p.rows == 0 || pr + n <= p.rows) && job.tile_begin >= 0 &&
+                         (p.ntiles == 0 || job.tile_begin + job.tile_count <= p.ntiles) && nc <= job_nc_max(CMAX),
+                     p.err)
 
   for (int tt = 0; tt < job.tile_count; ++tt) {
     const TileDesc td = p.tiles[job.tile_begin + tt];
     const int ht = td.nrows, kind = td.kind, off = td.off;
     const int64_t r0 = td.row0;
+    TSQR_CHECK_OR_SKIP(r0 >= 0 && ht >= 1 && ht <= ldt && (p.rows == 0 || r0 + ht <= p.rows) && kind >= GEQRT &&
+                           kind <= TTQRT && off >= 0 && off < n && td.refl >= 0 &&
+                           (p.nrefl == 0 || td.refl + n <= p.nrefl),
+                       p.err)
     const bool ge = (kind == GEQRT);
     // a TTQRT piece starting at row `off` of the child is untouched by reflectors j < off
     const int j0 = (kind == TTQRT) ? off : 0;
@@ -603,6 +610,230 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
   __syncthreads();
 }
 
+// ------------------------------------------------- cluster tier: pipelined tree levels
+// Three binary levels of the reduction tree in one launch of thread-block clusters of
+// kClusterSize CTAs (the GPU analogue of the paper's hierarchical tree, §2.3 and §3:
+// combines inside a cluster exchange their triangles on chip, through distributed shared
+// memory, and only the cluster's root goes on to the next level across the grid).
+//
+// A combine [R1; R2] -> R (TTQRT) reads at its column step j only row j of each child's
+// triangle (reflector j pivots on row j of R1 and has its tail in rows 0..j of R2, which
+// steps < j never touched), and that row is final once the child has finished its own step
+// j. So a parent starts step j as soon as both children have published j + 1 finished
+// steps: the levels of a cluster run as a pipeline, and three levels cost about n + 3 column
+// steps instead of 3n. Each CTA keeps its pivot triangle row-major in shared memory (the
+// rows of its output triangle as they become final); a parent copies a child's row j from
+// the child's shared memory (mapa + ld.shared::cluster) after an acquire load of the child's
+// progress counter, which the child advances with a release store at cluster scope. Every
+// wait is bounded: past the limit the CTA sets the device error word's timeout bit and
+// stops waiting, so the launch always ends.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_acquire_cluster_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.release.cluster.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ int cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+
+// polls of a child's progress counter before a wait gives up (each poll sleeps at least
+// 32 ns: above 0.1 s, five orders of magnitude above a combine's column step)
+constexpr uint32_t kClusterSpinLimit = 1u << 22;
+
+// One combine job of the cluster tier (a binary node: one TTQRT tile of n rows), run by
+// the factor kernel's eight warps plus a ninth, the copy warp.
+// Shared memory: T, the tile child's triangle (column-major, ld n, nc columns); PC, the
+// step's dot products then coefficients; P, the pivot triangle, row-major (ld ncp), whose
+// row j becomes this node's output row j at step j. `done` counts this CTA's finished
+// steps; `gave_up` (shared) is set once a wait timed out.
+// Column step j reads only rows 0..j of T and row j of P, so while the other warps run
+// step j the copy warp waits for the in-cluster children to finish their step j + 1 and
+// copies their row j + 1 in: the distributed-shared-memory latency overlaps the step, and
+// a step keeps the factor kernel's barriers (two named, one full).
+constexpr int kCopyWarp = kScalarWarp + 1;
+constexpr int kClusterThreads = kThreads + 32;
+
+template <int CMAX>
+__device__ __forceinline__ void run_node_cluster(const FactorParamsT<double> &p, const JobDesc job, const int c0,
+                                                 const int c1, unsigned char *smraw, unsigned *done, int *gave_up,
+                                                 int32_t *err) {
+  using R = double;
+  R *sm = reinterpret_cast<R *>(smraw);
+  const int n = p.n, nc = p.nc, ldt = n;
+  const int ncp = (nc + 7) & ~7;
+  R *T = sm;
+  R *PC = T + (size_t)nc * ldt;
+  R *P = PC + ncp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool sw = (warp == kScalarWarp), cw = (warp == kCopyWarp);
+  const int hl = tid & 15, hsub = (tid >> 4) & 1;
+  const TileDesc td = p.tiles[job.tile_begin];
+  const int64_t pr = job.piv_row, r0 = td.row0;
+  auto gptr = [&](int64_t row, int c) -> R * {
+    return (c < n) ? p.V + row + (int64_t)c * p.ldv : p.B + row + (int64_t)(c - n) * p.ldb;
+  };
+  constexpr int PCN = (job_nc_max(CMAX) + 31) / 32;
+  TSQR_CHECK_OR_SKIP(job.tile_count == 1 && td.kind == TTQRT && td.nrows == n && td.off == 0 && pr >= 0 && r0 >= 0 &&
+                         (p.rows == 0 || (pr + n <= p.rows && r0 + n <= p.rows)) && td.refl >= 0 &&
+                         (p.nrefl == 0 || td.refl + n <= p.nrefl) && c0 >= -1 && c0 < kClusterSize && c1 >= -1 &&
+                         c1 < kClusterSize && nc <= job_nc_max(CMAX),
+                     p.err)
+  const uint32_t a_done = smem_u32(done), a_P = smem_u32(P);
+  // the copy warp: wait until the in-cluster children have finished `steps` steps (every
+  // lane polls, so each lane's later loads are ordered after its own acquire), then copy
+  // their row `row` into P / T
+  auto fetch_row = [&](int row) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ch = q == 0 ? c0 : c1;
+      if (ch < 0) continue;  // warp-uniform
+      if (!*gave_up) {
+        const uint32_t a = cluster_map(a_done, ch);
+        uint32_t it = 0;
+        while (ld_acquire_cluster_u32(a) < (uint32_t)(row + 1)) {
+          if (++it > kClusterSpinLimit) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            *gave_up = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __syncwarp();
+      for (int c = row + lane; c < nc; c += 32) {
+        const R v = ld_cluster_f64(cluster_map(a_P + (uint32_t)(sizeof(R) * ((size_t)row * ncp + c)), ch));
+        if (q == 0)
+          P[(size_t)row * ncp + c] = v;
+        else
+          T[(size_t)c * ldt + row] = v;
+      }
+    }
+  };
+
+  // triangles complete in global memory (an earlier launch's) are staged whole; row 0 of
+  // in-cluster children before the first step
+  if (c1 < 0)
+    for (int c = warp; c < nc; c += kClusterThreads / 32) {
+      const int lim = (c < n) ? min(n, c + 1) : n;
+      warp_copy(T + (size_t)c * ldt, gptr(r0, c), lim, lane, [](const double *q) { return __ldcg(q); },
+                [](const double2 *q) { return __ldcg(q); });
+    }
+  if (c0 < 0)
+    for (int e = tid; e < n * nc; e += kClusterThreads) {
+      const int i = e % n, c = e / n;
+      if (c >= i) P[(size_t)i * ncp + c] = __ldcg(gptr(pr + i, c));
+    }
+  if (cw) fetch_row(0);
+  __syncthreads();
+
+  for (int j = 0; j < n; ++j) {
+    R *PV = P + (size_t)j * ncp;  // the pivot row of this step
+    const int lo = 0, hi = j + 1;  // reflector j's tail: rows 0..j of the child's triangle
+    if (cw) {
+      if (j + 1 < n) fetch_row(j + 1);
+    } else if (!sw) {
+      const int rw = (warp + j) % kWorkerWarps;
+      const int v = 2 * rw + hsub;
+      gram_row_dispatch<CMAX, R>(T, ldt, j, j + 1, nc, lo, hi, v, hl, rw, PC);
+      bar_arrive_n(1, kThreads);
+      bar_sync_n(2, kThreads);
+      update_dispatch<CMAX, R>(T, ldt, j, j + 1, nc, lo, hi, v, hl, rw, PC);
+    } else {
+      const R *Tj = T + (size_t)j * ldt;
+      R a0 = R(0), a1 = R(0);
+      int i = lo + lane;
+      for (; i + 32 < hi; i += 64) {
+        const R x0 = Tj[i], x1 = Tj[i + 32];
+        a0 = fma(x0, x0, a0);
+        a1 = fma(x1, x1, a1);
+      }
+      if (i < hi) a0 = fma(Tj[i], Tj[i], a0);
+      R s2 = a0 + a1;
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) s2 += __shfl_xor_sync(kFull, s2, m);
+      const Refl<R> rf = reflector<R>(PV[j], s2);
+      bar_sync_n(1, kThreads);
+      R pk[PCN];
+#pragma unroll
+      for (int q = 0; q < PCN; ++q) {
+        const int c = j + 1 + lane + 32 * q;
+        if (c < nc) {
+          const R p0 = PV[c];
+          const R w = fma(rf.scale, PC[c], p0);
+          PC[c] = rf.ts * w;
+          pk[q] = fma(-rf.tau, w, p0);
+        }
+      }
+      bar_arrive_n(2, kThreads);
+      // the output row j: kept in shared memory for the parent, and written to the pivot
+      // rows in global memory (the next launch's input, the apply kernels' R)
+#pragma unroll
+      for (int q = 0; q < PCN; ++q) {
+        const int c = j + 1 + lane + 32 * q;
+        if (c < nc) {
+          PV[c] = pk[q];
+          *gptr(pr + j, c) = pk[q];
+        }
+      }
+      if (lane == 0) {
+        PV[j] = rf.beta;
+        *gptr(pr + j, j) = rf.beta;
+        p.tau[td.refl + j] = rf.tau;
+        p.scl[td.refl + j] = rf.scale;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid == 0) st_release_cluster_u32(a_done, (uint32_t)(j + 1));
+  }
+  // the child's triangle becomes this node's triangular reflector block
+  for (int c = warp; c < nc; c += kClusterThreads / 32) {
+    const int lim = (c < n) ? min(n, c + 1) : n;
+    warp_copy(gptr(r0, c), T + (size_t)c * ldt, lim, lane, [](const double *q) { return *q; },
+              [](const double2 *q) { return *q; });
+  }
+}
+
+template <int CMAX>
+__global__ void __launch_bounds__(kClusterThreads, 2) k_factor_cluster(const FactorParamsT<double> p,
+                                                                       const ClusterSlot *__restrict__ slots,
+                                                                       int32_t *err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned s_done;
+  __shared__ int s_gave_up;
+  const ClusterSlot sl = slots[blockIdx.x];
+  if (threadIdx.x == 0) {
+    s_done = 0;
+    s_gave_up = 0;
+  }
+  cluster_barrier();  // every counter is initialised before any CTA of the cluster polls it
+  if (sl.job >= 0)
+    run_node_cluster<CMAX>(p, p.jobs[sl.job], sl.child[0], sl.child[1], smraw, &s_done, &s_gave_up, err);
+  cluster_barrier();  // no CTA leaves while a parent may still read its shared memory
+}
+
 // MINB = CTAs resident per SM the launch is planned for (2, or 3 with shorter tiles: more
 // independent column-step sequences per SM hide more of each step's serial latency).
 template <int CMAX, int MINB>
@@ -756,7 +987,51 @@ cudaError_t launch_factor_any(const FactorParamsT<double> &p, int njobs, int cta
   return launch_factor_c<2>(p, njobs, s);
 }
 
+template <int CMAX>
+cudaError_t launch_cluster_t(const FactorParamsT<double> &p, const ClusterSlot *slots, int nclusters, int32_t *err,
+                             cudaStream_t s) {
+  const int ncp = (p.nc + 7) & ~7;
+  const size_t bytes = sizeof(double) * ((size_t)p.nc * p.n + ncp + (size_t)p.n * ncp);
+  cudaError_t e = cudaFuncSetAttribute(k_factor_cluster<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nclusters * kClusterSize));
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_factor_cluster<CMAX>, p, slots, err);
+}
+
+__device__ int32_t g_error_word;
+
 }  // namespace
+
+size_t cluster_smem_bytes(int n, int nc, size_t optin_per_block) {
+  const size_t ncp = (size_t)((nc + 7) & ~7);
+  const size_t b = sizeof(double) * ((size_t)nc * n + ncp + (size_t)n * ncp);
+  return b <= optin_per_block ? b : 0;
+}
+
+cudaError_t launch_factor_cluster(const FactorParamsT<double> &p, const ClusterSlot *slots, int nclusters,
+                                  int32_t *err, cudaStream_t s) {
+  if (nclusters <= 0) return cudaSuccess;
+  if (p.nc <= 16) return launch_cluster_t<1>(p, slots, nclusters, err, s);
+  if (p.nc <= 32) return launch_cluster_t<2>(p, slots, nclusters, err, s);
+  if (p.nc <= 64) return launch_cluster_t<4>(p, slots, nclusters, err, s);
+  return launch_cluster_t<8>(p, slots, nclusters, err, s);
+}
+
+cudaError_t device_error_word(int32_t **ptr) {
+  return cudaGetSymbolAddress(reinterpret_cast<void **>(ptr), g_error_word);
+}
 
 size_t factor_smem_bytes(int nc, int ldt, size_t elem) {
   const size_t ncp = (size_t)((nc + 7) & ~7);

@@ -3,8 +3,9 @@
 //
 // Requests (tsqr_batch_item, device buffers owned by the caller) are queued by
 // tsqr_server_submit. A worker thread keeps up to `streams` batches in flight: whenever
-// a stream is free it admits the oldest pending requests, as many as fit the memory
-// budget still free (admission by device memory), up to max_batch, and launches them as
+// a stream is free it admits the oldest pending requests, as many as fit the device
+// memory free at that moment (and the caller's budget, if set), up to max_batch, and
+// launches them as
 // one persistent kernel on that stream. Completion is observed with an event per batch;
 // the request's latency runs from its submission to that observation. Requests that
 // arrive while others are on the GPU join the next batch as soon as a stream and memory
@@ -44,7 +45,8 @@ struct SrvSlot {
 
 struct tsqr_server {
   int device = 0;
-  size_t budget = 0, used = 0;
+  size_t budget = 0, used = 0;  // budget 0: admission by the live free device memory only
+  size_t last_free = 0;         // free device memory seen at the last admission
   int32_t max_batch = 256, chain_tiles = 0, ctas_per_sm = 0;
   std::vector<SrvSlot> slots;
   std::mutex mu;
@@ -81,13 +83,17 @@ static void server_loop(tsqr_server *S) {
     }
     for (SrvSlot &sl : S->slots) {
       if (sl.busy || S->pending.empty()) continue;
-      // admit the oldest requests that fit the free memory; a request larger than the
-      // whole budget runs alone once nothing else is in flight
+      // admit the oldest requests that fit the device memory free now (less a 5% margin;
+      // the in-flight batches' workspaces are already taken from it) and the budget, if
+      // one was set; a request larger than either runs alone once nothing else is in flight
+      const size_t live = tsqr::live_free_bytes();
+      S->last_free = live;
+      const size_t room = live - live / 20;
       std::vector<SrvReq> batch;
       size_t bytes = 0;
       while (!S->pending.empty() && (int32_t)batch.size() < S->max_batch) {
         const SrvReq &r = S->pending.front();
-        const bool fits = S->used + bytes + r.bytes <= S->budget;
+        const bool fits = bytes + r.bytes <= room && (S->budget == 0 || S->used + bytes + r.bytes <= S->budget);
         if (!fits && !(batch.empty() && S->used == 0)) break;
         bytes += r.bytes;
         batch.push_back(r);
@@ -138,12 +144,8 @@ tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t str
     delete S;
     return TSQR_ERR_CUDA;
   }
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-    delete S;
-    return TSQR_ERR_CUDA;
-  }
-  S->budget = max_bytes > 0 ? (size_t)max_bytes : free_b / 2;
+  S->budget = max_bytes > 0 ? (size_t)max_bytes : 0;
+  S->last_free = tsqr::live_free_bytes();
   S->max_batch = max_batch;
   S->chain_tiles = chain_tiles;
   S->ctas_per_sm = ctas_per_sm;
@@ -208,7 +210,7 @@ tsqr_status tsqr_server_stats(tsqr_server *S, int64_t *out) {
   out[1] = S->completed;
   out[2] = S->batches;
   out[3] = S->max_batch_seen;
-  out[4] = (int64_t)S->budget;
+  out[4] = (int64_t)(S->budget ? S->budget : S->last_free);
   out[5] = (int64_t)S->used;
   return TSQR_OK;
 }

@@ -2,6 +2,7 @@
 // reduction tree), the device-resident plan cache, the factor-set object and the opt-in
 // launch profiler. Every public entry point is declared and documented in include/tsqr.h.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -72,26 +73,57 @@ DeviceInfo device_info(int dev) {
   return d;
 }
 
-// Stream-ordered allocations come from the device's default pool, kept cached so
-// that repeated factorizations do not return memory to the driver.
-cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+// Test hook (tsqr_debug_fail_allocations): the next N device allocations of the library
+// fail as if the device were out of memory.
+std::atomic<int32_t> g_fail_allocs{0};
+
+// Stream-ordered allocations come from a memory pool of the library's own, one per device,
+// kept cached so that repeated factorizations do not return memory to the driver. Its
+// blocks freed on one stream are not reused by another stream through an inserted
+// dependency (cudaMemPoolReuseAllowInternalDependencies off): calls in flight on two
+// streams (the server's batches, pipelined host-buffer calls) then take fresh memory
+// instead of waiting for the other call's end.
+cudaError_t lib_pool(int dev, cudaMemPool_t *out) {
   static std::mutex mu;
-  static std::vector<int> done;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (std::find(done.begin(), done.end(), dev) == done.end()) {
-      cudaMemPool_t pool;
-      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-      }
-      done.push_back(dev);
+  static std::vector<std::pair<int, cudaMemPool_t>> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto &dp : pools)
+    if (dp.first == dev) {
+      *out = dp.second;
+      return cudaSuccess;
     }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  cudaError_t e = cudaMemPoolCreate(&pool, &props);
+  if (e != cudaSuccess) return e;
+  uint64_t thr = UINT64_MAX;
+  int no = 0;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  if (e != cudaSuccess) {
+    cudaMemPoolDestroy(pool);
+    return e;
   }
+  pools.push_back({dev, pool});
+  *out = pool;
+  return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+  for (int32_t f = g_fail_allocs.load(); f > 0; f = g_fail_allocs.load())
+    if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return cudaErrorMemoryAllocation;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  e = lib_pool(dev, &pool);
+  if (e != cudaSuccess) return e;
   if (bytes == 0) bytes = 16;
-  return cudaMallocAsync(p, bytes, s);
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 // One non-blocking helper stream per device, for work the library overlaps with the
@@ -154,7 +186,72 @@ struct Plan {
   std::vector<TileDesc> tiles;
   std::vector<JobDesc> jobs;
   std::vector<LaunchDesc> launches;  // launch 0: chains; 1..: tree levels
+  // TSQR_CLUSTER: the factorization runs binary levels lo..hi of the tree in one launch of
+  // clusters (kClusterSize slots per cluster); the apply kernels keep the per-level launches
+  struct ClusterLaunch {
+    int32_t slot_begin, nclusters, level_lo, level_hi;
+  };
+  std::vector<ClusterLaunch> cl_launches;
+  std::vector<ClusterSlot> cl_slots;
+  int cl_base = 0;  // tree levels 1..cl_base run one launch each before the cluster launches
+  // factorization launches (the chain launch, the per-level tree launches, the cluster launches)
+  int factor_launches() const {
+    return cl_launches.empty() ? (int)launches.size() : 1 + cl_base + (int)cl_launches.size();
+  }
 };
+
+// Groups the binary tree's levels three at a time into cluster launches: cluster c of the
+// launch based at level b holds the 8 consecutive nodes 8c..8c+7 of level b (complete in
+// global memory) and the combine jobs of levels b+1..b+3 over them. Node i of level t covers
+// the base nodes [i 2^(t-b), (i+1) 2^(t-b)) (a lone node passes up only at the end of a
+// level), so the groups are exactly subtrees of the binary tree.
+//
+// Levels wide enough to fill the GPU (more clusters than fit at once: max_ctas CTAs) stay
+// one launch per level: there the combines are throughput-bound and a cluster's waiting
+// CTAs would only take slots (measured at 4M x 64: 1.60 ms for levels 1-3 as one cluster
+// launch of four waves, 1.28 ms as three launches). The cluster launches start at the
+// first level whose clusters all fit at once, where the levels are latency-bound.
+static void plan_clusters(Plan &pl, int64_t max_ctas) {
+  const int L = (int)pl.launches.size() - 1;
+  if (L < 1) return;
+  std::vector<int64_t> N(L + 1);
+  N[0] = pl.launches[0].job_count;
+  for (int t = 1; t <= L; ++t) N[t] = (N[t - 1] + 1) / 2;
+  int b0 = 0;
+  while (b0 < L && (N[b0] + kClusterSize - 1) / kClusterSize * kClusterSize > max_ctas) ++b0;
+  if (b0 >= L) return;
+  pl.cl_base = b0;
+  for (int b = b0; b < L; b += 3) {
+    const int top = std::min(L, b + 3);
+    const int64_t span = int64_t(1) << (top - b);
+    const int64_t ncl = (N[b] + span - 1) / span;
+    Plan::ClusterLaunch cl{(int32_t)pl.cl_slots.size(), (int32_t)ncl, b + 1, top};
+    for (int64_t c = 0; c < ncl; ++c) {
+      ClusterSlot sl[kClusterSize];
+      for (auto &x : sl) x = {-1, {-1, -1}, 0};
+      int prod[4][kClusterSize];  // cluster rank producing node (level t - b, local index)
+      for (int q = 0; q < kClusterSize; ++q) prod[0][q] = -1;
+      int rank = 0;
+      for (int t = b + 1; t <= top; ++t) {
+        const int64_t per = span >> (t - b);
+        for (int64_t il = 0; il < per; ++il) {
+          const int64_t i = c * per + il;
+          if (i >= N[t]) break;
+          int *pv = prod[t - b - 1];
+          const int64_t l0 = 2 * il;  // local index of node 2i at level t - 1
+          if (i < N[t - 1] / 2) {
+            sl[rank] = {pl.launches[t].job_begin + (int32_t)i, {pv[l0], pv[l0 + 1]}, 0};
+            prod[t - b][il] = rank++;
+          } else {
+            prod[t - b][il] = pv[l0];  // passes up unchanged
+          }
+        }
+      }
+      pl.cl_slots.insert(pl.cl_slots.end(), sl, sl + kClusterSize);
+    }
+    pl.cl_launches.push_back(cl);
+  }
+}
 
 static void plan_build(Plan &pl, int64_t chains_target) {
   const int64_t m = pl.m, h = pl.leaf_h;
@@ -265,7 +362,7 @@ static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n
   pl.nc = nc;
   pl.leaf_h = leaf_h;
   pl.arity = arity;
-  pl.flags = flags & TSQR_TWO_LEVEL;
+  pl.flags = flags & (TSQR_TWO_LEVEL | TSQR_CLUSTER);
   pl.mixed = mixed;
   if (!choose_tiles(di, n, nc, leaf_h, pl.tile_h, pl.ctas_per_sm, mixed ? sizeof(float) : sizeof(double), max_cps))
     return fail(TSQR_ERR_UNSUPPORTED, "no tile height fits shared memory for nc=%d", nc);
@@ -274,6 +371,12 @@ static tsqr_status make_plan_on(const DeviceInfo &di, Plan &pl, int64_t m, int n
   const int64_t chains = chains_override > 0 ? chains_override : (int64_t)di.sms * pl.ctas_per_sm * 4;
   try {
     plan_build(pl, chains);
+    const size_t csm = cluster_smem_bytes(n, nc, di.optin);
+    // resident cluster CTAs per SM: the shared-memory limit, and the register limit (288
+    // threads per CTA at 64 registers, 80 beyond 64 columns: three, two)
+    const int64_t cl_cps = std::min<int64_t>(nc > 64 ? 2 : 3, (int64_t)(di.smem_sm / (csm + di.reserved + 1024)));
+    if ((pl.flags & TSQR_CLUSTER) && pl.arity == 2 && !mixed && csm > 0 && cl_cps >= 1)
+      plan_clusters(pl, (int64_t)di.sms * cl_cps);
     if (mixed) {
       // the tree works on a compact FP64 array: chain c's pivot block at rows c*n..c*n+n-1
       std::vector<std::pair<int64_t, int64_t>> idx;  // (global pivot row, chain)
@@ -307,12 +410,15 @@ struct DevPlan {
   int device = -1;
   JobDesc *jobs = nullptr;
   TileDesc *tiles = nullptr;
+  ClusterSlot *slots = nullptr;
+  int32_t *err = nullptr;  // the device error word
   ~DevPlan() {
     int cur = 0;
     cudaGetDevice(&cur);
     if (device >= 0) cudaSetDevice(device);
     if (jobs) cudaFree(jobs);
     if (tiles) cudaFree(tiles);
+    if (slots) cudaFree(slots);
     cudaSetDevice(cur);
   }
 };
@@ -326,7 +432,7 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
   const bool mixed = false;  // the mixed path plans through the batched engine
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  flags &= TSQR_TWO_LEVEL;
+  flags &= (TSQR_TWO_LEVEL | TSQR_CLUSTER);
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
@@ -350,6 +456,12 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
   CUDA_TRY(cudaMalloc(&dp->tiles, sizeof(TileDesc) * pl.tiles.size()));
   CUDA_TRY(cudaMemcpy(dp->jobs, pl.jobs.data(), sizeof(JobDesc) * pl.jobs.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(dp->tiles, pl.tiles.data(), sizeof(TileDesc) * pl.tiles.size(), cudaMemcpyHostToDevice));
+  if (!pl.cl_slots.empty()) {
+    CUDA_TRY(cudaMalloc(&dp->slots, sizeof(ClusterSlot) * pl.cl_slots.size()));
+    CUDA_TRY(cudaMemcpy(dp->slots, pl.cl_slots.data(), sizeof(ClusterSlot) * pl.cl_slots.size(),
+                        cudaMemcpyHostToDevice));
+  }
+  CUDA_TRY(device_error_word(&dp->err));
   std::lock_guard<std::mutex> lk(g_plan_mu);
   g_plans.push_front(dp);
   while (g_plans.size() > kPlanCacheSize) g_plans.pop_back();
@@ -401,6 +513,44 @@ static void factors_release(tsqr_factors *F) {
   delete F;
 }
 
+// The bounds a TSQR_CHECK build checks every job and tile descriptor against.
+template <typename P>
+static void set_bounds(const tsqr_factors *F, P &p) {
+  const Plan &pl = F->plan();
+  p.rows = pl.m;
+  p.nrefl = (int64_t)pl.tiles.size() * pl.n;
+  p.ntiles = (int32_t)pl.tiles.size();
+  p.njobs = (int32_t)pl.jobs.size();
+  p.err = F->dp->err;
+}
+
+// Factorization launch q of F's plan: the chain launch (q = 0), then one tree level per
+// launch, or with TSQR_CLUSTER one cluster launch per three levels. p.job0 is set here.
+static cudaError_t factor_launch(const tsqr_factors *F, FactorParams &p, int q, cudaStream_t s) {
+  const Plan &pl = F->plan();
+  if (q > pl.cl_base && !pl.cl_launches.empty()) {
+    const Plan::ClusterLaunch &cl = pl.cl_launches[q - 1 - pl.cl_base];
+    p.job0 = 0;
+    ProfScope ps(TSQR_PROF_FACTOR_TREE, s);
+    return launch_factor_cluster(p, F->dp->slots + cl.slot_begin, cl.nclusters,
+                                 F->dp->err, s);
+  }
+  const LaunchDesc &ld = pl.launches[q];
+  p.job0 = ld.job_begin;
+  ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
+  return launch_factor(p, ld.job_count, s, q == 0 ? pl.ctas_per_sm : 2);
+}
+
+// The binary tree levels (apply launches) that factorization launch q completes.
+static void factor_launch_levels(const Plan &pl, int q, int &lo, int &hi) {
+  if (q > pl.cl_base && !pl.cl_launches.empty()) {
+    lo = pl.cl_launches[q - 1 - pl.cl_base].level_lo;
+    hi = pl.cl_launches[q - 1 - pl.cl_base].level_hi;
+  } else {
+    lo = hi = q;
+  }
+}
+
 // Runs the factorization launches of F on A (first touch) and optional extra columns B.
 static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, double *B, int64_t ldb,
                               cudaStream_t s) {
@@ -419,12 +569,8 @@ static tsqr_status run_factor(tsqr_factors *F, const double *A, int64_t lda, dou
   p.n = pl.n;
   p.nc = B ? pl.nc : pl.n;
   p.ldt = pl.tile_h;
-  for (size_t q = 0; q < pl.launches.size(); ++q) {
-    const LaunchDesc &ld = pl.launches[q];
-    p.job0 = ld.job_begin;
-    ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
-    CUDA_TRY(launch_factor(p, ld.job_count, s, q == 0 ? pl.ctas_per_sm : 2));
-  }
+  set_bounds(F, p);
+  for (int q = 0; q < pl.factor_launches(); ++q) CUDA_TRY(factor_launch(F, p, q, s));
   return TSQR_OK;
 }
 
@@ -448,6 +594,7 @@ static tsqr_status apply_launch(const tsqr_factors *F, double *B, int64_t ldb, i
   p.formq = formq;
   p.col0 = c0;
   p.k = kg;
+  set_bounds(F, p);
   const LaunchDesc &ld = pl.launches[li];
   p.job0 = ld.job_begin;
   const int sms = device_info(F->device).sms;
@@ -498,7 +645,7 @@ static void plan_info(const Plan &pl, int64_t *out) {
   out[3] = pl.tile_h;
   out[4] = (int64_t)pl.jobs.size();
   out[5] = (int64_t)pl.tiles.size();
-  out[6] = (int64_t)pl.launches.size() + 1;
+  out[6] = (int64_t)pl.factor_launches() + 1;
   out[7] = pl.ctas_per_sm;
 }
 
@@ -563,13 +710,22 @@ struct BatchBuild {
   int32_t max_steps = kRefineSteps;  // refinement launches (mixed least-squares items)
 };
 
+tsqr_status batch_build_on(DeviceInfo di, const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                           int32_t arity, BatchBuild &b, int32_t max_steps, int32_t ctas_per_sm);
+
 tsqr_status batch_build(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
                         BatchBuild &b, int32_t max_steps = kRefineSteps, int32_t ctas_per_sm = 0) {
-  b.max_steps = max_steps;
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  DeviceInfo di = device_info(dev);
+  const DeviceInfo di = device_info(dev);
   if (di.sms == 0) return fail(TSQR_ERR_CUDA, "cannot query device %d", dev);
+  return batch_build_on(di, items, count, chain_tiles, arity, b, max_steps, ctas_per_sm);
+}
+
+// The host planning of a batch for a device described by di (no CUDA call).
+tsqr_status batch_build_on(DeviceInfo di, const tsqr_batch_item *items, int32_t count, int32_t chain_tiles,
+                           int32_t arity, BatchBuild &b, int32_t max_steps, int32_t ctas_per_sm) {
+  b.max_steps = max_steps;
   // the persistent kernel has a few bytes of static shared memory, and allocations are
   // rounded up: budget for both so that two CTAs per SM still fit where planned
   di.reserved += kBatchSmemSlack;
@@ -1066,6 +1222,22 @@ size_t tsqr::batch_item_bytes(const tsqr_batch_item &it) {
 
 const char *tsqr::last_error_text() { return g_last_error.c_str(); }
 
+// Device memory a new batch can take now: what the driver reports free plus what the
+// library's stream-ordered pool holds reserved but unused (it keeps freed blocks cached).
+size_t tsqr::live_free_bytes() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && lib_pool(dev, &pool) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+      free_b += (size_t)(reserved - used);
+  }
+  return free_b;
+}
+
 tsqr_status tsqr::set_last_error(tsqr_status s, const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -1140,6 +1312,27 @@ const char *tsqr_strerror(tsqr_status s) {
 
 const char *tsqr_last_error(void) { return g_last_error.c_str(); }
 
+tsqr_status tsqr_debug_fail_allocations(int32_t count) {
+  if (count < 0) return fail(TSQR_ERR_ARG, "count < 0");
+  g_fail_allocs.store(count);
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_error_word(void *stream, int32_t *word) {
+  g_last_error.clear();
+  if (!word) return fail(TSQR_ERR_ARG, "word is NULL");
+  int32_t *d = nullptr;
+  CUDA_TRY(device_error_word(&d));
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *word = h;
+  if (h & kErrTimeout) return fail(TSQR_ERR_TIMEOUT, "a bounded device wait gave up (error word 0x%x)", h);
+  return TSQR_OK;
+}
+
 }  // extern "C"
 
 // The factorization's launches on s; with QB, also Q^T QB on a helper stream of the
@@ -1153,7 +1346,7 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
   if (st != TSQR_OK) return st;
   if (!F) return fail(TSQR_ERR_ARG, "F is NULL");
   if (R && ldr < n) return fail(TSQR_ERR_ARG, "ldr=%lld < n=%d", (long long)ldr, n);
-  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "tsqr_factor: TSQR_MIXED is served by tsqr_lstsq");
   if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   *F = nullptr;
@@ -1179,7 +1372,7 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
     cudaStream_t hs = helper_stream(f->device);
     if (!hs) st = fail(TSQR_ERR_CUDA, "no helper stream");
     const Plan &pl = f->plan();
-    const int nl = (int)pl.launches.size();
+    const int nl = pl.factor_launches();
     std::vector<cudaEvent_t> ev(nl + 1, nullptr);
     cudaError_t e = cudaSuccess;
     for (int q = 0; q <= nl && e == cudaSuccess && st == TSQR_OK; ++q)
@@ -1205,22 +1398,21 @@ static tsqr_status factor_common(const double *A, int64_t m, int32_t n, int64_t 
     p.n = pl.n;
     p.nc = pl.n;
     p.ldt = pl.tile_h;
+    set_bounds(f, p);
     const int group = apply_group(kqb);
     for (int q = 0; q < nl && st == TSQR_OK; ++q) {
-      const LaunchDesc &ld = pl.launches[q];
-      p.job0 = ld.job_begin;
-      {
-        ProfScope ps(q == 0 ? TSQR_PROF_FACTOR_CHAINS : TSQR_PROF_FACTOR_TREE, s);
-        e = launch_factor(p, ld.job_count, s, q == 0 ? pl.ctas_per_sm : 2);
-      }
+      e = factor_launch(f, p, q, s);
       if (e == cudaSuccess) e = cudaEventRecord(ev[q], s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ev[q], 0);
       if (e != cudaSuccess) {
         st = fail(TSQR_ERR_CUDA, "factor launch %d: %s", q, cudaGetErrorString(e));
         break;
       }
-      for (int c0 = 0; c0 < kqb && st == TSQR_OK; c0 += group)
-        st = apply_launch(f, QB, ldqb, c0, std::min(group, kqb - c0), 1, 0, q, hs);
+      int lo = 0, hi = 0;
+      factor_launch_levels(pl, q, lo, hi);
+      for (int li = lo; li <= hi && st == TSQR_OK; ++li)
+        for (int c0 = 0; c0 < kqb && st == TSQR_OK; c0 += group)
+          st = apply_launch(f, QB, ldqb, c0, std::min(group, kqb - c0), 1, 0, li, hs);
     }
     // joined even after a failed launch: the factor set's buffers are freed in the order
     // of s, after whatever the helper stream still reads
@@ -1337,7 +1529,7 @@ static tsqr_status caqr_factor(const double *A, int64_t m, int32_t n, int64_t ld
   if (st != TSQR_OK) return st;
   if (!F) return fail(TSQR_ERR_ARG, "F is NULL");
   if (R && ldr < n) return fail(TSQR_ERR_ARG, "ldr=%lld < n=%d", (long long)ldr, n);
-  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   *F = nullptr;
   const int32_t b = panel > 0 ? panel : kCaqrPanel;
   tsqr_factors *f = new (std::nothrow) tsqr_factors();
@@ -1378,7 +1570,7 @@ static tsqr_status caqr_factor(const double *A, int64_t m, int32_t n, int64_t ld
     tsqr_factors *fp = nullptr;
     // the panel in place in the working copy; Q_p^T of the trailing columns overlaps the
     // panel's reduction tree (tsqr_factor_qt's launch pairing)
-    st = factor_common(Wp, m - c0, bp, f->ldv, leaf_h, arity, TSQR_FP64, (flags & TSQR_TWO_LEVEL) | TSQR_INPLACE, s,
+    st = factor_common(Wp, m - c0, bp, f->ldv, leaf_h, arity, TSQR_FP64, (flags & (TSQR_TWO_LEVEL | TSQR_CLUSTER)) | TSQR_INPLACE, s,
                        &fp, f->Rfull + c0 + (int64_t)c0 * n, n, Tp, f->ldv, kt);
     if (st != TSQR_OK) break;
     f->panels.push_back(fp);
@@ -1410,11 +1602,11 @@ static tsqr_status caqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda
   if (!B || !X) return fail(TSQR_ERR_ARG, "B or X is NULL");
   if (k < 1 || k > 64) return fail(TSQR_ERR_ARG, "k=%d outside [1, 64]", k);
   if (ldb < m || ldx < n) return fail(TSQR_ERR_ARG, "bad ldb/ldx");
-  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   if (prec == TSQR_MIXED) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_MIXED least squares takes n <= 128");
   if (prec != TSQR_FP64) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   tsqr_factors *F = nullptr;
-  st = caqr_factor(A, m, n, lda, 0, leaf_h, arity, flags & TSQR_TWO_LEVEL, s, &F, nullptr, 0);
+  st = caqr_factor(A, m, n, lda, 0, leaf_h, arity, flags & (TSQR_TWO_LEVEL | TSQR_CLUSTER), s, &F, nullptr, 0);
   if (st != TSQR_OK) return st;
   double *W = nullptr;  // Q^T B workspace (m-by-k)
   int32_t *status = nullptr;
@@ -1540,7 +1732,7 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   if (!B || !X) return fail(TSQR_ERR_ARG, "B or X is NULL");
   if (k < 1 || k > 64) return fail(TSQR_ERR_ARG, "k=%d outside [1, 64]", k);
   if (ldb < m || ldx < n) return fail(TSQR_ERR_ARG, "bad ldb/ldx");
-  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   if (max_refine < 0) return fail(TSQR_ERR_ARG, "max_refine < 0");
   if (prec != TSQR_FP64 && prec != TSQR_MIXED) return fail(TSQR_ERR_ARG, "unknown prec %d", prec);
   flags &= ~TSQR_INPLACE;
@@ -1612,6 +1804,92 @@ tsqr_status tsqr_lstsq(const double *A, int64_t m, int32_t n, int64_t lda, const
   return st;
 }
 
+
+// A column-major block copy: one linear copy when both leading dimensions equal the rows.
+static cudaError_t copy_block(double *dst, int64_t ldd, const double *src, int64_t lds, int64_t rows, int64_t cols,
+                              cudaMemcpyKind kind, cudaStream_t s) {
+  if (ldd == rows && lds == rows) return cudaMemcpyAsync(dst, src, sizeof(double) * rows * cols, kind, s);
+  return cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * lds, sizeof(double) * rows, cols, kind, s);
+}
+
+tsqr_status tsqr_qr_solve_host(const double *A, int64_t m, int32_t n, int64_t lda, const double *B, int64_t ldb,
+                               int32_t k, double *Q, int64_t ldq, double *R, int64_t ldr, double *X, int64_t ldx,
+                               int32_t *status, int32_t leaf_h, int32_t arity, int32_t flags, void *stream,
+                               void *after, void *done) {
+  g_last_error.clear();
+  tsqr_status st = check_factor_args(A, m, n, lda, leaf_h, arity);
+  if (st != TSQR_OK) return st;
+  if ((B == nullptr) != (X == nullptr)) return fail(TSQR_ERR_ARG, "B and X go together");
+  if (B && (k < 1 || ldb < m || ldx < n)) return fail(TSQR_ERR_ARG, "bad k=%d, ldb or ldx", k);
+  if (Q && ldq < m) return fail(TSQR_ERR_ARG, "ldq=%lld < m", (long long)ldq);
+  if (R && ldr < n) return fail(TSQR_ERR_ARG, "ldr=%lld < n", (long long)ldr);
+  if (flags & ~(TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (!B) k = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  // device copies of the inputs and outputs, from the stream-ordered pool
+  double *Ad = nullptr, *Bd = nullptr, *Qd = nullptr, *Rd = nullptr, *Xd = nullptr;
+  int32_t *sd = nullptr;
+  cudaError_t e = pool_alloc((void **)&Ad, sizeof(double) * (size_t)m * n, s);
+  if (e == cudaSuccess && B) e = pool_alloc((void **)&Bd, sizeof(double) * (size_t)m * k, s);
+  if (e == cudaSuccess && B) e = pool_alloc((void **)&Xd, sizeof(double) * (size_t)n * k, s);
+  if (e == cudaSuccess && Q) e = pool_alloc((void **)&Qd, sizeof(double) * (size_t)m * n, s);
+  if (e == cudaSuccess) e = pool_alloc((void **)&Rd, sizeof(double) * (size_t)n * n, s);
+  if (e == cudaSuccess) e = pool_alloc((void **)&sd, sizeof(int32_t), s);
+  if (e != cudaSuccess) st = fail(TSQR_ERR_OOM, "device buffers: %s", cudaGetErrorString(e));
+  if (st == TSQR_OK) {
+    e = copy_block(Ad, m, A, lda, m, n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && B) e = copy_block(Bd, m, B, ldb, m, k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sd, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && after) e = cudaStreamWaitEvent(s, (cudaEvent_t)after, 0);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "input copies: %s", cudaGetErrorString(e));
+  }
+  tsqr_factors *F = nullptr;
+  if (st == TSQR_OK) st = factor_common(Ad, m, n, m, leaf_h, arity, TSQR_FP64, flags, s, &F, Rd, n, nullptr, 0, 0);
+  // Q^T B and the back substitution on the library's helper stream, beside the thin Q
+  cudaStream_t hs = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool forked = false;
+  if (st == TSQR_OK && B) {
+    hs = helper_stream(F->device);
+    e = hs ? cudaSuccess : cudaErrorNotReady;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ev[0], 0);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "helper stream fork: %s", cudaGetErrorString(e));
+    forked = st == TSQR_OK;
+    if (st == TSQR_OK) st = apply_impl(F, Bd, m, k, 1, hs);
+    if (st == TSQR_OK) {
+      ProfScope ps(TSQR_PROF_SMALL, hs);
+      e = launch_trsv(F->V, F->ldv, n, Bd, m, k, Xd, n, F->d, sd, hs);
+      if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "trsv: %s", cudaGetErrorString(e));
+    }
+  }
+  if (st == TSQR_OK && Q) st = form_q_impl(F, Qd, m, s);
+  if (forked) {  // joined even after a failure: the buffers are freed in the order of s
+    e = cudaEventRecord(ev[1], hs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    if (e != cudaSuccess && st == TSQR_OK) st = fail(TSQR_ERR_CUDA, "helper stream join: %s", cudaGetErrorString(e));
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (st == TSQR_OK && done) {
+    e = cudaEventRecord((cudaEvent_t)done, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "done event: %s", cudaGetErrorString(e));
+  }
+  if (st == TSQR_OK) {
+    e = cudaSuccess;
+    if (Q) e = copy_block(Q, ldq, Qd, m, m, n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && R) e = copy_block(R, ldr, Rd, n, n, n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && X) e = copy_block(X, ldx, Xd, n, n, k, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, sd, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = fail(TSQR_ERR_CUDA, "output copies: %s", cudaGetErrorString(e));
+  }
+  if (F) factors_release(F);
+  for (void *b : {(void *)Ad, (void *)Bd, (void *)Qd, (void *)Rd, (void *)Xd, (void *)sd})
+    if (b) cudaFreeAsync(b, s);
+  return st;
+}
 
 tsqr_status tsqr_batch_plan_create(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
                                    tsqr_batch_plan **out) {
@@ -1844,7 +2122,7 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
   if (st != TSQR_OK) return st;
   if (!out) return fail(TSQR_ERR_ARG, "out is NULL");
   if (nc < n || nc > 256) return fail(TSQR_ERR_ARG, "nc=%d outside [n, 256]", nc);
-  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(TSQR_INPLACE | TSQR_TWO_LEVEL | TSQR_CLUSTER)) return fail(TSQR_ERR_ARG, "unknown flags 0x%x", flags);
   if (sms < 1 || smem_per_sm < 1 || smem_reserved < 0 || smem_optin < 1)
     return fail(TSQR_ERR_ARG, "bad device description");
   DeviceInfo di;
@@ -1878,6 +2156,87 @@ tsqr_status tsqr_plan_describe(int64_t m, int32_t n, int32_t nc, int32_t leaf_h,
         }
       }
     }
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_plan_clusters(int64_t m, int32_t n, int32_t nc, int32_t leaf_h, int32_t flags, int32_t sms,
+                               int64_t smem_per_sm, int64_t smem_reserved, int64_t smem_optin, int64_t *out,
+                               int32_t *launches, int64_t max_launches, int32_t *slots, int64_t max_slots) {
+  g_last_error.clear();
+  int dummy = 0;
+  tsqr_status st = check_factor_args(&dummy, m, n, m, leaf_h, 2);
+  if (st != TSQR_OK) return st;
+  if (!out) return fail(TSQR_ERR_ARG, "out is NULL");
+  if (nc < n || nc > 256) return fail(TSQR_ERR_ARG, "nc=%d outside [n, 256]", nc);
+  if (sms < 1 || smem_per_sm < 1 || smem_reserved < 0 || smem_optin < 1)
+    return fail(TSQR_ERR_ARG, "bad device description");
+  DeviceInfo di;
+  di.sms = sms;
+  di.smem_sm = (size_t)smem_per_sm;
+  di.reserved = (size_t)smem_reserved;
+  di.optin = (size_t)smem_optin;
+  Plan pl;
+  st = make_plan_on(di, pl, m, n, nc, leaf_h, 2, (flags & TSQR_TWO_LEVEL) | TSQR_CLUSTER);
+  if (st != TSQR_OK) return st;
+  out[0] = (int64_t)pl.cl_launches.size();
+  out[1] = (int64_t)pl.cl_slots.size();
+  if (launches && (int64_t)pl.cl_launches.size() > max_launches) return fail(TSQR_ERR_ARG, "max_launches too small");
+  if (slots && (int64_t)pl.cl_slots.size() > max_slots) return fail(TSQR_ERR_ARG, "max_slots too small");
+  for (size_t q = 0; launches && q < pl.cl_launches.size(); ++q) {
+    const Plan::ClusterLaunch &cl = pl.cl_launches[q];
+    launches[4 * q + 0] = cl.slot_begin;
+    launches[4 * q + 1] = cl.nclusters;
+    launches[4 * q + 2] = cl.level_lo;
+    launches[4 * q + 3] = cl.level_hi;
+  }
+  for (size_t q = 0; slots && q < pl.cl_slots.size(); ++q) {
+    slots[3 * q + 0] = pl.cl_slots[q].job;
+    slots[3 * q + 1] = pl.cl_slots[q].child[0];
+    slots[3 * q + 2] = pl.cl_slots[q].child[1];
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_batch_describe(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
+                                int32_t sms, int64_t smem_per_sm, int64_t smem_reserved, int64_t smem_optin,
+                                int64_t *out, int64_t *jobs, int64_t max_jobs) {
+  g_last_error.clear();
+  if (!out || count < 1 || !items) return fail(TSQR_ERR_ARG, "bad items/count/out");
+  if (chain_tiles < 0 || !(arity == 0 || (arity >= 2 && arity <= 16))) return fail(TSQR_ERR_ARG, "bad chain_tiles/arity");
+  if (sms < 1 || smem_per_sm < 1 || smem_reserved < 0 || smem_optin < 1)
+    return fail(TSQR_ERR_ARG, "bad device description");
+  for (int32_t q = 0; q < count; ++q) {
+    tsqr_status st = check_batch_item(items[q], q);
+    if (st != TSQR_OK) return st;
+  }
+  DeviceInfo di;
+  di.sms = sms;
+  di.smem_sm = (size_t)smem_per_sm;
+  di.reserved = (size_t)smem_reserved;
+  di.optin = (size_t)smem_optin;
+  try {
+    BatchBuild b;
+    tsqr_status st = batch_build_on(di, items, count, chain_tiles, arity, b, kRefineSteps, 0);
+    if (st != TSQR_OK) return st;
+    out[0] = b.nchains;
+    out[1] = b.njobs;
+    out[2] = b.ntiles;
+    out[3] = b.grid;
+    if (jobs && b.njobs > max_jobs) return fail(TSQR_ERR_ARG, "max_jobs too small");
+    for (int32_t j = 0; jobs && j < b.njobs; ++j) {
+      const BatchJob &bj = b.jobs[j];
+      int64_t *o = jobs + 7 * (int64_t)j;
+      o[0] = bj.inst;
+      o[1] = bj.parent;
+      o[2] = bj.nchild;
+      o[3] = bj.piv_row;
+      o[4] = bj.row64;
+      o[5] = bj.tile_begin;
+      o[6] = bj.tile_count;
+    }
+  } catch (const std::bad_alloc &) {
+    return fail(TSQR_ERR_OOM, "host allocation failed");
   }
   return TSQR_OK;
 }

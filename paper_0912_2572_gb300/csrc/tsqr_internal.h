@@ -64,6 +64,20 @@ __host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int 
 // ----------------------------------------------------------------- factor kernel
 // R is the element type of the factorization (double; float for the leaves of the
 // mixed-precision path). The input A is always FP64 and is rounded on load.
+// Index checks of a build compiled with -DTSQR_CHECK (libtsqr_check.so): a job or tile
+// descriptor that would take a kernel outside its buffers sets kErrBounds in the device
+// error word (params `err`) and the job is skipped; nothing traps. A bound of 0 is
+// unchecked. Normal builds compile the checks away.
+#ifdef TSQR_CHECK
+#define TSQR_CHECK_OR_SKIP(cond, err)         \
+  if (!(cond)) {                              \
+    if ((err) != nullptr) atomicOr((err), 2); \
+    return;                                   \
+  }
+#else
+#define TSQR_CHECK_OR_SKIP(cond, err)
+#endif
+
 template <typename R>
 struct FactorParamsT {
   const double *A;  // first-touch input for GEQRT/TSQRT tiles
@@ -80,6 +94,11 @@ struct FactorParamsT {
   int32_t nc;   // n + extra columns
   int32_t ldt;  // tile capacity in rows (shared-memory leading dimension)
   int32_t job0; // first job of this launch
+  // bounds for TSQR_CHECK builds (0 = unchecked): rows of V / A / B, entries of tau / scl,
+  // descriptors; and the device error word
+  int64_t rows, nrefl;
+  int32_t ntiles, njobs;
+  int32_t *err;
 };
 using FactorParams = FactorParamsT<double>;
 
@@ -146,6 +165,33 @@ struct BatchParams {
 
 cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s);
 
+// ------------------------------------------------------- cluster tier of the tree
+// With TSQR_CLUSTER, three binary tree levels run in one launch of thread-block clusters
+// of kClusterSize CTAs: cluster c reduces the 8 consecutive triangles 8c..8c+7 of the
+// level below (4 + 2 + 1 combine jobs, one CTA each). A combine's column step j needs only
+// row j of each child's output triangle, which is final once the child has finished its
+// own step j, so the levels run as a pipeline: a parent waits for its children's progress
+// counters and reads their rows from their shared memory (distributed shared memory).
+constexpr int kClusterSize = 8;
+struct ClusterSlot {
+  int32_t job;       // combine job of this CTA, or -1 (idle)
+  int32_t child[2];  // cluster rank producing the pivot (0) / tile (1) triangle, or -1 when
+                     // that triangle is complete in global memory (an earlier launch's)
+  int32_t pad;
+};
+// Shared memory of a cluster-tier combine CTA (the child's triangle, the dot products and
+// the pivot triangle), 0 when it exceeds the per-block maximum.
+size_t cluster_smem_bytes(int n, int nc, size_t optin_per_block);
+// err: the device error word (bit kErrTimeout set when a bounded wait gave up).
+cudaError_t launch_factor_cluster(const FactorParamsT<double> &p, const ClusterSlot *slots, int nclusters,
+                                  int32_t *err, cudaStream_t s);
+
+// Device error word: bit 1 (kErrTimeout) a bounded device wait gave up, bit 2 (kErrBounds)
+// an index check of a TSQR_CHECK build failed. One word per device.
+constexpr int32_t kErrTimeout = 1;
+constexpr int32_t kErrBounds = 2;
+cudaError_t device_error_word(int32_t **ptr);  // the current device's word
+
 // ------------------------------------------------ batched least-squares refinement
 // Mixed-precision least-squares items of a batch: after the batched factorization, one
 // launch per step of corrected semi-normal-equation refinement (refine_batch.cu). A
@@ -194,6 +240,7 @@ tsqr_status check_batch_item(const tsqr_batch_item &it, int32_t q);
 size_t batch_item_bytes(const tsqr_batch_item &it);  // device workspace estimate for admission
 int32_t resolve_batch_prec(const tsqr_batch_item &it);  // TSQR_FP64 or TSQR_MIXED
 const char *last_error_text();
+size_t live_free_bytes();  // device memory free now, counting the pool's unused reserve
 // the calling thread's error message (tsqr_last_error) for entry points outside tsqr_api.cu
 tsqr_status set_last_error(tsqr_status s, const char *fmt, ...);
 void clear_last_error();
@@ -216,6 +263,10 @@ struct ApplyParamsT {
   int32_t job0;
   int32_t trans;     // 1: Q^T (forward order), 0: Q (reverse order)
   int32_t formq;     // 1: forming the thin Q (tiles start at zero, column j >= ref j only)
+  // bounds for TSQR_CHECK builds (0 = unchecked), as FactorParamsT
+  int64_t rows, nrefl;
+  int32_t ntiles, njobs;
+  int32_t *err;
 };
 
 using ApplyParams = ApplyParamsT<double>;

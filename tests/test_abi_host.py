@@ -278,3 +278,148 @@ def test_batch_plan_entry_points_reject_bad_arguments(lib):
     assert lib.tsqr_batch_plan_run(None, None) == 1
     assert lib.tsqr_batch_plan_results(None, None, None) == 1
     assert lib.tsqr_batch_plan_destroy(None) == 0
+
+
+def clusters(lib, m, n, h, flags, nc=None, dev=GB300):
+    nc = n if nc is None else nc
+    out = (ctypes.c_int64 * 2)()
+    st = lib.tsqr_plan_clusters(m, n, nc, h, flags, dev["sms"], dev["smem"], dev["reserved"], dev["optin"], out,
+                                None, 0, None, 0)
+    assert st == 0, lib.tsqr_last_error()
+    nl, ns = out[0], out[1]
+    L = (ctypes.c_int32 * max(1, 4 * nl))()
+    S = (ctypes.c_int32 * max(1, 3 * ns))()
+    assert lib.tsqr_plan_clusters(m, n, nc, h, flags, dev["sms"], dev["smem"], dev["reserved"], dev["optin"], out,
+                                  L, nl, S, ns) == 0
+    return [tuple(L[4 * q:4 * q + 4]) for q in range(nl)], [tuple(S[3 * q:3 * q + 3]) for q in range(ns)]
+
+
+@pytest.mark.parametrize("m,n,h,flags", [
+    (4_194_304, 64, 144, 2), (1 << 20, 16, 64, 2), (100_000, 32, 64, 0), (5000, 64, 64, 0),
+    (3000, 16, 100, 0), (640, 64, 64, 0), (200, 8, 64, 0), (4096, 16, 256, 0), (1 << 20, 65, 144, 2),
+])
+def test_cluster_schedule_simulated(lib, m, n, h, flags):
+    """Host simulation of the TSQR_CLUSTER schedule against the binary tree of
+    tsqr_plan_describe: every combine job runs exactly once, in the launch that covers its
+    level; a slot's in-cluster children are the jobs that produced its pivot and tile
+    triangles (same rows), with a lower rank (the pipeline's waits point down the tree, so
+    no CTA waits on itself or in a cycle); out-of-cluster children were finished by an
+    earlier launch. Replaying the launches in order reduces every chain into the root."""
+    info, T, J = describe(lib, m, n, h, 2, flags | 4)  # TSQR_CLUSTER: the same jobs, fewer launches
+    launches, slots = clusters(lib, m, n, h, flags)
+    nlevels = max(j[3] for j in J)
+    if nlevels == 0:
+        assert launches == [] and slots == []
+        return
+    # levels too wide for one wave of clusters stay one launch each; the rest go in threes
+    base = launches[0][2] - 1
+    assert 0 <= base < nlevels and len(launches) == (nlevels - base + 2) // 3
+    chains = sum(1 for j in J if j[3] == 0)
+    width = -(-chains // 2 ** base)
+    assert -(-width // 8) * 8 <= GB300["sms"] * (2 if n > 64 else 3)  # the first cluster launch is one wave
+    assert info["launches"] == 1 + base + len(launches) + 1  # chains, plain levels, clusters, sign fix
+    seen = set()
+    done_before = {j[0]: True for j in J if j[3] <= base}  # pivot row -> its triangle is final
+    for sb, ncl, lo, hi in launches:
+        assert 1 <= lo <= hi <= nlevels and hi - lo <= 2
+        final_here = {}
+        for c in range(ncl):
+            cl = slots[sb + 8 * c: sb + 8 * c + 8]
+            for rank, (job, c0, c1) in enumerate(cl):
+                if job < 0:
+                    assert c0 == -1 and c1 == -1
+                    continue
+                piv, tb, tc, lvl = J[job]
+                assert lo <= lvl <= hi and job not in seen
+                seen.add(job)
+                assert tc == 1
+                trow = T[tb][0]
+                for ch, row in ((c0, piv), (c1, trow)):
+                    if ch < 0:
+                        assert done_before.get(row), "an external child must be final before the launch"
+                    else:
+                        assert 0 <= ch < rank
+                        cj = cl[ch][0]
+                        assert cj >= 0 and J[cj][0] == row and J[cj][3] < lvl
+                final_here[piv] = True
+        done_before.update(final_here)
+    assert seen == {i for i, j in enumerate(J) if j[3] > base}
+
+
+def test_cluster_flag_ignored_when_it_cannot_fit(lib):
+    """n = 128 triangles do not fit one CTA's shared memory twice: no cluster schedule, the
+    plain per-level launches stay."""
+    launches, slots = clusters(lib, 1 << 20, 128, 128, 2)
+    assert launches == [] and slots == []
+
+
+def batch_jobs(lib, items, chain_tiles=8, arity=2, dev=GB300):
+    arr = (_lib.BatchItem * len(items))()
+    for q, (m, n, k, prec) in enumerate(items):
+        arr[q].A, arr[q].m, arr[q].n, arr[q].lda = FAKE, m, n, m
+        arr[q].B, arr[q].ldb, arr[q].k = (FAKE if k else None), m, k
+        arr[q].R, arr[q].ldr, arr[q].X, arr[q].ldx, arr[q].prec = FAKE, n, (FAKE if k else None), n, prec
+    out = (ctypes.c_int64 * 4)()
+    st = lib.tsqr_batch_describe(arr, len(items), chain_tiles, arity, dev["sms"], dev["smem"], dev["reserved"],
+                                 dev["optin"], out, None, 0)
+    assert st == 0, lib.tsqr_last_error()
+    nj = out[1]
+    J = (ctypes.c_int64 * (7 * nj))()
+    assert lib.tsqr_batch_describe(arr, len(items), chain_tiles, arity, dev["sms"], dev["smem"], dev["reserved"],
+                                   dev["optin"], out, J, nj) == 0
+    return out[0], [tuple(J[7 * j:7 * j + 7]) for j in range(nj)]
+
+
+@pytest.mark.parametrize("chain_tiles,arity", [(8, 2), (2, 4), (32, 2), (1, 16)])
+def test_batch_job_table_simulated(lib, chain_tiles, arity):
+    """Host simulation of the persistent batched kernel's protocol on its real job table:
+    CTAs finish chain jobs in an arbitrary order; a finished job arrives at its parent's
+    counter and the last child to arrive runs the parent. Every job must run exactly once
+    and only after all of its children, every item's root must be reached exactly once,
+    and a node's child count must equal the jobs that name it as parent. Several random
+    completion orders are replayed."""
+    import random
+    g = random.Random(chain_tiles * 31 + arity)
+    items = []
+    for q in range(40):
+        n = g.choice([1, 8, 16, 33, 64, 100, 128])
+        m = max(n, int(2 ** g.uniform(8, 17)))
+        prec = g.choice([0, 1])
+        k = g.choice([0, 0, 3]) if n <= 100 else 0
+        items.append((m, n, k, prec))
+    nchains, J = batch_jobs(lib, items, chain_tiles, arity)
+    nj = len(J)
+    assert 0 < nchains <= nj
+    kids = [0] * nj
+    for j, (inst, parent, nchild, *_rest) in enumerate(J):
+        assert -1 <= parent < nj and parent != j
+        if parent >= 0:
+            assert parent >= nchains, "a chain job is never a parent"
+            assert J[parent][0] == inst, "a parent belongs to the same item"
+            kids[parent] += 1
+    for j in range(nchains, nj):
+        assert J[j][2] == kids[j] >= 2, f"node {j}: child count {J[j][2]} vs {kids[j]}"
+    assert all(J[j][2] == 0 for j in range(nchains))
+    roots = [j for j in range(nj) if J[j][1] < 0]
+    assert sorted(J[r][0] for r in roots) == list(range(len(items)))
+    for _ in range(5):
+        order = list(range(nchains))
+        g.shuffle(order)
+        ran = [0] * nj
+        arrivals = [0] * nj
+        finished_items = []
+        for c in order:               # each CTA runs a chain, then climbs while it arrives last
+            jb = c
+            while True:
+                assert ran[jb] == 0 and arrivals[jb] == J[jb][2]
+                ran[jb] += 1
+                parent = J[jb][1]
+                if parent < 0:
+                    finished_items.append(J[jb][0])
+                    break
+                arrivals[parent] += 1
+                if arrivals[parent] < J[parent][2]:
+                    break
+                jb = parent
+        assert ran == [1] * nj
+        assert sorted(finished_items) == list(range(len(items)))

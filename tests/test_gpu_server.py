@@ -201,3 +201,53 @@ def test_served_mixed_and_auto_match_oracle(cuda_lib, prec_name):
         assert np.array_equal(Xs, to_host(Xa)), f"request {i}: served != alone"
         err = rel(Xs, oracle.lstsq(A, B))
         assert err <= 1e-10, f"request {i} (m={A.shape[0]}, n={A.shape[1]}, k={B.shape[1]}): {err:.2e}"
+
+
+def test_server_survives_a_failed_batch_allocation(cuda_lib):
+    """Host-side failure injection (no GPU fault): the library's next device allocation
+    fails as if the device were out of memory. The batch that hits it reports
+    TSQR_ERR_OOM for each of its requests, nothing is left in flight, and the server goes
+    on serving: every other request completes and equals the request solved alone."""
+    import paper_0912_2572_gb300 as ts
+    lib = cuda_lib
+    reqs = requests(12, 6, mhi=5000, ns=(16, 32))
+    dev = [({"A": to_dev(A), **({"B": to_dev(B)} if B is not None else {})}) for A, B in reqs]
+    outs = {}
+    try:
+        assert lib.tsqr_debug_fail_allocations(1) == 0
+        with ts.Server(max_batch=4, streams=1, chain_tiles=8) as srv:
+            for i, it in enumerate(dev):
+                t, out = srv.submit(it)
+                outs[t] = (i, out)
+            srv.drain()
+            done = srv.poll()
+            stats = srv.stats()
+    finally:
+        lib.tsqr_debug_fail_allocations(0)
+    assert len(done) == len(reqs) and stats["bytes_in_flight"] == 0
+    st = {t: s for t, _, s in done}
+    assert set(st.values()) <= {0, 2} and 1 <= list(st.values()).count(2) <= 4
+    assert list(st.values()).count(0) >= len(reqs) - 4
+    for t, (i, (R, X)) in outs.items():
+        if st[t] != 0:
+            continue
+        A, B = reqs[i]
+        R1, X1 = alone(A, B)
+        assert np.array_equal(to_host(R), R1)
+        if B is not None:
+            assert np.array_equal(to_host(X), X1)
+
+
+def test_admission_follows_live_free_memory(cuda_lib):
+    """Without a budget the server admits by the device memory free at admission time:
+    its stats report that figure (positive, at most the device's memory)."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    reqs = requests(4, 8, mhi=3000, ns=(16,))
+    with ts.Server(max_batch=8, streams=2) as srv:
+        for A, B in reqs:
+            srv.submit({"A": to_dev(A), **({"B": to_dev(B)} if B is not None else {})})
+        srv.drain()
+        stats = srv.stats()
+    total = torch.cuda.get_device_properties(0).total_memory
+    assert 0 < stats["budget_bytes"] <= total
