@@ -108,6 +108,9 @@ def parse(argv=None):
     p.add_argument("--batch-count", type=int, default=10000)
     p.add_argument("--no-serve", action="store_true", help="skip the served least-squares workload")
     p.add_argument("--serve-only", action="store_true", help="run only the served least-squares workload")
+    p.add_argument("--wy-min-n", type=int, default=-1,
+                   help="mixed items with at least this many columns use the compact-WY 3xTF32 leaf (0: never; "
+                        "-1: the library default)")
     p.add_argument("--profile-batch", type=int, default=0, metavar="N",
                    help="only run N mixed batches of 32 served-mix requests (a small case for ncu)")
     return p.parse_args(argv)
@@ -830,6 +833,8 @@ def bench_ours(args):
         tsbuild.build()
     if world > 1:
         dist.barrier()
+    if args.wy_min_n >= 0:
+        ts.set_mixed_wy_min_n(args.wy_min_n)
     if args.serve_only:
         if rank == 0:
             print(json.dumps({"served": bench_served(ts)}), flush=True)
@@ -880,46 +885,7 @@ def bench_ours(args):
     info.free()
     torch.cuda.synchronize()
 
-    # --- timed region: K steps, CUDA events on the launching stream, launch profile live
     stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        def timed():
-            ev0.record(stream)
-            for _ in range(args.steps):
-                run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
-            ev1.record(stream)
-            torch.cuda.synchronize()
-        _, prof = ts.profile_collect(timed)
-    if world > 1:
-        dist.barrier()
-    t_ms = ev0.elapsed_time(ev1)
-    t_max = rank_max(t_ms, world, "cuda")
-    value = whole_job_rate(fl_step * args.steps, world, t_max) / 1e9
-
-    # --- per-phase times from the launch profile
-    phase_ms = {}
-    for kind, ms in prof:
-        phase_ms[kind] = phase_ms.get(kind, 0.0) + ms
-    chain = [ms for kind, ms in prof if kind == "factor_chains"]
-    chain_ms = sum(chain) / max(1, len(chain))
-    # chain launch algorithmic flops: every chain is a Householder QR of its own rows
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    if two:
-        n_chains = min(plan["leaves"], sms * plan["ctas_per_sm"] * 4)
-    else:
-        n_chains = 1 if args.arity == 0 else plan["leaves"]
-    chain_flops = 2.0 * m * n * n - n_chains * 2.0 * n ** 3 / 3.0
-    achieved = chain_flops / (chain_ms * 1e-3) / 1e12
-    clocks = clk.summary()
-    peak_derived = sms * FP64_SM_FLOPS_PER_CLK * 2.070e9 / 1e12
-    peak_measured, probe_mhz = ts.probe_fp64_peak(clock=True)  # after the timed region
-    peak = peak_measured if peak_measured > 0 else peak_derived
-    factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
-
     # --- end to end through the library's host-buffer call (tsqr_qr_solve_host): every
     # step copies A and b from pinned host memory to the device, runs the whole path, and
     # copies Q, R and x back, all inside the timed region. Steps rotate over E2E_SLOTS
@@ -971,6 +937,7 @@ def bench_ours(args):
                "clocks": e2e_clk.summary()}
         last = slots[(args.e2e_steps - 1) % E2E_SLOTS]
         xe = last["xh"].numpy()[:, 0]
+        run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
         xd = x.cpu().numpy()[:, 0]
         e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
         e2e["status"] = int(last["st"][0])
@@ -987,6 +954,47 @@ def bench_ours(args):
         e2e["copy_gbs"] = {"h2d": 8.0 * m * n / (c0.elapsed_time(c1) * 1e-3) / 1e9,
                            "d2h": 8.0 * m * n / (c1.elapsed_time(c2) * 1e-3) / 1e9}
         del Ah, slots, Qd, Ad2
+
+    # --- timed region: K steps, CUDA events on the launching stream, launch profile live
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        def timed():
+            ev0.record(stream)
+            for _ in range(args.steps):
+                run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        _, prof = ts.profile_collect(timed)
+    if world > 1:
+        dist.barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = rank_max(t_ms, world, "cuda")
+    value = whole_job_rate(fl_step * args.steps, world, t_max) / 1e9
+
+    # --- per-phase times from the launch profile
+    phase_ms = {}
+    for kind, ms in prof:
+        phase_ms[kind] = phase_ms.get(kind, 0.0) + ms
+    chain = [ms for kind, ms in prof if kind == "factor_chains"]
+    chain_ms = sum(chain) / max(1, len(chain))
+    # chain launch algorithmic flops: every chain is a Householder QR of its own rows
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if two:
+        n_chains = min(plan["leaves"], sms * plan["ctas_per_sm"] * 4)
+    else:
+        n_chains = 1 if args.arity == 0 else plan["leaves"]
+    chain_flops = 2.0 * m * n * n - n_chains * 2.0 * n ** 3 / 3.0
+    achieved = chain_flops / (chain_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    peak_derived = sms * FP64_SM_FLOPS_PER_CLK * 2.070e9 / 1e12
+    peak_measured, probe_mhz = ts.probe_fp64_peak(clock=True)  # after the timed region
+    dmma_tflops, dmma_mhz = ts.probe_dmma_peak(clock=True)      # FP64 tensor cores, for comparison
+    peak = peak_measured if peak_measured > 0 else peak_derived
+    factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
 
     # the library's factorization autotuner on the same matrix (leaf height x arity x tree
     # form, factor only); reported beside the headline's fixed configuration
@@ -1041,7 +1049,11 @@ def bench_ours(args):
                                       f"on every SM): {peak_measured:.3f} TFLOP/s at {probe_mhz:.0f} MHz; derived {sms} SMs x "
                                       f"{FP64_SM_FLOPS_PER_CLK} flop/clk x 2.07 GHz = {peak_derived:.3f}; the "
                                       "measured-peaks file has no FP64 entry",
-                         "frac_of_derived": achieved / peak_derived},
+                         "frac_of_derived": achieved / peak_derived,
+                         "fp64_tensor_tflops_measured": dmma_tflops,
+                         "fp64_tensor_note": f"DMMA (mma.sync m8n8k4 FP64, tsqr_probe_dmma_peak): {dmma_tflops:.3f} "
+                                             f"TFLOP/s at {dmma_mhz:.0f} MHz against the FMA pipe's "
+                                             f"{peak_measured:.3f}: the FP64 path stays on the FMA pipe"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(prof), "clocks": clocks,
             "factor_autotune": tuned, "config2": config2, "caqr": caqr, "mixed_lsq": mixed,
             "block_orth": block_orth, "batched": batched,

@@ -482,6 +482,19 @@ tsqr_status tsqr_server_stats(tsqr_server *srv, int64_t *out);
 tsqr_status tsqr_server_destroy(tsqr_server *srv);
 
 /*
+ * tsqr_set_mixed_wy_min_n — the FP32 leaf chains of mixed-precision items (tsqr_lstsq with
+ * TSQR_MIXED, batch and server items) with at least `min_n` columns (and more than 16)
+ * are factored in panels of 16 columns whose 16 reflectors are applied to the trailing
+ * columns at once in compact-WY form, I - V T V^T (paper §2.2's blocked Householder
+ * update), with V^T C and V (T^T W) on the tensor cores as 3xTF32 products (FP32 operands
+ * split into two TF32 parts, FP32 accumulation); narrower items, and every item when
+ * min_n = 0, keep the unblocked FP32 register-tile chains. R agrees with the unblocked
+ * chains to FP32 rounding; refined solutions meet the same 1e-10. Process-wide, for
+ * batches planned after the call; returns the previous value. No error.
+ */
+int32_t tsqr_set_mixed_wy_min_n(int32_t min_n);
+
+/*
  * tsqr_debug_fail_allocations — failure injection for tests: the next `count` device
  * allocations the library makes fail as if the device were out of memory (the calls
  * return TSQR_ERR_OOM; a server batch whose workspace allocation fails reports
@@ -520,6 +533,14 @@ tsqr_status tsqr_profile_stop(int64_t max_records, int32_t *kind, float *ms, int
  * kernels' roofline denominator; synchronizes the stream. No paper counterpart.
  */
 tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz);
+
+/*
+ * tsqr_probe_dmma_peak — the same measurement for the FP64 tensor cores (DMMA: independent
+ * mma.sync m8n8k4 FP64 accumulator chains in every warp of every SM). The evidence for
+ * running the FP64 factorization on the FMA pipe: on GB300 the FP64 tensor rate is no
+ * higher than the FP64 FMA rate. Synchronizes the stream. No paper counterpart.
+ */
+tsqr_status tsqr_probe_dmma_peak(void *stream, double *tflops, double *sm_mhz);
 
 /*
  * tsqr_error_word — reads and clears the current device's error word after waiting for

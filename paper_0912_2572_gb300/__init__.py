@@ -19,7 +19,7 @@ from . import _lib
 __all__ = ["FP64", "MIXED", "INPLACE", "TWO_LEVEL", "Factors", "factor", "caqr", "lstsq", "colmajor",
            "TSQRError", "profile_collect", "plan_describe", "batch_solve", "batch_autotune", "factor_autotune",
            "AUTO", "BatchPlan", "Server", "probe_fp64_peak", "orthonormalize", "CLUSTER", "error_word",
-           "qr_solve_host"]
+           "qr_solve_host", "set_mixed_wy_min_n", "probe_dmma_peak"]
 
 FP64 = 0
 MIXED = 1
@@ -459,6 +459,13 @@ def qr_solve_host(A, B=None, Q=None, R=None, X=None, leaf_h: int = 256, arity: i
     return Q, R, X
 
 
+def set_mixed_wy_min_n(min_n: int) -> int:
+    """Mixed-precision items with at least ``min_n`` columns factor their FP32 leaf chains
+    by compact-WY panels with 3xTF32 tensor-core updates (0: never). Returns the previous
+    threshold (tsqr_set_mixed_wy_min_n)."""
+    return _lib.load().tsqr_set_mixed_wy_min_n(int(min_n))
+
+
 def error_word(stream=None) -> int:
     """Reads and clears the device error word (tsqr_error_word; waits for the stream):
     bit 1 = a bounded device wait gave up, bit 2 = an index check of a TSQR_CHECK build."""
@@ -467,6 +474,17 @@ def error_word(stream=None) -> int:
     if st not in (0, 5):
         _lib.check(st, "tsqr_error_word")
     return w.value
+
+
+def probe_dmma_peak(stream=None, clock: bool = False):
+    """Measured burst FP64 tensor-core (DMMA) throughput in TFLOP/s (with ``clock``, also
+    the SM clock in MHz), for comparison with probe_fp64_peak."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    mhz = ctypes.c_double(0.0)
+    _lib.check(lib.tsqr_probe_dmma_peak(_stream(stream), ctypes.byref(out), ctypes.byref(mhz)),
+               "tsqr_probe_dmma_peak")
+    return (out.value, mhz.value) if clock else out.value
 
 
 def profile_collect(fn):

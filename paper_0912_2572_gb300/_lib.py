@@ -52,11 +52,13 @@ SIGNATURES = {
     "tsqr_qr_solve_host": (_i32, [_vp, _i64, _i32, _i64, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
                                   _i32, _i32, _i32, _vp, _vp, _vp]),
     "tsqr_debug_fail_allocations": (_i32, [_i32]),
+    "tsqr_set_mixed_wy_min_n": (_i32, [_i32]),
     "tsqr_batch_describe": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _i64, _i64, _i64,
                                    ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i64]),
     "tsqr_plan_clusters": (_i32, [_i64, _i32, _i32, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.POINTER(_i64),
                                   ctypes.POINTER(_i32), _i64, ctypes.POINTER(_i32), _i64]),
     "tsqr_probe_fp64_peak": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "tsqr_probe_dmma_peak": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "tsqr_batch_plan_create": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "tsqr_batch_plan_run": (_i32, [_vp, _vp]),
     "tsqr_batch_plan_results": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),

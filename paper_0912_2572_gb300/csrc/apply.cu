@@ -19,6 +19,7 @@
 //     diag(sign(r_jj)) and each node's Q blocks are triangular), so reflector j only
 //     touches columns >= j and forming Q costs as many flops as the factorization, not
 //     twice as many.
+#include "cluster_sync.cuh"
 #include "tsqr_internal.h"
 #include "warp_reduce.cuh"
 
@@ -462,6 +463,165 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(const ApplyPa
   }
 }
 
+// ------------------------------------------ cluster tier: pipelined tree levels of Q B
+// B <- Q B (and the thin Q) through three binary tree levels in one launch of clusters of
+// kClusterSize CTAs, the mirror of the factorization's cluster tier: the levels run top
+// down, and a node applies its reflectors n-1 .. 0 to [pivot block; tile block] of 16
+// columns. Reflector j touches pivot row j and tile rows 0..j, so after the node's step s
+// (reflector n-1-s) row n-1-s of both blocks is final; a child's step s needs exactly that
+// row of its parent's block (its pivot rows are the parent's pivot rows or tile rows). The
+// copy warp of the child waits for the parent's progress counter and copies the row for the
+// next step from the parent's shared memory (distributed shared memory) while the other
+// warps run the current step. Each block goes to global memory once, from the CTA that
+// finishes it (a block whose rows an in-cluster child takes over is left to that child).
+constexpr int kClusterCols = 16;
+constexpr int kApplyClusterThreads = kTileThreads + 32;
+
+template <int RM>
+__device__ __forceinline__ void apply_node_cluster(const ApplyParamsT<double> &p, const JobDesc job,
+                                                   const ApplyClusterSlot sl, unsigned char *smraw, unsigned *done,
+                                                   int *gave_up) {
+  using R = double;
+  constexpr int KC = kClusterCols, KCP = KC + 1;
+  R *sm = reinterpret_cast<R *>(smraw);
+  const int n = p.n, ldt = n;
+  const int col0 = p.col0 + blockIdx.y * KC;
+  const int kc = min(KC, p.k - (int)blockIdx.y * KC);
+  R *Bt = sm;                     // the tile block: KC columns of n rows
+  R *PC = Bt + (size_t)KC * ldt;  // dot products, then update coefficients
+  R *P = PC + KC;                 // the pivot block, row-major: P[i * KCP + c]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hw = tid >> 4, hl = tid & 15;
+  const bool cw = (warp == kTileThreads / 32);
+  const TileDesc td = p.tiles[job.tile_begin];
+  const int64_t pr = job.piv_row, r0 = td.row0;
+  TSQR_CHECK_OR_SKIP(job.tile_count == 1 && td.kind == TTQRT && td.nrows == n && td.off == 0 && pr >= 0 &&
+                         r0 >= 0 && (p.rows == 0 || (pr + n <= p.rows && r0 + n <= p.rows)) && td.refl >= 0 &&
+                         (p.nrefl == 0 || td.refl + n <= p.nrefl) && sl.parent >= -1 &&
+                         sl.parent < kClusterSize && kc >= 1,
+                     p.err)
+  auto bp = [&](int64_t row, int c) -> R * { return p.B + row + (int64_t)(col0 + c) * p.ldb; };
+  const uint32_t a_done = smem_u32(done), a_P = smem_u32(P), a_T = smem_u32(Bt);
+  // the copy warp: row `row` of the parent's block, final once the parent has finished its
+  // step n - 1 - row
+  auto fetch_row = [&](int row) {
+    if (!*gave_up) {
+      const uint32_t a = cluster_map(a_done, sl.parent);
+      uint32_t it = 0;
+      while (ld_acquire_cluster_u32(a) < (uint32_t)(n - row)) {
+        if (++it > kClusterSpinLimit) {
+          if (lane == 0) atomicOr(p.err, kErrTimeout);
+          *gave_up = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __syncwarp();
+    for (int c = lane; c < kc; c += 32) {
+      const uint32_t src = sl.side == 0 ? a_P + (uint32_t)(sizeof(R) * (row * KCP + c))
+                                        : a_T + (uint32_t)(sizeof(R) * ((size_t)c * ldt + row));
+      P[row * KCP + c] = ld_cluster_f64(cluster_map(src, sl.parent));
+    }
+  };
+
+  // the tile block starts at B's rows (zero when forming Q); the pivot block is complete in
+  // global memory when the parent ran in an earlier launch, else it arrives row by row
+  for (int c = warp; c < kc; c += kApplyClusterThreads / 32)
+    for (int i = lane; i < n; i += 32) Bt[(size_t)c * ldt + i] = p.formq ? R(0) : *bp(r0 + i, c);
+  if (sl.parent < 0) {
+    for (int e = tid; e < n * kc; e += kApplyClusterThreads) {
+      const int i = e % n, c = e / n;
+      P[i * KCP + c] = __ldcg(bp(pr + i, c));
+    }
+  } else if (cw) {
+    fetch_row(n - 1);
+  }
+  const R *Vt = p.V + r0;
+  R xv[RM], xn[RM];
+  R tau = R(0), sc = R(0), tau_n = R(0), sc_n = R(0);
+  if (warp == 0) {
+    tau = __ldg(p.tau + td.refl + n - 1);
+    sc = __ldg(p.scl + td.refl + n - 1);
+  }
+#pragma unroll
+  for (int r = 0; r < RM; ++r) {
+    const int i = hl + 16 * r;
+    xv[r] = (!cw && i < n) ? __ldg(Vt + i + (int64_t)(n - 1) * p.ldv) : R(0);
+  }
+  __syncthreads();
+
+  for (int s = 0; s < n; ++s) {
+    const int j = n - 1 - s, jn = j - 1;
+    const bool more = (s + 1 < n);
+    const int lo = 0, hi = j + 1;  // reflector j's tail: tile rows 0..j
+    const int cs = p.formq ? max(0, j - col0) : 0;
+    if (cw) {
+      if (more && sl.parent >= 0) fetch_row(jn);
+    } else if (more) {
+      if (warp == 0) {
+        tau_n = __ldg(p.tau + td.refl + jn);
+        sc_n = __ldg(p.scl + td.refl + jn);
+      }
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        const int i = hl + 16 * r;
+        xn[r] = (i <= jn) ? __ldg(Vt + i + (int64_t)jn * p.ldv) : R(0);
+      }
+    }
+    const int rw = (warp + s) & 7;
+    const int hr = 2 * rw + (hw & 1);
+    if (cs < kc) {
+      if (!cw) dots_dispatch<1, RM, R>(Bt, ldt, cs, kc, lo, hi, hr, hl, rw, xv, PC);
+      __syncthreads();
+      if (warp == 0) {
+        const R ts = tau * sc;
+        for (int c = cs + lane; c < kc; c += 32) {
+          const R piv = P[j * KCP + c];
+          const R w = fma(sc, PC[c], piv);
+          PC[c] = ts * w;
+          P[j * KCP + c] = fma(-tau, w, piv);
+        }
+      }
+      __syncthreads();
+      if (!cw) update_dispatch<1, RM, R>(Bt, ldt, cs, kc, lo, hi, hr, hl, rw, xv, PC);
+    }
+    if (!cw) {
+#pragma unroll
+      for (int r = 0; r < RM; ++r) xv[r] = xn[r];
+      tau = tau_n;
+      sc = sc_n;
+    }
+    __syncthreads();
+    if (tid == 0) st_release_cluster_u32(a_done, (uint32_t)(s + 1));
+  }
+  // each block to global memory unless an in-cluster child takes its rows over
+  if (!(sl.kids & 1))
+    for (int e = tid; e < n * kc; e += kApplyClusterThreads) {
+      const int i = e % n, c = e / n;
+      *bp(pr + i, c) = P[i * KCP + c];
+    }
+  if (!(sl.kids & 2))
+    for (int c = warp; c < kc; c += kApplyClusterThreads / 32)
+      for (int i = lane; i < n; i += 32) *bp(r0 + i, c) = Bt[(size_t)c * ldt + i];
+}
+
+template <int RM>
+__global__ void __launch_bounds__(kApplyClusterThreads, 2)
+    k_apply_cluster(const ApplyParamsT<double> p, const ApplyClusterSlot *__restrict__ slots) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned s_done;
+  __shared__ int s_gave_up;
+  const ApplyClusterSlot sl = slots[blockIdx.x];
+  if (threadIdx.x == 0) {
+    s_done = 0;
+    s_gave_up = 0;
+  }
+  cluster_barrier();  // every counter is initialised before any child polls it
+  if (sl.job >= 0) apply_node_cluster<RM>(p, p.jobs[sl.job], sl, smraw, &s_done, &s_gave_up);
+  cluster_barrier();  // no CTA leaves while a child may still read its shared memory
+}
+
 template <int CMAX, int RM, typename R, int MINB>
 cudaError_t launch_tile_t(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   constexpr int KC = 16 * CMAX;
@@ -524,7 +684,39 @@ cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_s
   return launch_tile_rm<4, R>(p, njobs, ctas_per_sm, s);
 }
 
+template <int RM>
+cudaError_t launch_cluster_rm(const ApplyParamsT<double> &p, const ApplyClusterSlot *slots, int nclusters,
+                              cudaStream_t s) {
+  const size_t bytes = apply_cluster_smem_bytes(p.n);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_cluster<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nclusters * kClusterSize), (unsigned)((p.k + kClusterCols - 1) / kClusterCols));
+  cfg.blockDim = dim3(kApplyClusterThreads);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterSize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_apply_cluster<RM>, p, slots);
+}
+
 }  // namespace
+
+size_t apply_cluster_smem_bytes(int n) {
+  return sizeof(double) * ((size_t)kClusterCols * n + kClusterCols + (size_t)n * (kClusterCols + 1));
+}
+
+cudaError_t launch_apply_cluster(const ApplyParamsT<double> &p, const ApplyClusterSlot *slots, int nclusters,
+                                 cudaStream_t s) {
+  if (nclusters <= 0 || p.k <= 0) return cudaSuccess;
+  if (p.n <= 128) return launch_cluster_rm<8>(p, slots, nclusters, s);
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm,
                          int cols_per_cta) {

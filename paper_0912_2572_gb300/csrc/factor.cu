@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "cluster_sync.cuh"
 #include "tsqr_internal.h"
 #include "warp_reduce.cuh"
 
@@ -610,6 +611,333 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
   __syncthreads();
 }
 
+// ------------------------------------ FP32 chains: compact-WY panels on tensor cores
+// The same chain job as run_job_f32r (same register tile, same reflector storage and R),
+// blocked: the columns are factored in panels of 16 (one register slot), each column step
+// touching only the panel's columns, and the panel's 16 reflectors are then applied to the
+// trailing columns at once in compact-WY form (paper §2.2: the blocked Householder update):
+//   Q_panel = H_c0 ... H_c0+15 = I - V T V^T,   C <- Q_panel^T C = C - V (T^T (V^T C)),
+// T upper triangular from the forward recurrence T[0:j, j] = -tau_j T[0:j, 0:j] (V^T v_j)[0:j].
+// V^T C and V (T^T W) are dense contractions and run on the tensor cores as 3xTF32
+// (mma.sync m16n8k8, every FP32 operand split as hi + lo with hi = tf32(x),
+// lo = tf32(x - hi); products hi*hi + hi*lo + lo*hi accumulated in FP32, which keeps FP32
+// accuracy; Ootomo & Yokota 2022). The trailing columns pass through shared memory in
+// chunks of 32 (two register slots) for the products.
+// For a leaf tile (GEQRT) v_j is 1 at tile row j and zero above; for a triangle-on-tile
+// step (TSQRT) v_j is 1 at pivot row j of the chain's R (shared memory) and scale_j times
+// the tile's column j below, so V^T C gains R's pivot rows and R's rows take -T^T W.
+constexpr int kWyPanel = 16;
+constexpr int kWyChunk = 32;
+constexpr int kWyLd = kF32TileRows + 4;  // column stride of V and of a chunk (bank spread)
+constexpr int kWyLdT = kWyPanel + 4;     // row stride of V^T and column stride of W'
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+// d += a b for one m16n8k8 TF32 tile (a: 16x8 row-major fragment, b: 8x8 column-major)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// 3xTF32: d += a b from FP32 fragments (the small cross terms first)
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tf32_split(a[q], ah[q], al[q]);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) tf32_split(b[q], bh[q], bl[q]);
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+template <int CPT>
+__device__ __forceinline__ void run_job_f32wy(const FactorParamsT<float> &p, const JobDesc job, unsigned char *smraw) {
+  float *sm = reinterpret_cast<float *>(smraw);
+  const int n = p.n, nc = p.nc;
+  const int ncp = (nc + 7) & ~7;
+  float *xcol = sm;
+  float *PC = xcol + kF32TileRows;
+  float *PVb = PC + ncp;
+  const int ldr = ncp + 1;
+  float *Rs = PVb + 2 * ncp;              // R(i, c) at Rs[i * ldr + c]
+  float *VS = Rs + (size_t)n * ldr;       // V, column q at VS[q * kWyLd + i]
+  float *VT = VS + kWyPanel * kWyLd;      // V again, row-major: VT[i * kWyLdT + q]
+  float *CT = VT + kF32TileRows * kWyLdT; // a chunk of trailing columns, CT[c * kWyLd + i]
+  float *WP = CT + kWyChunk * kWyLd;      // two partial V^T C (K halves), WP[h][c * 16 + q]
+  float *WT = WP + 2 * kWyPanel * kWyChunk;  // W' = T^T W, WT[c * kWyLdT + q]
+  float *GG = WT + kWyChunk * kWyLdT;     // G = V^T V, GG[a * 17 + b]
+  float *TT = GG + kWyPanel * (kWyPanel + 1);  // T, TT[i * 17 + j]
+  float *TAU = TT + kWyPanel * (kWyPanel + 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hw = tid >> 4, hl = tid & 15;
+  const int g = lane >> 2, tg = lane & 3;  // mma fragment coordinates
+  const int64_t pr = job.piv_row;
+  float v[CPT][kF32Rpt];
+
+  for (int tt = 0; tt < job.tile_count; ++tt) {
+    const TileDesc td = p.tiles[job.tile_begin + tt];
+    const int ht = td.nrows;
+    const int64_t r0 = td.row0;
+    const bool ge = (td.kind == GEQRT);
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = hw + 16 * t;
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        const int i = hl + 16 * r;
+        float val = 0.f;
+        if (c < nc && i < ht)
+          val = (c < n) ? (float)__ldg(p.A + r0 + i + (int64_t)c * p.lda)
+                        : __ldcg(p.B + r0 + i + (int64_t)(c - n) * p.ldb);
+        v[t][r] = val;
+      }
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int pp = 0; pp < CPT; ++pp) {  // panel pp = columns 16 pp .. 16 pp + 15 (register slot pp)
+      const int c0 = kWyPanel * pp;
+      if (c0 >= n) break;
+      const int pend = min(n, c0 + kWyPanel);
+      // ---- the panel's column steps (only the panel's columns are touched)
+      for (int j = c0; j < pend; ++j) {
+        const int jl = j & 15;
+        float *PV = ge ? PVb + (j & 1) * ncp : Rs + j * ldr;
+        if (hw == jl)
+#pragma unroll
+          for (int r = 0; r < kF32Rpt; ++r) xcol[hl + 16 * r] = v[pp][r];
+        if (ge && hl == jl) {  // pivot row j (= tile row j) of the panel's columns
+          const int c = hw + c0;
+#pragma unroll
+          for (int r = 0; r < kF32Rpt; ++r)
+            if (r == pp && c >= j && c < pend) PV[c] = v[pp][r];
+        }
+        __syncthreads();
+        float x[kF32Rpt];
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r) {
+          const int i = hl + 16 * r;
+          x[r] = (ge && i <= j) ? 0.f : xcol[i];
+        }
+        {  // Gram row over the panel (column c = c0 + hw; c == j gives the tail's squared norm)
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < kF32Rpt; ++r) acc = fmaf(x[r], v[pp][r], acc);
+#pragma unroll
+          for (int o = 8; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+          const int c = c0 + hw;
+          if (hl == 0 && c >= j && c < pend) PC[c] = acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          const Refl<float> rf = reflector<float>(PV[j], PC[j]);
+          __syncwarp();  // every lane has read PC[j] before lane 0 replaces it
+          const int c = j + 1 + lane;
+          if (c < pend) {
+            const float pk = PV[c];
+            const float w = fmaf(rf.scale, PC[c], pk);
+            PC[c] = rf.ts * w;
+            PV[c] = fmaf(-rf.tau, w, pk);
+          }
+          if (lane == 0) {
+            PV[j] = rf.beta;
+            p.tau[td.refl + j] = rf.tau;
+            p.scl[td.refl + j] = rf.scale;
+            TAU[j - c0] = rf.tau;
+            PC[j] = rf.scale;  // kept for V's scaling below
+          }
+        }
+        __syncthreads();
+        {
+          const int c = c0 + hw;
+          if (c > j && c < pend) {
+            const float cf = PC[c];
+#pragma unroll
+            for (int r = 0; r < kF32Rpt; ++r) v[pp][r] = fmaf(-cf, x[r], v[pp][r]);
+          }
+          if (ge && hl == jl && c >= j && c < pend)
+#pragma unroll
+            for (int r = 0; r < kF32Rpt; ++r)
+              if (r == (j >> 4)) v[pp][r] = PV[c];
+        }
+      }
+      if (pend >= nc) continue;  // no trailing columns
+      __syncthreads();
+      // ---- V (scaled reflectors) in both layouts, then G = V^T V and T
+      {
+        const int q = hw, c = c0 + hw;
+        const float sc = (c < pend) ? PC[c] : 0.f;
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r) {
+          const int i = hl + 16 * r;
+          float val;
+          if (c >= pend)
+            val = 0.f;
+          else if (ge)
+            val = (i < c) ? 0.f : (i == c ? 1.f : sc * v[pp][r]);
+          else
+            val = sc * v[pp][r];
+          VS[q * kWyLd + i] = val;
+          VT[i * kWyLdT + q] = val;
+        }
+      }
+      __syncthreads();
+      {  // G[a][b] = v_a . v_b (the TSQRT unit pivots add the identity)
+        const int a = tid >> 4, b = tid & 15;
+        float acc = (!ge && a == b) ? 1.f : 0.f;
+        for (int i = 0; i < kF32TileRows; ++i) acc = fmaf(VS[a * kWyLd + i], VS[b * kWyLd + i], acc);
+        GG[a * 17 + b] = acc;
+      }
+      __syncthreads();
+      if (tid < kWyPanel) {  // T column by column; thread i owns row i and reads only it
+        const int i = tid, nb = pend - c0;
+        for (int j = 0; j < kWyPanel; ++j) {
+          float tv = 0.f;
+          if (j < nb) {
+            if (i == j) {
+              tv = TAU[j];
+            } else if (i < j) {
+              float s2 = 0.f;
+              for (int l = i; l < j; ++l) s2 = fmaf(TT[i * 17 + l], GG[l * 17 + j], s2);
+              tv = -TAU[j] * s2;
+            }
+          }
+          TT[i * 17 + j] = tv;
+        }
+      }
+      __syncthreads();
+      // ---- the trailing columns, two register slots (32 columns) at a time
+#pragma unroll
+      for (int ts = 0; ts < CPT; ts += 2) {
+        if (ts + 1 <= pp) continue;          // chunk entirely inside the factored columns
+        const int cb = 16 * ts;              // first column of the chunk
+        // stage: slots ts and ts + 1 (columns not past the panel are zeroed: V^T C of them
+        // is not needed and they must stay unchanged)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int t = ts + u;
+          if (t >= CPT) continue;
+          const int c = hw + 16 * t;
+#pragma unroll
+          for (int r = 0; r < kF32Rpt; ++r)
+            CT[(16 * u + hw) * kWyLd + hl + 16 * r] = (c >= pend && c < nc) ? v[t][r] : 0.f;
+        }
+        __syncthreads();
+        {  // V^T C: warp w takes columns 8 (w & 3) .. + 7 and rows 64 (w >> 2) .. + 63
+          const int nb = 8 * (warp & 3), kh = warp >> 2;
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+          for (int kk = 0; kk < 8; ++kk) {
+            const int kb = 64 * kh + 8 * kk;
+            const float a[4] = {VS[g * kWyLd + kb + tg], VS[(g + 8) * kWyLd + kb + tg], VS[g * kWyLd + kb + tg + 4],
+                                VS[(g + 8) * kWyLd + kb + tg + 4]};
+            const float b[2] = {CT[(nb + g) * kWyLd + kb + tg], CT[(nb + g) * kWyLd + kb + tg + 4]};
+            mma_3xtf32(d, a, b);
+          }
+          float *w = WP + kh * kWyPanel * kWyChunk;
+          w[(nb + 2 * tg) * kWyPanel + g] = d[0];
+          w[(nb + 2 * tg + 1) * kWyPanel + g] = d[1];
+          w[(nb + 2 * tg) * kWyPanel + g + 8] = d[2];
+          w[(nb + 2 * tg + 1) * kWyPanel + g + 8] = d[3];
+        }
+        __syncthreads();
+        // W = the two halves (+ R's pivot rows for a TSQRT tile); W' = T^T W; R's pivot
+        // rows take -W' (the unit pivots of V)
+        for (int e = tid; e < kWyPanel * kWyChunk; e += kThreads) {
+          const int q = e & 15, c = e >> 4;
+          const int col = cb + c;
+          float wsum = 0.f;
+          for (int l = 0; l <= q; ++l) {
+            float wl = WP[c * kWyPanel + l] + WP[kWyPanel * kWyChunk + c * kWyPanel + l];
+            if (!ge && col >= pend && col < nc && c0 + l < pend) wl += Rs[(c0 + l) * ldr + col];
+            wsum = fmaf(TT[l * 17 + q], wl, wsum);
+          }
+          WT[c * kWyLdT + q] = wsum;
+        }
+        __syncthreads();
+        if (!ge)
+          for (int e = tid; e < kWyPanel * kWyChunk; e += kThreads) {
+            const int q = e & 15, c = e >> 4, col = cb + c;
+            if (col >= pend && col < nc && c0 + q < pend) Rs[(c0 + q) * ldr + col] -= WT[c * kWyLdT + q];
+          }
+        {  // C -= V W': warp w takes rows 16 w .. 16 w + 15, all 32 columns
+          const int mb = 16 * warp;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const int nb = 8 * nt;
+            float d[4] = {CT[(nb + 2 * tg) * kWyLd + mb + g], CT[(nb + 2 * tg + 1) * kWyLd + mb + g],
+                          CT[(nb + 2 * tg) * kWyLd + mb + g + 8], CT[(nb + 2 * tg + 1) * kWyLd + mb + g + 8]};
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const int kb = 8 * kk;
+              const float a[4] = {-VT[(mb + g) * kWyLdT + kb + tg], -VT[(mb + g + 8) * kWyLdT + kb + tg],
+                                  -VT[(mb + g) * kWyLdT + kb + tg + 4], -VT[(mb + g + 8) * kWyLdT + kb + tg + 4]};
+              const float b[2] = {WT[(nb + g) * kWyLdT + kb + tg], WT[(nb + g) * kWyLdT + kb + tg + 4]};
+              mma_3xtf32(d, a, b);
+            }
+            CT[(nb + 2 * tg) * kWyLd + mb + g] = d[0];
+            CT[(nb + 2 * tg + 1) * kWyLd + mb + g] = d[1];
+            CT[(nb + 2 * tg) * kWyLd + mb + g + 8] = d[2];
+            CT[(nb + 2 * tg + 1) * kWyLd + mb + g + 8] = d[3];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int t = ts + u;
+          if (t >= CPT) continue;
+          const int c = hw + 16 * t;
+          if (c >= pend && c < nc)
+#pragma unroll
+            for (int r = 0; r < kF32Rpt; ++r) v[t][r] = CT[(16 * u + hw) * kWyLd + hl + 16 * r];
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (ge) {
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int c = hw + 16 * t;
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r) {
+          const int i = hl + 16 * r;
+          if (c < nc && i < n && (i <= c || c >= n)) Rs[i * ldr + c] = v[t][r];
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      const int c = hw + 16 * t;
+      if (c >= nc) continue;
+      float *dst = (c < n) ? p.V + r0 + (int64_t)c * p.ldv : p.B + r0 + (int64_t)(c - n) * p.ldb;
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        const int i = hl + 16 * r;
+        if (i < ht) dst[i] = v[t][r];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * nc; e += kThreads) {
+    const int i = e % n, c = e / n;
+    if (i <= c || c >= n) {
+      float *dst = (c < n) ? p.V + pr + i + (int64_t)c * p.ldv : p.B + pr + i + (int64_t)(c - n) * p.ldb;
+      *dst = Rs[i * ldr + c];
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------- cluster tier: pipelined tree levels
 // Three binary levels of the reduction tree in one launch of thread-block clusters of
 // kClusterSize CTAs (the GPU analogue of the paper's hierarchical tree, §2.3 and §3:
@@ -627,40 +955,6 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
 // progress counter, which the child advances with a release store at cluster scope. Every
 // wait is bounded: past the limit the CTA sets the device error word's timeout bit and
 // stops waiting, so the launch always ends.
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, int rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ uint32_t ld_acquire_cluster_u32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-  return v;
-}
-__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_cluster_u32(uint32_t addr, uint32_t v) {
-  asm volatile("st.release.cluster.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ int cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return (int)r;
-}
-
-// polls of a child's progress counter before a wait gives up (each poll sleeps at least
-// 32 ns: above 0.1 s, five orders of magnitude above a combine's column step)
-constexpr uint32_t kClusterSpinLimit = 1u << 22;
 
 // One combine job of the cluster tier (a binary node: one TTQRT tile of n rows), run by
 // the factor kernel's eight warps plus a ninth, the copy warp.
@@ -888,7 +1182,9 @@ __device__ __forceinline__ void finish_instance(const BatchInst &in, int64_t row
   __syncthreads();
 }
 
-template <int CMAX>
+// WY: the build that can run mixed chains by compact-WY panels (run_job_f32wy); the
+// kernel without it keeps its register budget for the other job kinds.
+template <int CMAX, bool WY>
 __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams bp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_job, s_go;
@@ -915,11 +1211,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.n = in.n;
         fp.nc = in.n;
         fp.ldt = in.ldt;
-        switch (in.n <= 16 ? 1 : (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8))) {
-          case 1: run_job_f32r<1>(fp, jd, smraw); break;
-          case 2: if (CMAX >= 2) run_job_f32r<(CMAX >= 2 ? 2 : 1)>(fp, jd, smraw); break;
-          case 4: if (CMAX >= 4) run_job_f32r<(CMAX >= 4 ? 4 : 1)>(fp, jd, smraw); break;
-          default: if (CMAX >= 8) run_job_f32r<(CMAX >= 8 ? 8 : 1)>(fp, jd, smraw); break;
+        if (WY && in.wy) {  // compact-WY panels, 3xTF32 tensor-core trailing updates
+          switch (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8)) {
+            case 2: if constexpr (WY && CMAX >= 2) run_job_f32wy<2>(fp, jd, smraw); break;
+            case 4: if constexpr (WY && CMAX >= 4) run_job_f32wy<4>(fp, jd, smraw); break;
+            default: if constexpr (WY && CMAX >= 8) run_job_f32wy<8>(fp, jd, smraw); break;
+          }
+        } else {
+          switch (in.n <= 16 ? 1 : (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8))) {
+            case 1: run_job_f32r<1>(fp, jd, smraw); break;
+            case 2: if (CMAX >= 2) run_job_f32r<(CMAX >= 2 ? 2 : 1)>(fp, jd, smraw); break;
+            case 4: if (CMAX >= 4) run_job_f32r<(CMAX >= 4 ? 4 : 1)>(fp, jd, smraw); break;
+            default: if (CMAX >= 8) run_job_f32r<(CMAX >= 8 ? 8 : 1)>(fp, jd, smraw); break;
+          }
         }
         // hand the chain's triangle to the FP64 tree storage
         const float *Vs = static_cast<const float *>(in.V) + bj.piv_row;
@@ -1014,6 +1318,12 @@ __device__ int32_t g_error_word;
 
 }  // namespace
 
+size_t f32wy_smem_extra_bytes() {
+  return sizeof(float) * ((size_t)kWyPanel * kWyLd + (size_t)kF32TileRows * kWyLdT + (size_t)kWyChunk * kWyLd +
+                          2 * (size_t)kWyPanel * kWyChunk + (size_t)kWyChunk * kWyLdT +
+                          2 * (size_t)kWyPanel * (kWyPanel + 1) + kWyPanel);
+}
+
 size_t cluster_smem_bytes(int n, int nc, size_t optin_per_block) {
   const size_t ncp = (size_t)((nc + 7) & ~7);
   const size_t b = sizeof(double) * ((size_t)nc * n + ncp + (size_t)n * ncp);
@@ -1072,18 +1382,25 @@ cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_
   return launch_factor_any(p, njobs, ctas_per_sm, s);
 }
 
-cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s) {
+cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s,
+                                bool wy) {
   auto go = [&](auto kernel) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     kernel<<<grid, kThreads, smem_bytes, s>>>(p);
     return cudaGetLastError();
   };
-  if (cmax <= 1) return go(k_factor_batch<1>);
-  if (cmax <= 2) return go(k_factor_batch<2>);
-  if (cmax <= 4) return go(k_factor_batch<4>);
-  if (cmax <= 8) return go(k_factor_batch<8>);
-  return go(k_factor_batch<16>);
+  if (wy) {
+    if (cmax <= 2) return go(k_factor_batch<2, true>);
+    if (cmax <= 4) return go(k_factor_batch<4, true>);
+    if (cmax <= 8) return go(k_factor_batch<8, true>);
+    return go(k_factor_batch<16, true>);
+  }
+  if (cmax <= 1) return go(k_factor_batch<1, false>);
+  if (cmax <= 2) return go(k_factor_batch<2, false>);
+  if (cmax <= 4) return go(k_factor_batch<4, false>);
+  if (cmax <= 8) return go(k_factor_batch<8, false>);
+  return go(k_factor_batch<16, false>);
 }
 
 }  // namespace tsqr

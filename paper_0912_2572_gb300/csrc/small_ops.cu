@@ -89,7 +89,46 @@ __global__ void k_dfma_probe(double *out, int iters, double a, double b, unsigne
   out[gid] = sum;
 }
 
+// FP64 tensor-core (DMMA) throughput probe: every warp runs kDmmaChains independent
+// accumulator chains of mma.sync m8n8k4 FP64 (256 FMAs per warp instruction), operands
+// from runtime values. Thread 0 of block 0 records cycles and nanoseconds as above.
+constexpr int kDmmaChains = 4;
+__global__ void k_dmma_probe(double *out, int iters, double a, double b, unsigned long long *clk) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[kDmmaChains][2];
+#pragma unroll
+  for (int u = 0; u < kDmmaChains; ++u) {
+    acc[u][0] = gid * 1e-12 + u;
+    acc[u][1] = gid * 1e-12 - u;
+  }
+  const double fa = a + gid * 1e-15, fb = b - gid * 1e-15;
+  const uint64_t c0 = clock64(), t0 = probe_ns();
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kDmmaChains; ++u)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(acc[u][0]), "+d"(acc[u][1])
+                   : "d"(fa), "d"(fb));
+  }
+  const uint64_t c1 = clock64(), t1 = probe_ns();
+  if (gid == 0) {
+    clk[0] = c1 - c0;
+    clk[1] = t1 - t0;
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int u = 0; u < kDmmaChains; ++u) sum += acc[u][0] + acc[u][1];
+  out[gid] = sum;
+}
+
 }  // namespace
+
+double launch_dmma_probe(double *out, unsigned long long *clk, int sms, int ctas_per_sm, int iters,
+                         cudaStream_t s) {
+  k_dmma_probe<<<sms * ctas_per_sm, 256, 0, s>>>(out, iters, 0.999999, 1e-7, clk);
+  // 8 warps per CTA, each instruction 8 x 8 x 4 FMAs = 512 flops
+  return 512.0 * kDmmaChains * (double)iters * 8.0 * sms * ctas_per_sm;
+}
 
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr, double *d,
                              cudaStream_t s) {

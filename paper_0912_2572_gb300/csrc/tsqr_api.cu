@@ -77,6 +77,10 @@ DeviceInfo device_info(int dev) {
 // fail as if the device were out of memory.
 std::atomic<int32_t> g_fail_allocs{0};
 
+// Mixed-precision items with at least this many columns factor their FP32 chains by
+// compact-WY panels with 3xTF32 tensor-core updates (0: never; tsqr_set_mixed_wy_min_n).
+std::atomic<int32_t> g_wy_min_n{0};
+
 // Stream-ordered allocations come from a memory pool of the library's own, one per device,
 // kept cached so that repeated factorizations do not return memory to the driver. Its
 // blocks freed on one stream are not reused by another stream through an inserted
@@ -193,6 +197,7 @@ struct Plan {
   };
   std::vector<ClusterLaunch> cl_launches;
   std::vector<ClusterSlot> cl_slots;
+  std::vector<ApplyClusterSlot> cl_apply;  // the same slots seen top down (parents), for Q B
   int cl_base = 0;  // tree levels 1..cl_base run one launch each before the cluster launches
   // factorization launches (the chain launch, the per-level tree launches, the cluster launches)
   int factor_launches() const {
@@ -248,6 +253,17 @@ static void plan_clusters(Plan &pl, int64_t max_ctas) {
         }
       }
       pl.cl_slots.insert(pl.cl_slots.end(), sl, sl + kClusterSize);
+      // top down: each in-cluster child's parent and the side of the parent it continues
+      ApplyClusterSlot as[kClusterSize];
+      for (int r = 0; r < kClusterSize; ++r) as[r] = {sl[r].job, -1, 0, 0};
+      for (int r = 0; r < kClusterSize; ++r)
+        for (int q = 0; q < 2; ++q)
+          if (sl[r].job >= 0 && sl[r].child[q] >= 0) {
+            as[sl[r].child[q]].parent = r;
+            as[sl[r].child[q]].side = q;
+            as[r].kids |= 1 << q;
+          }
+      pl.cl_apply.insert(pl.cl_apply.end(), as, as + kClusterSize);
     }
     pl.cl_launches.push_back(cl);
   }
@@ -411,6 +427,7 @@ struct DevPlan {
   JobDesc *jobs = nullptr;
   TileDesc *tiles = nullptr;
   ClusterSlot *slots = nullptr;
+  ApplyClusterSlot *aslots = nullptr;
   int32_t *err = nullptr;  // the device error word
   ~DevPlan() {
     int cur = 0;
@@ -419,6 +436,7 @@ struct DevPlan {
     if (jobs) cudaFree(jobs);
     if (tiles) cudaFree(tiles);
     if (slots) cudaFree(slots);
+    if (aslots) cudaFree(aslots);
     cudaSetDevice(cur);
   }
 };
@@ -459,6 +477,9 @@ static tsqr_status get_plan(int64_t m, int n, int nc, int leaf_h, int arity, int
   if (!pl.cl_slots.empty()) {
     CUDA_TRY(cudaMalloc(&dp->slots, sizeof(ClusterSlot) * pl.cl_slots.size()));
     CUDA_TRY(cudaMemcpy(dp->slots, pl.cl_slots.data(), sizeof(ClusterSlot) * pl.cl_slots.size(),
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&dp->aslots, sizeof(ApplyClusterSlot) * pl.cl_apply.size()));
+    CUDA_TRY(cudaMemcpy(dp->aslots, pl.cl_apply.data(), sizeof(ApplyClusterSlot) * pl.cl_apply.size(),
                         cudaMemcpyHostToDevice));
   }
   CUDA_TRY(device_error_word(&dp->err));
@@ -615,15 +636,55 @@ static int apply_group(int k) { return (k <= 8) ? 8 : 64; }
 // tile small enough for two or three CTAs of four jobs per SM.
 static int formq_group(int n) { return (n <= 32) ? 4 : 64; }
 
+// The cluster launch of F's plan that completes tree level li top down (the launch whose
+// highest level is li), for the columns [c0, c0 + kg) of B.
+static tsqr_status apply_cluster_launch(const tsqr_factors *F, double *B, int64_t ldb, int c0, int kg, int formq,
+                                        const Plan::ClusterLaunch &cl, cudaStream_t s) {
+  const Plan &pl = F->plan();
+  ApplyParams p{};
+  p.V = F->V;
+  p.ldv = F->ldv;
+  p.B = B;
+  p.ldb = ldb;
+  p.jobs = F->dp->jobs;
+  p.tiles = F->dp->tiles;
+  p.tau = F->tau;
+  p.scl = F->scl;
+  p.n = pl.n;
+  p.ldt = pl.n;
+  p.trans = 0;
+  p.formq = formq;
+  p.col0 = c0;
+  p.k = kg;
+  set_bounds(F, p);
+  ProfScope ps(formq ? TSQR_PROF_FORM_Q : TSQR_PROF_APPLY_Q, s);
+  CUDA_TRY(launch_apply_cluster(p, F->dp->aslots + cl.slot_begin, cl.nclusters, s));
+  return TSQR_OK;
+}
+
 static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int k, int trans, int formq,
                              cudaStream_t s) {
-  const int nl = (int)F->plan().launches.size();
+  const Plan &pl = F->plan();
+  const int nl = (int)pl.launches.size();
   const int group = formq ? formq_group(k) : apply_group(k);
-  for (int c0 = 0; c0 < k; c0 += group)
+  // Q B top down with groups of more than 8 columns (the tile kernel's arithmetic, which the
+  // cluster launches share, so results stay bitwise those of the per-level launches): the
+  // levels of the cluster launches run as cluster launches, highest first
+  for (int c0 = 0; c0 < k; c0 += group) {
+    const int kg = std::min(group, k - c0);
+    const bool clustered = !trans && kg > 8 && !pl.cl_launches.empty() && F->dp->aslots;
     for (int q = 0; q < nl; ++q) {
-      tsqr_status st = apply_launch(F, B, ldb, c0, std::min(group, k - c0), trans, formq, trans ? q : nl - 1 - q, s);
+      const int li = trans ? q : nl - 1 - q;
+      tsqr_status st = TSQR_OK;
+      if (clustered && li > pl.cl_base) {
+        for (const Plan::ClusterLaunch &cl : pl.cl_launches)
+          if (cl.level_hi == li) st = apply_cluster_launch(F, B, ldb, c0, kg, formq, cl, s);
+      } else {
+        st = apply_launch(F, B, ldb, c0, kg, trans, formq, li, s);
+      }
       if (st != TSQR_OK) return st;
     }
+  }
   return TSQR_OK;
 }
 
@@ -687,7 +748,8 @@ struct BatchBuild {
   int32_t count = 0;
   std::vector<tsqr_batch_item> items;
   std::vector<Plan> plans;
-  std::vector<int32_t> prec, tree_rows;
+  std::vector<int32_t> prec, tree_rows, wy;
+  bool wy_any = false;
   size_t smem = 0;
   int cmax = 1, grid = 0;
   int32_t nchains = 0, njobs = 0;
@@ -736,6 +798,8 @@ tsqr_status batch_build_on(DeviceInfo di, const tsqr_batch_item *items, int32_t 
   b.plans.resize(count);
   b.prec.resize(count);
   b.tree_rows.resize(count);
+  b.wy.assign(count, 0);
+  const int32_t wy_min = g_wy_min_n.load();
   int cps_min = 2;
   bool any_refine = false;
   for (int32_t q = 0; q < count; ++q) {
@@ -759,7 +823,17 @@ tsqr_status batch_build_on(DeviceInfo di, const tsqr_batch_item *items, int32_t 
     // tree nodes (FP64) in pieces that fit the chains' CTAs per SM
     const int node_rows = b.tree_rows[q] = split_tree_tiles(
         b.plans[q], factor_max_rows(nc, b.plans[q].ctas_per_sm, di.smem_sm, di.reserved, di.optin, sizeof(double)));
-    b.smem = std::max(b.smem, factor_smem_bytes(nc, b.plans[q].tile_h, elem));
+    size_t chain_smem = factor_smem_bytes(nc, b.plans[q].tile_h, elem);
+    if (mixed && wy_min > 0 && it.n >= wy_min && it.n > 16) {
+      // compact-WY FP32 chains, if their buffers still fit two CTAs per SM
+      const size_t wsm = chain_smem + f32wy_smem_extra_bytes();
+      if (wsm <= di.optin && 2 * (wsm + di.reserved) <= di.smem_sm) {
+        chain_smem = wsm;
+        b.wy[q] = 1;
+        b.wy_any = true;
+      }
+    }
+    b.smem = std::max(b.smem, chain_smem);
     b.smem = std::max(b.smem, factor_smem_bytes(nc, node_rows, sizeof(double)));
     b.smem = std::max(b.smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
     while (16 * b.cmax < nc) b.cmax *= 2;
@@ -963,6 +1037,7 @@ void batch_bind(BatchBuild &b, char *base) {
     bi.ldt = pl.tile_h;
     bi.ldt_tree = b.tree_rows[q];
     bi.mixed = pl.mixed ? 1 : 0;
+    bi.wy = b.wy[q];
   }
   int32_t *flags = (int32_t *)(base + b.o_rflags);  // counter, done per instance
   for (size_t r = 0; r < b.rinst.size(); ++r) {
@@ -1020,7 +1095,7 @@ tsqr_status batch_enqueue(const BatchBuild &b, char *base, cudaStream_t s, bool 
   bp.nchains = b.nchains;
   {
     ProfScope ps(profile ? TSQR_PROF_BATCH : -1, s);
-    CUDA_TRY(launch_factor_batch(bp, b.cmax, b.grid, b.smem, s));
+    CUDA_TRY(launch_factor_batch(bp, b.cmax, b.grid, b.smem, s, b.wy_any));
   }
   if (!b.rinst.empty()) {
     RefineParams rp{};
@@ -1250,7 +1325,17 @@ void tsqr::clear_last_error() { g_last_error.clear(); }
 
 extern "C" {
 
+static tsqr_status probe_peak(void *stream, double *tflops, double *sm_mhz, bool dmma);
+
 tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz) {
+  return probe_peak(stream, tflops, sm_mhz, false);
+}
+
+tsqr_status tsqr_probe_dmma_peak(void *stream, double *tflops, double *sm_mhz) {
+  return probe_peak(stream, tflops, sm_mhz, true);
+}
+
+static tsqr_status probe_peak(void *stream, double *tflops, double *sm_mhz, bool dmma) {
   if (!tflops) return fail(TSQR_ERR_ARG, "null output");
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -1273,7 +1358,8 @@ tsqr_status tsqr_probe_fp64_peak(void *stream, double *tflops, double *sm_mhz) {
   const int iters = 1 << 13;
   for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
     e = cudaEventRecord(e0, s);
-    const double fl = launch_dfma_probe(out, clk, di.sms, ctas, iters, s);
+    const double fl = dmma ? launch_dmma_probe(out, clk, di.sms, ctas, iters / 4, s)
+                           : launch_dfma_probe(out, clk, di.sms, ctas, iters, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1311,6 +1397,8 @@ const char *tsqr_strerror(tsqr_status s) {
 }
 
 const char *tsqr_last_error(void) { return g_last_error.c_str(); }
+
+int32_t tsqr_set_mixed_wy_min_n(int32_t min_n) { return g_wy_min_n.exchange(min_n < 0 ? 0 : min_n); }
 
 tsqr_status tsqr_debug_fail_allocations(int32_t count) {
   if (count < 0) return fail(TSQR_ERR_ARG, "count < 0");

@@ -109,6 +109,9 @@ constexpr int kF32TileRows = 16 * kF32Rpt;
 // Shared memory of a factor job: the tile plus its step buffers (FP64), or only the
 // step buffers of a register-tile FP32 chain (elem = 4).
 size_t factor_smem_bytes(int nc, int ldt, size_t elem = sizeof(double));
+// extra shared memory of an FP32 chain job with compact-WY panels (V twice, a chunk of
+// trailing columns, V^T C, T^T W, G and T)
+size_t f32wy_smem_extra_bytes();
 // ctas_per_sm: CTAs per SM the tile height was planned for (3 selects the build that fits
 // three in the register file; anything else, two).
 cudaError_t launch_factor(const FactorParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2);
@@ -143,7 +146,9 @@ struct BatchInst {
   int64_t ldx;
   int32_t *status;  // device flag set to 4 when R is singular (solve only)
   int32_t n, k, ldt, mixed;
-  int32_t ldt_tree, pad;  // shared-memory rows of a tree-node tile (a piece of a triangle)
+  int32_t ldt_tree;  // shared-memory rows of a tree-node tile (a piece of a triangle)
+  int32_t wy;        // mixed items: FP32 chains by compact-WY panels with 3xTF32 tensor-core
+                     // updates (run_job_f32wy) instead of the unblocked register tile
 };
 
 struct BatchJob {   // chain jobs first (queue order), then tree nodes
@@ -163,7 +168,8 @@ struct BatchParams {
   int32_t nchains;
 };
 
-cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_factor_batch(const BatchParams &p, int cmax, int grid, size_t smem_bytes, cudaStream_t s,
+                                bool wy = false);
 
 // ------------------------------------------------------- cluster tier of the tree
 // With TSQR_CLUSTER, three binary tree levels run in one launch of thread-block clusters
@@ -277,6 +283,18 @@ using ApplyParams = ApplyParamsT<double>;
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2,
                          int cols_per_cta = 64);
 
+// Cluster tier of B <- Q B (top down): one CTA per combine of a cluster launch of the
+// factorization's schedule, for 16 columns of B; parent = the cluster rank whose block this
+// node's pivot rows come from (-1: complete in global memory), side 0 = the parent's pivot
+// block, 1 = its tile block; kids bit q = the pivot (0) / tile (1) child is in the cluster.
+struct ApplyClusterSlot {
+  int32_t job;
+  int32_t parent, side, kids;
+};
+size_t apply_cluster_smem_bytes(int n);
+cudaError_t launch_apply_cluster(const ApplyParamsT<double> &p, const ApplyClusterSlot *slots, int nclusters,
+                                 cudaStream_t s);
+
 // ------------------------------------------------------------------- small kernels
 cudaError_t launch_extract_r(const double *V, int64_t ldv, int n, double *R, int64_t ldr,
                              double *d, cudaStream_t s);
@@ -287,6 +305,9 @@ cudaError_t launch_formq_init(double *Q, int64_t ldq, int n, const double *d, cu
 // The FP64 FMA throughput probe (out: one double per thread; clk: cycles and ns of one
 // thread); returns the flops of one launch.
 double launch_dfma_probe(double *out, unsigned long long *clk, int sms, int ctas_per_sm, int iters,
+                         cudaStream_t s);
+// The FP64 tensor-core (DMMA, mma.sync m8n8k4) throughput probe, same outputs.
+double launch_dmma_probe(double *out, unsigned long long *clk, int sms, int ctas_per_sm, int iters,
                          cudaStream_t s);
 
 // X = R^{-1} (D C[0:n]) for the raw upper triangle R (leading dimension ldr) and the

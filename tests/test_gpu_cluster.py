@@ -97,3 +97,32 @@ def test_cluster_tree_overlapped_apply(cuda_lib):
     assert np.array_equal(to_host(F1.R), to_host(F0.R))
     F0.free()
     F1.free()
+
+
+@pytest.mark.parametrize("m,n,k", [(1 << 20, 64, 0), (300_000, 48, 0), (200_000, 32, 24), (60_000, 100, 12)])
+def test_cluster_apply_top_down_bitwise(cuda_lib, m, n, k):
+    """The thin Q (k = 0) and Q B (k > 8 columns) through the cluster tier of the apply (the
+    tree levels run top down in clusters, pipelined through distributed shared memory) are
+    bitwise those of the per-level launches; Q^T (Q B) = B and the thin Q is orthonormal."""
+    import torch
+    import paper_0912_2572_gb300 as ts
+    A = inputs.gaussian(m, n, m % 1000 + n)
+    Ad = to_dev(A)
+    F0 = ts.factor(Ad, leaf_h=144, two_level=True)
+    F1 = ts.factor(Ad, leaf_h=144, two_level=True, cluster=True)
+    if k == 0:
+        Q0, Q1 = to_host(F0.form_q()), to_host(F1.form_q())
+        assert np.array_equal(Q1, Q0)
+        assert np.linalg.norm(Q1.T @ Q1 - np.eye(n)) <= 1e-13
+    else:
+        B = inputs.gaussian(m, k, 7)
+        B0, B1 = to_dev(B), to_dev(B)
+        F0.apply_q(B0)
+        F1.apply_q(B1)
+        assert np.array_equal(to_host(B1), to_host(B0))
+        F1.apply_qt(B1)
+        assert _rel(to_host(B1), B) <= 1e-13
+    F0.free()
+    F1.free()
+    torch.cuda.synchronize()
+    assert ts.error_word() == 0

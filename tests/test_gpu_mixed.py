@@ -99,3 +99,24 @@ def test_mixed_strided_and_many_rhs(cuda_lib):
     ts.lstsq(Abig.t()[:m], Bbig.t()[:m], prec=ts.MIXED, X=X)
     assert rel(to_host(X), oracle.lstsq(A, B)) <= TOL
     assert torch.all(Xbig[:, n:] == 5.0)
+
+
+@pytest.mark.parametrize("m,n,dec,seed", [(20_000, 16, 4, 1), (50_000, 64, 3, 2), (8_000, 128, 2, 3)])
+def test_gpu_refinement_against_oracle_csne(cuda_lib, m, n, dec, seed):
+    """The GPU's refinement is corrected semi-normal equations iterated from x = 0 (Bjorck
+    1987); the oracle runs the same iteration around its own FP32 Householder R. Both
+    must land on the FP64 least-squares solution: the GPU x within 1e-10 of the oracle's
+    CSNE x, each step's correction of the GPU history after the first smaller than the
+    one before until the stop, and the first correction all of x (ratio 1)."""
+    import paper_0912_2572_gb300 as ts
+    A = inputs.graded(m, n, dec, seed_g=40 + seed, seed_v=50 + seed)
+    b, _ = inputs.lstsq_rhs(A, 1, 1e-6, 60 + seed)
+    X, hist = ts.lstsq(to_dev(A), to_dev(b), prec=ts.MIXED, max_refine=10, info=True)
+    xg = to_host(X)[:, 0]
+    xc, hc = oracle.lstsq_refine_csne(A, b[:, 0], max_steps=20, tol=1e-10)
+    xo = oracle.lstsq(A, b[:, 0])
+    assert rel(xc, xo) <= TOL
+    assert rel(xg, xc) <= 2 * TOL
+    h = [v for v in hist if v > 0]
+    assert h[0] == 1.0 and 2 <= len(h) <= 6
+    assert all(h[s + 1] < h[s] for s in range(len(h) - 1))
