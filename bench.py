@@ -885,76 +885,6 @@ def bench_ours(args):
     info.free()
     torch.cuda.synchronize()
 
-    stream = torch.cuda.current_stream()
-    # --- end to end through the library's host-buffer call (tsqr_qr_solve_host): every
-    # step copies A and b from pinned host memory to the device, runs the whole path, and
-    # copies Q, R and x back, all inside the timed region. Steps rotate over E2E_SLOTS
-    # streams; each call's kernels wait (its `after` event) for the previous call's kernels,
-    # so one step's copies overlap the neighbouring steps' kernels.
-    e2e = None
-    if not args.no_e2e:
-        Ah = host_pinned_colmajor(A)
-        bh = host_pinned_colmajor(b)
-        slots = []
-        for q in range(E2E_SLOTS):
-            ev = torch.cuda.Event()
-            ev.record(stream)  # materialise the event handle
-            slots.append({"s": torch.cuda.Stream(), "ev": ev,
-                          "Qh": torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
-                          "Rh": torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
-                          "xh": torch.empty((1, n), dtype=torch.float64, pin_memory=True).t(),
-                          "st": torch.zeros(1, dtype=torch.int32).pin_memory()})
-        torch.cuda.synchronize()
-        done = [None]
-
-        def e2e_step(i):
-            sl = slots[i % E2E_SLOTS]
-            ts.qr_solve_host(Ah, bh, Q=sl["Qh"], R=sl["Rh"], X=sl["xh"], status=sl["st"], leaf_h=leaf_h,
-                             arity=args.arity, two_level=two, cluster=cl, stream=sl["s"], after=done[0],
-                             done=sl["ev"])
-            done[0] = sl["ev"]
-
-        # one untimed pass per stream (each stream's first allocations grow the pool)
-        for i in range(E2E_SLOTS):
-            e2e_step(i)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as e2e_clk:
-            e0.record(stream)
-            for sl in slots:
-                sl["s"].wait_event(e0)
-            for i in range(args.e2e_steps):
-                e2e_step(i)
-            for sl in slots:
-                stream.wait_stream(sl["s"])
-            e1.record(stream)
-            torch.cuda.synchronize()
-        te = rank_max(e0.elapsed_time(e1), world, "cuda")
-        e2e = {"value": whole_job_rate(fl_step * args.e2e_steps, world, te) / 1e9, "unit": "Gflop/s",
-               "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
-               "ms_per_step": te / args.e2e_steps, "pipelined_streams": E2E_SLOTS,
-               "api": "tsqr_qr_solve_host (host buffers, copies inside the call)",
-               "clocks": e2e_clk.summary()}
-        last = slots[(args.e2e_steps - 1) % E2E_SLOTS]
-        xe = last["xh"].numpy()[:, 0]
-        run_step(ts, Ad, bd, b0, Q, x, leaf_h, args.arity, two, cl).free()
-        xd = x.cpu().numpy()[:, 0]
-        e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
-        e2e["status"] = int(last["st"][0])
-        # this box's pinned-copy bandwidth, after the timed region (the e2e figure depends on it)
-        Qd = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
-        Ad2 = torch.empty_like(Ad)
-        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        c0.record(stream)
-        Ad2.copy_(Ah, non_blocking=True)
-        c1.record(stream)
-        last["Qh"].copy_(Qd, non_blocking=True)
-        c2.record(stream)
-        torch.cuda.synchronize()
-        e2e["copy_gbs"] = {"h2d": 8.0 * m * n / (c0.elapsed_time(c1) * 1e-3) / 1e9,
-                           "d2h": 8.0 * m * n / (c1.elapsed_time(c2) * 1e-3) / 1e9}
-        del Ah, slots, Qd, Ad2
-
     # --- timed region: K steps, CUDA events on the launching stream, launch profile live
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -995,6 +925,86 @@ def bench_ours(args):
     dmma_tflops, dmma_mhz = ts.probe_dmma_peak(clock=True)      # FP64 tensor cores, for comparison
     peak = peak_measured if peak_measured > 0 else peak_derived
     factor_ms = (phase_ms.get("factor_chains", 0) + phase_ms.get("factor_tree", 0)) / args.steps
+
+    # --- end to end through the library's host-buffer call (tsqr_qr_solve_host): every
+    # step copies A and b from pinned host memory to the device, runs the whole path, and
+    # copies Q, R and x back, all inside the timed region. Steps rotate over E2E_SLOTS
+    # streams; each call's kernels wait (its `after` event) for the previous call's kernels,
+    # so one step's copies overlap the neighbouring steps' kernels.
+    e2e = None
+    if not args.no_e2e:
+        # the pinned outputs first and the inputs last, right before the loop: on the GB300
+        # box the host-to-device bandwidth from a pinned buffer decays in the seconds after
+        # it was written (210 -> 145 GB/s in 20 s idle, and lower right after other large
+        # pinned allocations), so the copy bandwidth is also measured just before the loop
+        slots = []
+        for q in range(E2E_SLOTS):
+            ev = torch.cuda.Event()
+            ev.record(stream)  # materialise the event handle
+            slots.append({"s": torch.cuda.Stream(), "ev": ev,
+                          "Qh": torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
+                          "Rh": torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
+                          "xh": torch.empty((1, n), dtype=torch.float64, pin_memory=True).t(),
+                          "st": torch.zeros(1, dtype=torch.int32).pin_memory()})
+        torch.cuda.synchronize()
+        Ah = host_pinned_colmajor(A)
+        bh = host_pinned_colmajor(b)
+        probe = torch.empty_like(Ad)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        probe.copy_(Ah, non_blocking=True)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        h2d_before = 8.0 * m * n / (p0.elapsed_time(p1) * 1e-3) / 1e9
+        del probe
+        done = [None]
+
+        def e2e_step(i):
+            sl = slots[i % E2E_SLOTS]
+            ts.qr_solve_host(Ah, bh, Q=sl["Qh"], R=sl["Rh"], X=sl["xh"], status=sl["st"], leaf_h=leaf_h,
+                             arity=args.arity, two_level=two, cluster=cl, stream=sl["s"], after=done[0],
+                             done=sl["ev"])
+            done[0] = sl["ev"]
+
+        # one untimed pass per stream (each stream's first allocations grow the pool)
+        for i in range(E2E_SLOTS):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as e2e_clk:
+            e0.record(stream)
+            for sl in slots:
+                sl["s"].wait_event(e0)
+            for i in range(args.e2e_steps):
+                e2e_step(i)
+            for sl in slots:
+                stream.wait_stream(sl["s"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+        te = rank_max(e0.elapsed_time(e1), world, "cuda")
+        e2e = {"value": whole_job_rate(fl_step * args.e2e_steps, world, te) / 1e9, "unit": "Gflop/s",
+               "h2d_bytes_per_step": 8 * (m * n + m), "d2h_bytes_per_step": 8 * (m * n + n * n + n),
+               "ms_per_step": te / args.e2e_steps, "pipelined_streams": E2E_SLOTS,
+               "api": "tsqr_qr_solve_host (host buffers, copies inside the call)",
+               "clocks": e2e_clk.summary()}
+        last = slots[(args.e2e_steps - 1) % E2E_SLOTS]
+        xe = last["xh"].numpy()[:, 0]
+        xd = x.cpu().numpy()[:, 0]
+        e2e["x_rel_diff_vs_device_run"] = float(np.linalg.norm(xe - xd) / np.linalg.norm(xd))
+        e2e["status"] = int(last["st"][0])
+        # this box's pinned-copy bandwidth, after the timed region (the e2e figure depends on it)
+        Qd = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+        Ad2 = torch.empty_like(Ad)
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        Ad2.copy_(Ah, non_blocking=True)
+        c1.record(stream)
+        last["Qh"].copy_(Qd, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        e2e["copy_gbs"] = {"h2d_before": h2d_before, "h2d": 8.0 * m * n / (c0.elapsed_time(c1) * 1e-3) / 1e9,
+                           "d2h": 8.0 * m * n / (c1.elapsed_time(c2) * 1e-3) / 1e9}
+        del Ah, slots, Qd, Ad2
 
     # the library's factorization autotuner on the same matrix (leaf height x arity x tree
     # form, factor only); reported beside the headline's fixed configuration

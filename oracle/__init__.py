@@ -77,6 +77,7 @@ def _load():
             "oracle_lstsq_refine_csne": (ctypes.c_int, [_i64, _i64, _dp, _i64, _dp, _i32, ctypes.c_double,
                                                         _dp, _dp]),
             "oracle_apply_qt_f32": (None, [_i64, _i64, _fp, _i64, _fp, _fp]),
+            "oracle_r_mixed": (None, [_i64, _i64, _dp, _i64, _i64, _dp, _i64]),
             "oracle_apply_q_f32": (None, [_i64, _i64, _fp, _i64, _fp, _fp]),
         }
         for name, (res, args) in sig.items():
@@ -260,9 +261,23 @@ def lstsq_refine_mixed(A, b, max_steps: int = 10, tol: float = 1e-14):
     return x, r, hist[:steps]
 
 
+def r_mixed(A, h: int = 128):
+    """R (diag >= 0) of the mixed-precision TSQR: FP32 Householder QR of every h-row leaf,
+    FP64 Householder QR of the stacked leaf triangles."""
+    lib = _load()
+    Aw = _f64(A)
+    m, n = Aw.shape
+    R = np.zeros((n, n), order="F")
+    lib.oracle_r_mixed(m, n, _p(Aw), m, max(h, n), _p(R), n)
+    d = np.ones(n)
+    lib.oracle_sign_normalise_r(n, _p(R), n, _p(d))
+    return R
+
+
 def lstsq_refine_csne(A, b, max_steps: int = 10, tol: float = 1e-10):
-    """Corrected semi-normal equations iterated from x = 0 around the R of an FP32
-    Householder QR (Bjorck 1987), with the library's stopping rule.
+    """Corrected semi-normal equations iterated from x = 0 around the R of the
+    mixed-precision TSQR (FP32 leaves of 128 rows, FP64 combine; Bjorck 1987), with the
+    library's stopping rule.
     Returns (x, hist) where hist[s] = ||dx||/||x|| after step s."""
     lib = _load()
     Aw = _f64(A)

@@ -21,9 +21,11 @@
  *   - Mixed-precision least squares: an FP32 Householder QR used inside Bjorck's
  *     augmented-system iterative refinement with FP64 residuals and corrections
  *     (Bjorck 1967; Higham, "Accuracy and Stability of Numerical Algorithms",
- *     §20.5), and Bjorck's corrected semi-normal equations iterated around the R
- *     of the same FP32 QR (Bjorck 1987), the refinement the library runs. The paper
- *     has no mixed-precision algorithm; these are the readings the library documents.
+ *     §20.5), and Bjorck's corrected semi-normal equations (Bjorck 1987), the
+ *     refinement the library runs, iterated around the R of the mixed-precision TSQR
+ *     (FP32 Householder QR of each leaf, FP64 QR of the stacked leaf triangles: the
+ *     paper's TSQR of §2.3 with the library's precision pattern). The paper has no
+ *     mixed-precision algorithm; these are the readings the library documents.
  *   - Error measures ||A - QR||_F / ||A||_F and ||Q^T Q - I||_F, accumulated with
  *     Neumaier's compensated summation (Neumaier 1974).
  *
@@ -414,12 +416,41 @@ int oracle_lstsq_refine_x_only(int64_t m, int64_t n, const double *A, int64_t ld
 }
 
 /*
+ * R of the mixed-precision TSQR (the library's precision pattern for the mixed path on
+ * the paper's TSQR, §2.3): the rows are split into leaves of h rows (the last leaf takes the
+ * remainder; one leaf when m < 2h), each leaf is rounded to FP32 and factored by the FP32
+ * Householder QR, and the stacked leaf triangles (promoted to FP64) are factored by the
+ * FP64 Householder QR, whose R is returned (n-by-n, any diagonal signs, zeros below).
+ * Every tree shape gives the same R up to rounding (the reduce operator is associative),
+ * so one combine of all leaves stands for any tree. Requires h >= n.
+ */
+void oracle_r_mixed(int64_t m, int64_t n, const double *A, int64_t lda, int64_t h, double *R, int64_t ldr) {
+  const int64_t P = m / h > 0 ? m / h : 1;
+  double *S = (double *)malloc(sizeof(double) * (size_t)(P * n * n));
+  double *tau = (double *)malloc(sizeof(double) * (size_t)n);
+  float *L = (float *)malloc(sizeof(float) * (size_t)((m - (P - 1) * h) * n));
+  float *tau32 = (float *)malloc(sizeof(float) * (size_t)n);
+  const int64_t lds = P * n;
+  for (int64_t l = 0; l < P; l++) {
+    const int64_t r0 = l * h, rows = (l == P - 1) ? m - r0 : h;
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < rows; i++) L[i + j * rows] = (float)AT(A, r0 + i, j, lda);
+    oracle_geqr2_f32(rows, n, L, rows, tau32);
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < n; i++) AT(S, l * n + i, j, lds) = (i <= j) ? (double)L[i + j * rows] : 0.0;
+  }
+  oracle_geqr2(lds, n, S, lds, tau);
+  oracle_extract_r(n, S, lds, R, ldr);
+  free(S); free(tau); free(L); free(tau32);
+}
+
+/*
  * Mixed-precision least squares by corrected semi-normal equations, iterated
  * (Bjorck, "Stability analysis of the method of seminormal equations for linear least
  * squares problems", 1987; Higham, "Accuracy and Stability", §20.6). This is the
  * refinement the library runs; the paper has no mixed-precision algorithm. R is the R
- * factor of an FP32 Householder QR of A (promoted to FP64, any diagonal signs); every
- * other operation is FP64. From x = 0:
+ * of the mixed-precision TSQR with 128-row FP32 leaves (oracle_r_mixed); every other
+ * operation is FP64. From x = 0:
  *   r = b - A x,  g = A^T r,  R^T y = g,  R d = y,  x <- x + d.
  * Stopping rule (the library's reading): stop after the step whose ||d|| / ||x|| is
  * <= 1e-15; or, from the second step on, once ||d|| / ||x|| times rho / (1 - rho) is
@@ -431,18 +462,12 @@ int oracle_lstsq_refine_x_only(int64_t m, int64_t n, const double *A, int64_t ld
  */
 int oracle_lstsq_refine_csne(int64_t m, int64_t n, const double *A, int64_t lda, const double *b,
                              int32_t max_steps, double tol, double *x, double *hist) {
-  float *A32 = (float *)malloc(sizeof(float) * (size_t)(m * n));
-  float *tau = (float *)malloc(sizeof(float) * (size_t)n);
   double *R = (double *)malloc(sizeof(double) * (size_t)(n * n));
   double *r = (double *)malloc(sizeof(double) * (size_t)m);
   double *y = (double *)malloc(sizeof(double) * (size_t)n);
   double *h = (double *)malloc(sizeof(double) * (size_t)(max_steps > 0 ? max_steps : 1));
   int steps = 0;
-  for (int64_t j = 0; j < n; j++)
-    for (int64_t i = 0; i < m; i++) A32[i + j * m] = (float)AT(A, i, j, lda);
-  oracle_geqr2_f32(m, n, A32, m, tau);
-  for (int64_t j = 0; j < n; j++)
-    for (int64_t i = 0; i < n; i++) R[i + j * n] = (i <= j) ? (double)A32[i + j * m] : 0.0;
+  oracle_r_mixed(m, n, A, lda, n > 128 ? n : 128, R, n);
   for (int64_t i = 0; i < n; i++) x[i] = 0.0;
   for (int32_t s = 0; s < max_steps; s++) {
     for (int64_t i = 0; i < m; i++) {          /* r = b - A x */
@@ -475,6 +500,6 @@ int oracle_lstsq_refine_csne(int64_t m, int64_t n, const double *A, int64_t lda,
       if (rho < 0.5 && ratio * rho / (1.0 - rho) <= tol) break;
     }
   }
-  free(A32); free(tau); free(R); free(r); free(y); free(h);
+  free(R); free(r); free(y); free(h);
   return steps;
 }

@@ -82,3 +82,27 @@ def test_three_cta_plan_widths(cuda_lib, n):
     assert _rel(R, Ro) <= R_TOL
     assert _rel(Q, Qo) <= R_TOL
     assert oracle.orth_error(Q) <= BE_TOL
+
+
+@pytest.mark.parametrize("scale", [1e100, 1e-100, 1e140, 1e-140])
+def test_factor_near_the_edges_of_the_supported_range(cuda_lib, scale):
+    """Entries are squared without rescaling, so the supported range is about 1e-150..1e150
+    (the header's numerical range): matrices scaled by 1e+-100 and 1e+-140 factor to the
+    oracle's R (which scales its norms) and an orthonormal Q, the least-squares solution is
+    the unscaled one divided by the scale."""
+    import paper_0912_2572_gb300 as ts
+    m, n = 20_000, 24
+    A0 = inputs.graded(m, n, 3.0, seed_g=77, seed_v=78)
+    A = A0 * scale
+    Ad = to_dev(A)
+    F = ts.factor(Ad, leaf_h=144)
+    R, Q = to_host(F.R), to_host(F.form_q())
+    F.free()
+    Ro = oracle.r_factor(A)
+    assert np.all(np.isfinite(R)) and np.all(np.isfinite(Q))
+    assert _rel(R, Ro) <= R_TOL
+    assert oracle.orth_error(Q) <= BE_TOL
+    b = inputs.gaussian(m, 1, 79)
+    x = to_host(ts.lstsq(Ad, to_dev(b), leaf_h=144))
+    xo = oracle.lstsq(A0, b)
+    assert _rel(x * scale, xo) <= 1e-11

@@ -409,6 +409,27 @@ def test_geqr2_f32_near_triangular_is_stable():
     assert oracle.orth_error(Q) <= 50 * n * U32
 
 
+# --------------------------------------------------- the mixed-precision TSQR R
+def test_r_mixed_single_leaf_and_combine():
+    """oracle_r_mixed: with one leaf (h >= m) the FP64 combine of a single triangle leaves it
+    unchanged, so R is exactly the FP32 QR's R; with several leaves (a ragged last one) it is
+    the FP64 R of the stacked FP32 leaf triangles (paper §2.3's reduce, any tree shape), and
+    it lies within the FP32 bound of the FP64 R of A without being FP64-accurate."""
+    A = inputs.graded(1000, 12, 2.0, seed_g=21, seed_v=22)
+    V32, _ = oracle.geqr2_f32(A)
+    assert np.array_equal(oracle.r_mixed(A, h=1000), oracle.normalised_r_from(V32))
+    leaves = [A[0:128], A[128:256], A[256:384], A[384:512], A[512:640], A[640:768], A[768:1000]]
+    tri = []
+    for L in leaves:
+        VL, _ = oracle.geqr2_f32(L)
+        tri.append(np.triu(np.asarray(VL[:12], dtype=np.float64)))
+    Rs = oracle.r_factor(np.vstack(tri))
+    Rm = oracle.r_mixed(A, h=128)
+    assert rel(Rm, Rs) <= 1e-14
+    err = rel(Rm, oracle.r_factor(A))
+    assert 1e-11 < err <= 50 * 12 * U32
+
+
 # ---------------------------------- corrected semi-normal equations (the GPU's refinement)
 def test_csne_refinement_reaches_fp64_solution():
     """CSNE iterated around the FP32 R reaches the FP64 least-squares solution for
@@ -420,10 +441,11 @@ def test_csne_refinement_reaches_fp64_solution():
     x, hist = oracle.lstsq_refine_csne(A, b[:, 0], max_steps=10)
     assert rel(x, xo) <= 1e-10
     assert hist[0] == 1.0                     # from x = 0 the first correction is all of x
-    # the unblocked FP32 R (4000-term FP32 sums) perturbs the first step most; from the
-    # second correction on each one is smaller than the last
-    assert all(hist[s + 1] < hist[s] for s in range(1, len(hist) - 1))
-    assert hist[-1] <= 1e-13
+    assert all(hist[s + 1] < hist[s] for s in range(len(hist) - 1))
+    rho = max(hist[s + 1] / hist[s] for s in range(len(hist) - 1))
+    assert hist[-1] * rho / (1 - rho) <= 1e-10  # the stop: predicted remaining correction
+    x2, hist2 = oracle.lstsq_refine_csne(A, b[:, 0], max_steps=20, tol=1e-30)
+    assert rel(x2, xo) <= 1e-12 and hist2[-1] <= 1e-13  # run on to the rounding level
     A2 = inputs.graded(1500, 12, 2)
     x_true = inputs.gaussian(12, 1, 20)[:, 0]
     x2, _ = oracle.lstsq_refine_csne(A2, A2 @ x_true, max_steps=10)
@@ -468,6 +490,8 @@ MUTANTS = {
                         "hypotf(alpha, sigma);\n      tau[j] = (beta - alpha) / alpha;"),
     "f32_dropped_pivot_term": ("float w = Bc[j];", "float w = 0.0f;"),
     "f32_scale_denominator": ("float denom = alpha - beta;", "float denom = beta;"),
+    "r_mixed_leaf_remainder": ("const int64_t r0 = l * h, rows = (l == P - 1) ? m - r0 : h;",
+                               "const int64_t r0 = l * h, rows = h;"),
     "csne_gradient_sign": ("for (int64_t i = 0; i < m; i++) t += AT(A, i, j, lda) * r[i];\n      y[j] = t;",
                            "for (int64_t i = 0; i < m; i++) t -= AT(A, i, j, lda) * r[i];\n      y[j] = t;"),
     "scale_denominator": ("for (int64_t i = 1; i < m - j; i++) x[i] = x[i] / denom;",
@@ -502,6 +526,7 @@ run("f32_exact", t.test_geqr2_f32_against_fp64_and_exact)
 run("f32_closed", t.test_geqr2_f32_closed_form_and_reflectors)
 run("f32_near_triangular", t.test_geqr2_f32_near_triangular_is_stable)
 run("csne", t.test_csne_refinement_reaches_fp64_solution)
+run("r_mixed", t.test_r_mixed_single_leaf_and_combine)
 print("FAILED:" + ",".join(failed))
 """
 
