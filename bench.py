@@ -1047,7 +1047,9 @@ def bench_ours(args):
             "phases": {"factor_ms": factor_ms,
                        "factor_gflops": fl["factor"] / (factor_ms * 1e-3) / 1e9 if factor_ms else None,
                        "form_q_ms": phase_ms.get("form_q", 0) / args.steps,
-                       "apply_qt_ms": phase_ms.get("apply_qt", 0) / args.steps,
+                       # Q^T b runs beside the thin Q on a second stream: its launches' event
+                       # times include the time they wait for SMs (alone: config2.apply_qt_k1_ms)
+                       "apply_qt_ms_beside_form_q": phase_ms.get("apply_qt", 0) / args.steps,
                        "small_ms": phase_ms.get("small", 0) / args.steps},
             "roofline": {"kernel": "k_factor (leaf/flat-chain launch)", "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -676,9 +676,17 @@ static tsqr_status run_apply(const tsqr_factors *F, double *B, int64_t ldb, int 
     for (int q = 0; q < nl; ++q) {
       const int li = trans ? q : nl - 1 - q;
       tsqr_status st = TSQR_OK;
-      if (clustered && li > pl.cl_base) {
+      // a cluster launch runs only while all its CTAs (16 columns each) fit one wave at two
+      // per SM: on wider levels the pipelined launch is slower than the per-level launches
+      // (measured at 4M x 64: levels 3-5 of the thin Q 0.65 ms clustered, 0.43 ms per level)
+      const Plan::ClusterLaunch *hit = nullptr;
+      if (clustered && li > pl.cl_base)
         for (const Plan::ClusterLaunch &cl : pl.cl_launches)
-          if (cl.level_hi == li) st = apply_cluster_launch(F, B, ldb, c0, kg, formq, cl, s);
+          if (li >= cl.level_lo && li <= cl.level_hi) hit = &cl;
+      const int sms = device_info(F->device).sms;
+      if (hit && (int64_t)hit->nclusters * kClusterSize * ((kg + 15) / 16) > (int64_t)sms * 2) hit = nullptr;
+      if (hit) {
+        if (li == hit->level_hi) st = apply_cluster_launch(F, B, ldb, c0, kg, formq, *hit, s);
       } else {
         st = apply_launch(F, B, ldb, c0, kg, trans, formq, li, s);
       }
