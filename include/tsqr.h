@@ -495,6 +495,18 @@ tsqr_status tsqr_server_destroy(tsqr_server *srv);
 int32_t tsqr_set_mixed_wy_min_n(int32_t min_n);
 
 /*
+ * tsqr_set_apply_tile_pairs — kernel choice for applying Q^T or Q (tsqr_apply_qt,
+ * tsqr_apply_q, the overlapped Q^T B of tsqr_factor_qt and tsqr_lstsq) to ONE column
+ * (paper §2.3: the implicit Q is applied tile by tile along each flat chain). With `on`
+ * (the default) a launch whose jobs hold several tiles gives each job one warp whose two
+ * half-warps run consecutive tiles of the chain one reflector apart; with 0 one warp runs
+ * the job's tiles one after the other. The two differ only in summation order (results
+ * agree to rounding). Process-wide, for calls made after it; returns the previous value.
+ * No error.
+ */
+int32_t tsqr_set_apply_tile_pairs(int32_t on);
+
+/*
  * tsqr_debug_fail_allocations — failure injection for tests: the next `count` device
  * allocations the library makes fail as if the device were out of memory (the calls
  * return TSQR_ERR_OOM; a server batch whose workspace allocation fails reports

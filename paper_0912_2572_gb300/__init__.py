@@ -466,6 +466,12 @@ def set_mixed_wy_min_n(min_n: int) -> int:
     return _lib.load().tsqr_set_mixed_wy_min_n(int(min_n))
 
 
+def set_apply_tile_pairs(on: bool) -> bool:
+    """Q^T b / Q b with one column: tile pairs per warp (True, the default) or one warp per
+    tile in sequence (False). Returns the previous setting (tsqr_set_apply_tile_pairs)."""
+    return bool(_lib.load().tsqr_set_apply_tile_pairs(1 if on else 0))
+
+
 def error_word(stream=None) -> int:
     """Reads and clears the device error word (tsqr_error_word; waits for the stream):
     bit 1 = a bounded device wait gave up, bit 2 = an index check of a TSQR_CHECK build."""

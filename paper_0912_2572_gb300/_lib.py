@@ -53,6 +53,7 @@ SIGNATURES = {
                                   _i32, _i32, _i32, _vp, _vp, _vp]),
     "tsqr_debug_fail_allocations": (_i32, [_i32]),
     "tsqr_set_mixed_wy_min_n": (_i32, [_i32]),
+    "tsqr_set_apply_tile_pairs": (_i32, [_i32]),
     "tsqr_batch_describe": (_i32, [ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _i64, _i64, _i64,
                                    ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i64]),
     "tsqr_plan_clusters": (_i32, [_i64, _i32, _i32, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.POINTER(_i64),

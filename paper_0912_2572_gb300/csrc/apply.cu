@@ -228,6 +228,179 @@ __global__ void __launch_bounds__(128, 2) k_apply_warp(const ApplyParamsT<R> p, 
     for (int j = lane; j < n; j += 32) bcol(c)[pr + j] = PR[c * n + j];
 }
 
+// ------------------------------------------- one column: tile pairs per warp
+// Q^T b or Q b for a single column is, per reflector, a dot product over the tile rows, a
+// reduction and an update of one vector. With a whole warp on one tile (k_apply_warp) a
+// lane holds about five rows of a 144-row tile, and the FP64 pipe spends as much on the
+// 32-lane reduction and the scalar step as on the dot product and the update. Here a job's
+// tiles are dealt alternately to the two half-warps: half 1 runs the next tile in the
+// processing order one reflector step behind half 0. Reflector j of a tile needs only the
+// pivot entry PR[j] as the previous tile's reflector j left it (and reflectors j' > j do
+// not touch it), so the lag of one step is enough. Each warp instruction then carries two
+// reflector applications, each lane holds about ten rows, and a reduction spans 16 lanes.
+//
+// Half h runs local steps u = 0, 1, ...: tile position q = 2 (u / n) + h, reflector step
+// u mod n, at warp step t = u + h. The pivot entries live in two buffers: tile q reads
+// buffer q mod 2 and writes the other, so no entry is rewritten in the step that reads it,
+// and the final pivot rows are in buffer nt mod 2. A leaf tile (GEQRT) holds the pivot
+// rows themselves: applying Q^T (the leaf first) it starts from the input buffer and
+// publishes row j after reflector j (later reflectors touch rows > j only); applying Q
+// (the leaf last) it takes row j from the input buffer at reflector j (reflectors j' > j,
+// which run before, touch rows >= j' only) and writes its rows < n out at the end.
+
+template <int RV>
+__global__ void __launch_bounds__(128, 3) k_apply_vec(const ApplyParamsT<double> p, int njobs) {
+  // reflector tails loaded ahead per half (fewer for tall tiles, to stay in registers)
+  constexpr int kVecD = RV <= 16 ? 3 : 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane >> 4, hl = lane & 15;
+  const int jid = blockIdx.x * 4 + warp;
+  if (jid >= njobs) return;  // warp-uniform; this kernel uses no block barrier
+  const int n = p.n, ldt = p.ldt;
+  double *PR = reinterpret_cast<double *>(smraw) + (size_t)warp * (2 * (size_t)ldt + 2 * n);  // 2 x n
+  double *Bt = PR + 2 * n + (size_t)h * ldt;  // this half's tile
+  double *B = p.B + (int64_t)p.col0 * p.ldb;
+  TSQR_CHECK_OR_SKIP(p.njobs == 0 || p.job0 + jid < p.njobs, p.err)
+  const JobDesc job = p.jobs[p.job0 + jid];
+  const int64_t pr = job.piv_row;
+  const int nt = job.tile_count;
+  TSQR_CHECK_OR_SKIP(pr >= 0 && (p.rows == 0 || pr + n <= p.rows) &&
+                         (p.ntiles == 0 || job.tile_begin + nt <= p.ntiles),
+                     p.err)
+#ifdef TSQR_CHECK
+  // every tile is checked before the pipeline starts: a check inside it would let one half
+  // leave while the other waits for it in a shuffle
+  for (int q = 0; q < nt; ++q) {
+    const TileDesc tq = p.tiles[job.tile_begin + q];
+    TSQR_CHECK_OR_SKIP(tq.row0 >= 0 && tq.nrows >= 1 && tq.nrows <= ldt &&
+                           (p.rows == 0 || tq.row0 + tq.nrows <= p.rows) && tq.refl >= 0 &&
+                           (p.nrefl == 0 || tq.refl + n <= p.nrefl),
+                       p.err)
+  }
+#endif
+  for (int j = lane; j < n; j += 32) PR[j] = B[pr + j];
+
+  const int usteps = ((nt - h + 1) >> 1) * n;                 // this half's local steps
+  const int T = max(((nt + 1) >> 1) * n, (nt >> 1) * n + 1);  // warp steps
+  auto tile_of = [&](int u) -> TileDesc {
+    const int q = 2 * (u / n) + h;
+    return p.tiles[job.tile_begin + (p.trans ? q : nt - 1 - q)];
+  };
+  auto refl_of = [&](int u) -> int { return p.trans ? u % n : n - 1 - u % n; };
+  // this lane's rows of the tail of local step u's reflector, its tau, scale, tau * scale
+  double xb[kVecD][RV], tb[kVecD], sb[kVecD], cb[kVecD];
+  auto load = [&](int d, int u) {
+#pragma unroll
+    for (int r = 0; r < RV; ++r) xb[d][r] = 0.0;
+    tb[d] = sb[d] = cb[d] = 0.0;
+    if (u < 0 || u >= usteps) return;
+    const TileDesc tq = tile_of(u);
+    const int j = refl_of(u);
+    int lo, hi;
+    refl_rows(tq.kind, j, tq.nrows, lo, hi, tq.off);
+    const double *v = p.V + tq.row0 + (int64_t)j * p.ldv;
+#pragma unroll
+    for (int r = 0; r < RV; ++r) {
+      const int i = lo + hl + 16 * r;
+      if (i < hi) xb[d][r] = __ldg(v + i);
+    }
+    tb[d] = __ldg(p.tau + tq.refl + j);
+    sb[d] = __ldg(p.scl + tq.refl + j);
+    cb[d] = tb[d] * sb[d];
+  };
+#pragma unroll
+  for (int d = 0; d < kVecD; ++d) load(d, d - h);
+
+  TileDesc td{};  // the half's current tile
+  double *Pin = PR, *Pout = PR + n;  // its pivot buffers (tile q: in = q mod 2)
+  // A tile leaves shared memory at the warp step after its last reflector (the rows of
+  // that update belong to other lanes); the leaf's pivot rows go back to PR (applying Q)
+  // or were published row by row (applying Q^T).
+  auto store_prev = [&](int u) {
+    const int up = u - 1;
+    if (up < 0 || up >= usteps || up % n != n - 1) return;
+    const bool ge = (td.kind == GEQRT);
+    for (int i = hl; i < td.nrows; i += 16) {
+      if (ge && i < n) {
+        if (!p.trans) Pout[i] = Bt[i];
+      } else {
+        B[td.row0 + i] = Bt[i];
+      }
+    }
+  };
+  for (int t0 = 0; t0 < T; t0 += kVecD) {
+#pragma unroll
+    for (int d = 0; d < kVecD; ++d) {
+      const int t = t0 + d;
+      if (t >= T) break;  // warp-uniform
+      const int u = t - h;
+      const bool act = (u >= 0 && u < usteps);
+      __syncwarp();  // the previous step's updates and head entries are visible
+      store_prev(u);
+      if (act && u % n == 0) {  // stage the next tile
+        td = tile_of(u);
+        const int q = 2 * (u / n) + h;
+        Pin = PR + (q & 1) * n;
+        Pout = PR + ((q + 1) & 1) * n;
+        const bool ge = (td.kind == GEQRT);
+        for (int i = hl; i < td.nrows; i += 16) {
+          if (ge && i < n) {
+            if (p.trans) Bt[i] = Pin[i];
+          } else {
+            Bt[i] = B[td.row0 + i];
+          }
+        }
+      }
+      __syncwarp();
+      const int j = refl_of(act ? u : 0);
+      int lo = 0, hi = 0;
+      if (act) refl_rows(td.kind, j, td.nrows, lo, hi, td.off);
+      const int rh = (hi - lo + 15) >> 4;
+      const int ra = max(rh, __shfl_xor_sync(kFull, rh, 16));
+      const double(&xv)[RV] = xb[d];
+      double acc = 0.0;
+#define TSQR_VDOT(r)                                                                         \
+  {                                                                                          \
+    const int i = lo + hl + 16 * (r);                                                        \
+    if (i < hi) acc = fma(xv[r], Bt[i], acc);                                                \
+  }
+      TSQR_ROW_SLOTS(ra, RV, TSQR_VDOT)
+#undef TSQR_VDOT
+#pragma unroll
+      for (int m = 8; m >= 1; m >>= 1) acc += __shfl_xor_sync(kFull, acc, m);
+      if (act) {
+        // v = [1; scale * tail]: w = v^T b, the head entry becomes piv - tau w and the tail
+        // rows take b_i - (tau scale w) x_i
+        const bool ge = (td.kind == GEQRT);
+        const double piv = (ge && p.trans) ? Bt[j] : Pin[j];
+        const double w = fma(sb[d], acc, piv);
+        const double cf = cb[d] * w;
+#define TSQR_VUPD(r)                                                                         \
+  {                                                                                          \
+    const int i = lo + hl + 16 * (r);                                                        \
+    if (i < hi) Bt[i] = fma(-cf, xv[r], Bt[i]);                                              \
+  }
+        TSQR_ROW_SLOTS(ra, RV, TSQR_VUPD)
+#undef TSQR_VUPD
+        if (hl == 0) {
+          const double np = fma(-tb[d], w, piv);
+          if (ge && !p.trans)
+            Bt[j] = np;  // later reflectors j' < j update row j as a tail row
+          else
+            Pout[j] = np;
+        }
+      }
+      load(d, u + kVecD);
+    }
+  }
+  __syncwarp();
+  store_prev(T - h);
+  __syncwarp();
+  const double *Pf = PR + (nt & 1) * n;
+  for (int j = lane; j < n; j += 32) B[pr + j] = Pf[j];
+}
+
 // ------------------------------------------------------------ one CTA per job
 // The structure of the factor kernel: the job's tile of B (up to 16*CMAX columns of this
 // pass) is staged in shared memory, the pivot row of each reflector is staged from
@@ -661,6 +834,15 @@ cudaError_t launch_warp_k(const ApplyParamsT<R> &p, int njobs, cudaStream_t s) {
   return launch_warp_t<K, 16, R>(p, njobs, s);
 }
 
+template <int RV>
+cudaError_t launch_vec_t(const ApplyParamsT<double> &p, int njobs, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * 4 * (2 * (size_t)p.ldt + 2 * (size_t)p.n);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_vec<RV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_apply_vec<RV><<<(njobs + 3) / 4, 128, bytes, s>>>(p, njobs);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_apply_any(const ApplyParamsT<R> &p, int njobs, int ctas_per_sm, int cols_per_cta,
                              cudaStream_t s) {
@@ -719,7 +901,17 @@ cudaError_t launch_apply_cluster(const ApplyParamsT<double> &p, const ApplyClust
 }
 
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm,
-                         int cols_per_cta) {
+                         int cols_per_cta, bool tile_pairs) {
+  // one column of B over jobs of several tiles: the tile-pair kernel (its one-step lag
+  // needs n >= 2; forming Q keeps the warp kernel)
+  if (tile_pairs && p.k == 1 && !p.formq && p.n >= 2 && njobs > 0) {
+    const int rows_per_lane = (p.ldt + 15) / 16;
+    if (rows_per_lane <= 8) return launch_vec_t<8>(p, njobs, s);
+    if (rows_per_lane <= 9) return launch_vec_t<9>(p, njobs, s);
+    if (rows_per_lane <= 16) return launch_vec_t<16>(p, njobs, s);
+    if (rows_per_lane <= 32) return launch_vec_t<32>(p, njobs, s);
+    return cudaErrorInvalidValue;
+  }
   return launch_apply_any(p, njobs, ctas_per_sm, cols_per_cta, s);
 }
 

@@ -81,6 +81,10 @@ std::atomic<int32_t> g_fail_allocs{0};
 // compact-WY panels with 3xTF32 tensor-core updates (0: never; tsqr_set_mixed_wy_min_n).
 std::atomic<int32_t> g_wy_min_n{0};
 
+// Q^T b and Q b with one column run the tile-pair kernel on launches whose jobs hold
+// several tiles (1, the default; 0: the one-warp-per-tile kernel; tsqr_set_apply_tile_pairs).
+std::atomic<int32_t> g_tile_pairs{1};
+
 // Stream-ordered allocations come from a memory pool of the library's own, one per device,
 // kept cached so that repeated factorizations do not return memory to the driver. Its
 // blocks freed on one stream are not reused by another stream through an inserted
@@ -623,7 +627,9 @@ static tsqr_status apply_launch(const tsqr_factors *F, double *B, int64_t ldb, i
   // a tree level whose nodes, four CTAs each, still fit one wave of two CTAs per SM runs
   // 16 columns per CTA: each node's reflector steps get shorter
   const bool narrow = li > 0 && (int64_t)ld.job_count * 4 <= (int64_t)sms * 2;
-  CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2, narrow ? 16 : 64));
+  // one column over jobs of several tiles (the chains): tile pairs per warp
+  const bool pairs = ld.job_count > 0 && pl.jobs[ld.job_begin].tile_count >= 2 && g_tile_pairs.load() != 0;
+  CUDA_TRY(launch_apply(p, ld.job_count, s, li == 0 ? pl.ctas_per_sm : 2, narrow ? 16 : 64, pairs));
   return TSQR_OK;
 }
 
@@ -1407,6 +1413,8 @@ const char *tsqr_strerror(tsqr_status s) {
 const char *tsqr_last_error(void) { return g_last_error.c_str(); }
 
 int32_t tsqr_set_mixed_wy_min_n(int32_t min_n) { return g_wy_min_n.exchange(min_n < 0 ? 0 : min_n); }
+
+int32_t tsqr_set_apply_tile_pairs(int32_t on) { return g_tile_pairs.exchange(on ? 1 : 0); }
 
 tsqr_status tsqr_debug_fail_allocations(int32_t count) {
   if (count < 0) return fail(TSQR_ERR_ARG, "count < 0");

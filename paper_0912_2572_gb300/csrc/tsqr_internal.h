@@ -280,8 +280,10 @@ using ApplyParams = ApplyParamsT<double>;
 // cols_per_cta caps the columns of B one CTA of the tile kernel handles (16, 32 or 64): a
 // launch with few jobs (a tree level) spreads a job's columns over more CTAs. Columns are
 // independent; only the summation order of a column's dot products changes with the cap.
+// tile_pairs: a launch whose jobs hold several tiles, with one column of B (Q^T b, Q b),
+// runs the tile-pair kernel (the job's tiles alternate between the two half-warps).
 cudaError_t launch_apply(const ApplyParamsT<double> &p, int njobs, cudaStream_t s, int ctas_per_sm = 2,
-                         int cols_per_cta = 64);
+                         int cols_per_cta = 64, bool tile_pairs = false);
 
 // Cluster tier of B <- Q B (top down): one CTA per combine of a cluster launch of the
 // factorization's schedule, for 16 columns of B; parent = the cluster rank whose block this

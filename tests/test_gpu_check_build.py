@@ -48,13 +48,14 @@ def run_path(lib, A, B, m, n, k, leaf_h, arity, flags, wide=False):
 CASES = [
     # (m, n, k, leaf_h, arity, flags, wide): two-level, pure binary with a ragged tail,
     # 4-ary, flat, the cluster tier, the warp apply (k <= 8) and the tile apply (k > 8),
-    # thin Q by passes (n <= 32) and by tiles, CAQR
+    # thin Q by passes (n <= 32) and by tiles, CAQR, the tile-pair apply (k = 1)
     (20_000, 32, 3, 144, 2, 2, False),
     (5_003, 16, 12, 100, 2, 0, False),
     (9_000, 64, 1, 256, 4, 0, False),
     (2_000, 8, 2, 64, 0, 0, False),
     (60_000, 48, 2, 64, 2, 4, False),
     (3_000, 200, 2, 144, 2, 2, True),
+    (2_000, 8, 1, 64, 0, 0, False),  # one column over a flat tree: the tile-pair apply
 ]
 
 
