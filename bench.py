@@ -38,13 +38,16 @@ FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20
 # capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum at m = 1,048,576,
 # n = 64, 144-row tiles: 1.050 GB); traffic grows with the rows, so it is scaled by m.
 # Valid for n = 64 and that kernel build.
-# end-to-end pipeline: steps alternate between this many streams, each with its own
-# device buffers; the steps' kernels are ordered one after another by an event chain, so
-# one step's result copy and the next step's input copy overlap the kernels of the step in
-# between (measured at 4M x 64: 82.0 ms per step with two streams, 82.5 with three; without
-# the event chain 89.6 with two, because concurrent steps finish together and their copies
-# then queue while the GPU idles; 101.8 with one stream)
-E2E_SLOTS = 2
+# end-to-end pipeline: steps rotate over this many streams, each with its own device
+# buffers; the steps' kernels are ordered one after another by an event chain, so one
+# step's result copy and the next steps' input copies overlap the kernels in between.
+# Host-device copy bandwidth on the GB300 machines varies from run to run (a 2 GB copy takes
+# 10 ms or, now and then, 30-60 ms), and a third stream absorbs more of that: measured at
+# 4M x 64 on one box through tsqr_qr_solve_host, 84.3 / 79.9 ms per step with three
+# streams against 94.4 / 86.7 / 89.8 / 90.4 with two (without the event chain: 89.6 with
+# two, because concurrent steps finish together and their copies then queue while the GPU
+# idles; 101.8 with one stream)
+E2E_SLOTS = 3
 CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.427328e6 + 502.893824e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
@@ -651,12 +654,17 @@ def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plai
             time.sleep(0.0002)
         return done
 
-    def closed_loop(prec):
-        with ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8) as srv:
+    def server(resident):
+        if resident:  # one persistent kernel admitting requests while it runs
+            return ts.Server(resident=True, chain_tiles=8, idle_us=20_000)
+        return ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8)
+
+    def closed_loop(prec, resident=False):
+        with server(resident) as srv:
             warm = [int(i) for i in g.integers(0, pool_size, size=64)]
             submit_all(srv, warm, prec)
             collect(srv, len(warm))
-            b0 = srv.stats()["batches"]
+            b0 = srv.stats()["launches" if resident else "batches"]
             idx = [int(i) for i in g.integers(0, pool_size, size=closed)]
             t0 = time.perf_counter()
             outs = submit_all(srv, idx, prec)
@@ -666,12 +674,16 @@ def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plai
         lat = np.array([d[1] for d in done])
         errs = [float(torch.linalg.norm(X - Xplain[i]) / torch.linalg.norm(Xplain[i]))
                 for i, X in outs.values() if i in Xplain]
-        return {"requests": closed, "solves_per_s": closed / t,
-                "gflops_fp64_equiv": sum(lsq_flops(pool[i]) for i in idx) / t / 1e9,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "batches": st["batches"] - b0, "largest_batch": st["max_batch"],
-                "failed": sum(1 for d in done if d[2] != 0),
-                "max_rel_diff_vs_plain_fp64": max(errs) if errs else None}
+        out = {"requests": closed, "solves_per_s": closed / t,
+               "gflops_fp64_equiv": sum(lsq_flops(pool[i]) for i in idx) / t / 1e9,
+               "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "failed": sum(1 for d in done if d[2] != 0),
+               "max_rel_diff_vs_plain_fp64": max(errs) if errs else None}
+        if resident:
+            out.update({"launches": st["launches"] - b0, "most_in_flight": st["max_in_flight"]})
+        else:
+            out.update({"batches": st["batches"] - b0, "largest_batch": st["max_batch"]})
+        return out
 
     res = {"closed_loop": {}}
     for name, prec in (("fp64", ts.FP64), ("auto", ts.AUTO), ("mixed", ts.MIXED)):
@@ -717,8 +729,8 @@ def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plai
         return {"offered_per_s": rate_, "arrivals": count, "completed_per_s": count / (time.perf_counter() - start),
                 "p50_ms": float(np.percentile(lat_, 50) * 1e3), "p99_ms": float(np.percentile(lat_, 99) * 1e3)}
 
-    def served_open_loop(rate_, count, prec_):
-        with ts.Server(max_batch=max_batch, streams=streams, chain_tiles=8) as srv:
+    def served_open_loop(rate_, count, prec_, resident=False):
+        with server(resident) as srv:
             warm = [int(i) for i in g.integers(0, pool_size, size=32)]
             submit_all(srv, warm, prec_)
             collect(srv, len(warm))
@@ -735,6 +747,11 @@ def bench_served(ts, pool_size=160, rate=2000.0, arrivals=2000, closed=800, plai
 
     res["plain_open_loop"] = plain_open_loop(rate, 300)
     res["low_rate_200_per_s"] = {"plain": plain_open_loop(200.0, 300), "served": served_open_loop(200.0, 300, prec)}
+    # the resident server (requests admitted into the running persistent kernel), MIXED
+    res["resident"] = {"closed_loop_mixed": closed_loop(ts.MIXED, resident=True),
+                       "open_loop_2000_per_s": served_open_loop(rate, arrivals, ts.MIXED, resident=True),
+                       "open_loop_200_per_s": served_open_loop(200.0, 300, ts.MIXED, resident=True),
+                       "launching_server_open_loop_200_per_s_mixed": served_open_loop(200.0, 300, ts.MIXED)}
     res["plain_fp64"] = {"solves_per_s": 1.0 / t_plain, "ms_per_solve": t_plain * 1e3,
                          "gflops": plain_fl / t_plain / 1e9, "sample": plain_sample}
     res["speedup_closed_vs_plain"] = {k: v["solves_per_s"] / res["plain_fp64"]["solves_per_s"]

@@ -474,6 +474,35 @@ tsqr_status tsqr_batch_plan_destroy(tsqr_batch_plan *plan);
 typedef struct tsqr_server tsqr_server;
 tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t streams, int32_t chain_tiles,
                                int32_t ctas_per_sm, tsqr_server **srv);
+
+/*
+ * Resident server (the paper has no counterpart): the same requests, admitted into a
+ * persistent kernel that is already running. One kernel stays on the GPU and takes work
+ * from a ring in device memory; the server's worker thread appends each admitted request
+ * to the ring while the kernel runs, so a request starts as soon as its uploads land, not
+ * when a launch slot frees up. FP64 and mixed requests both run inside the kernel: the
+ * refinement steps of mixed least-squares requests are queued by the kernel itself. The
+ * kernel ends after idle_us without work and is launched again when requests arrive.
+ * Results are bitwise those of tsqr_batch_solve on the request alone (same plan, same
+ * arithmetic; the compact-WY leaf of tsqr_set_mixed_wy_min_n is not used here).
+ *
+ * tsqr_server_create_resident(max_bytes, chain_tiles, ctas_per_sm, idle_us, &srv)
+ *   max_bytes    device memory reserved at creation for requests in flight (the arena;
+ *                admission waits for room in it); <= 0 = a quarter of the memory free now.
+ *   chain_tiles  as for tsqr_batch_solve (0 = automatic).
+ *   ctas_per_sm  0 or 2: two CTAs per SM; 1: one, with twice the shared memory per CTA
+ *                (needed by FP64 requests with n + k above about 100 columns).
+ *   idle_us      >= 0, how long the kernel polls for work before it ends (about).
+ *   Errors: TSQR_ERR_ARG, TSQR_ERR_OOM (the arena), TSQR_ERR_CUDA.
+ * tsqr_server_submit on a resident server also plans the request and returns
+ * TSQR_ERR_UNSUPPORTED (nothing queued) when it needs more shared memory per CTA than the
+ * kernel has, or more device memory than the arena. tsqr_server_stats: out[2] = launches
+ * of the resident kernel, out[3] = most requests in flight at once, out[4] = arena bytes,
+ * out[5] = arena bytes in use. poll, drain and destroy are as above. While the kernel
+ * runs, a device-wide synchronization (cudaDeviceSynchronize) waits for it to go idle.
+ */
+tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, int32_t ctas_per_sm,
+                                        int32_t idle_us, tsqr_server **srv);
 tsqr_status tsqr_server_submit(tsqr_server *srv, const tsqr_batch_item *item, int64_t *ticket);
 tsqr_status tsqr_server_poll(tsqr_server *srv, int32_t max, int64_t *tickets, double *latency_s,
                              int32_t *status, int32_t *count);

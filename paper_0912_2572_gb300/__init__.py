@@ -242,7 +242,7 @@ def batch_solve(items, chain_tiles: int = 0, arity: int = 0, stream=None, status
 
     items: list of dicts with "A" (m-by-n column-major float64 CUDA tensor) and optional
     "B" (m-by-k), "R" and "X" output tensors (allocated here when missing and "want_r" /
-    B are given) and "prec" (FP64 or MIXED; MIXED takes no B). Returns the list of
+    B are given) and "prec" (FP64, MIXED or AUTO). Returns the list of
     (R, X) per item (None where not requested); with ``status`` also the per-item status
     codes, and with ``info`` the per-item (refinement steps, last ||dX||/||X||) (both
     synchronize the stream).
@@ -361,11 +361,19 @@ class Server:
     """
 
     def __init__(self, max_bytes: int = 0, max_batch: int = 256, streams: int = 2, chain_tiles: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, resident: bool = False, idle_us: int = 2000):
+        """``resident``: admit requests into one persistent kernel that stays on the GPU
+        (tsqr_server_create_resident; ``max_bytes`` is then its arena, ``idle_us`` how long
+        it polls for work before it ends) instead of launching a batch per free stream."""
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
-        _lib.check(self._lib.tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctas_per_sm,
-                                                ctypes.byref(self._h)), "tsqr_server_create")
+        self.resident = bool(resident)
+        if resident:
+            _lib.check(self._lib.tsqr_server_create_resident(max_bytes, chain_tiles, ctas_per_sm, idle_us,
+                                                             ctypes.byref(self._h)), "tsqr_server_create_resident")
+        else:
+            _lib.check(self._lib.tsqr_server_create(max_bytes, max_batch, streams, chain_tiles, ctas_per_sm,
+                                                    ctypes.byref(self._h)), "tsqr_server_create")
         self._live = {}
 
     def submit(self, item):
@@ -394,7 +402,9 @@ class Server:
     def stats(self):
         out = (ctypes.c_int64 * 6)()
         _lib.check(self._lib.tsqr_server_stats(self._h, out), "tsqr_server_stats")
-        keys = ("submitted", "completed", "batches", "max_batch", "budget_bytes", "bytes_in_flight")
+        keys = (("submitted", "completed", "launches", "max_in_flight", "arena_bytes", "bytes_in_flight")
+                if self.resident else
+                ("submitted", "completed", "batches", "max_batch", "budget_bytes", "bytes_in_flight"))
         return dict(zip(keys, list(out)))
 
     def close(self):

@@ -122,8 +122,7 @@ cudaError_t lib_pool(int dev, cudaMemPool_t *out) {
 }
 
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
-  for (int32_t f = g_fail_allocs.load(); f > 0; f = g_fail_allocs.load())
-    if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return cudaErrorMemoryAllocation;
+  if (tsqr::debug_take_allocation_failure()) return cudaErrorMemoryAllocation;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1221,6 +1220,102 @@ tsqr_status tsqr::batch_solve_internal(const tsqr_batch_item *items, int32_t cou
   return st;
 }
 
+// ------------------------------------------------- requests of the resident kernel
+// A request is planned exactly as a one-item batch (so it is bitwise the same request as
+// tsqr_batch_solve solves alone) and laid out in one device block of the resident
+// server's arena: the batched layout, then the count of refinement groups still running.
+size_t tsqr::resident_smem_bytes(int ctas_per_sm) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const DeviceInfo di = device_info(dev);
+  if (di.sms == 0 || ctas_per_sm < 1) return 0;
+  const size_t per = di.smem_sm / (size_t)ctas_per_sm;
+  const size_t fixed = di.reserved + kBatchSmemSlack;
+  if (per <= fixed) return 0;
+  return std::min(per - fixed, di.optin);
+}
+
+int64_t tsqr::refine_rows_per_task() { return kRefineRows; }
+int32_t tsqr::refine_max_steps() { return kRefineSteps; }
+double tsqr::refine_tolerance() { return kBatchRefineTol; }
+
+tsqr_status tsqr::resident_plan(const tsqr_batch_item &it, int32_t chain_tiles, ResidentPlan &out) {
+  out = ResidentPlan{};
+  tsqr_status st = check_batch_item(it, 0);
+  if (st != TSQR_OK) return st;
+  BatchBuild *b = new (std::nothrow) BatchBuild();
+  if (!b) return fail(TSQR_ERR_OOM, "host memory for a plan");
+  st = batch_build(&it, 1, chain_tiles, 2, *b);
+  if (st != TSQR_OK) {
+    delete b;
+    return st;
+  }
+  out.impl = b;
+  out.bytes = b->bytes + 256;  // + the refinement groups still running
+  // the resident kernel runs the register-tile FP32 leaf; a compact-WY plan only asked
+  // for more shared memory
+  size_t smem = 0;
+  for (int32_t q = 0; q < b->count; ++q) {
+    const int nc = b->plans[q].mixed ? it.n : it.n + it.k;
+    const size_t elem = b->plans[q].mixed ? sizeof(float) : sizeof(double);
+    smem = std::max(smem, factor_smem_bytes(nc, b->plans[q].tile_h, elem));
+    smem = std::max(smem, factor_smem_bytes(nc, b->tree_rows[q], sizeof(double)));
+    smem = std::max(smem, sizeof(double) * (size_t)it.n * std::max(it.k, 1));
+  }
+  out.smem = std::max(smem, b->rsmem);
+  out.cmax = b->cmax;
+  out.nchains = b->nchains;
+  out.njobs = b->njobs;
+  out.ngroups = (int32_t)b->rinst.size();
+  out.nt = b->rinst.empty() ? 0 : b->rinst[0].nt;
+  out.wy = b->wy_any;
+  return TSQR_OK;
+}
+
+void tsqr::resident_plan_free(ResidentPlan &p) {
+  delete static_cast<BatchBuild *>(p.impl);
+  p.impl = nullptr;
+}
+
+tsqr_status tsqr::resident_upload(const ResidentPlan &p, char *base, cudaStream_t s, ResItemDev &dev) {
+  BatchBuild &b = *static_cast<BatchBuild *>(p.impl);
+  batch_bind(b, base);
+  tsqr_status st = batch_upload(b, base, s);
+  if (st != TSQR_OK) return st;
+  const tsqr_batch_item &it = b.items[0];
+  const BatchInst &bi = b.inst[0];
+  if (bi.k > 0)
+    CUDA_TRY(cudaMemcpy2DAsync(bi.B, sizeof(double) * it.m, it.B, sizeof(double) * it.ldb, sizeof(double) * it.m,
+                               it.k, cudaMemcpyDeviceToDevice, s));
+  // counters, status and flags are cleared by copies (copy engines), never by kernels: the
+  // resident kernel may hold every SM while these run
+  int32_t *pending = (int32_t *)(base + b.bytes);
+  const int32_t groups = (int32_t)b.rinst.size();
+  const size_t n_cnt = sizeof(int32_t) * ((size_t)b.njobs + 1), n_st = sizeof(int32_t) * b.count;
+  const size_t n_fl = sizeof(int32_t) * 2 * b.rinst.size(), n_hist = sizeof(double) * b.max_steps * b.rinst.size();
+  std::vector<unsigned char> zeros(std::max({n_cnt, n_st, n_fl}), 0), ones(n_hist, 0xff);
+  CUDA_TRY(cudaMemcpyAsync(base + b.o_cnt, zeros.data(), n_cnt, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(base + b.o_st, zeros.data(), n_st, cudaMemcpyHostToDevice, s));
+  if (groups > 0) {
+    CUDA_TRY(cudaMemcpyAsync(base + b.o_rflags, zeros.data(), n_fl, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(base + b.o_rhist, ones.data(), n_hist, cudaMemcpyHostToDevice, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(pending, &groups, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  dev = ResItemDev{};
+  dev.inst = bi;
+  dev.inst.wy = 0;
+  dev.jobs = (const BatchJob *)(base + b.o_jobs);
+  dev.tiles = (const TileDesc *)(base + b.o_tiles);
+  dev.counters = (int32_t *)(base + b.o_cnt);
+  dev.rinst = groups > 0 ? (RefineInst *)(base + b.o_rinst) : nullptr;
+  dev.pending = pending;
+  dev.m = it.m;
+  dev.nchains = b.nchains;
+  dev.ngroups = groups;
+  dev.nt = p.nt;
+  return TSQR_OK;
+}
+
 // ------------------------------------------------------------ reusable batch plans
 // A batch planned once and replayed as a CUDA graph: the tables are uploaded at creation,
 // and one run is the captured sequence of batch_enqueue plus the status and history
@@ -1313,6 +1408,12 @@ const char *tsqr::last_error_text() { return g_last_error.c_str(); }
 
 // Device memory a new batch can take now: what the driver reports free plus what the
 // library's stream-ordered pool holds reserved but unused (it keeps freed blocks cached).
+bool tsqr::debug_take_allocation_failure() {
+  for (int32_t f = g_fail_allocs.load(); f > 0; f = g_fail_allocs.load())
+    if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return true;
+  return false;
+}
+
 size_t tsqr::live_free_bytes() {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;

@@ -32,6 +32,27 @@ struct TileDesc {
   int32_t pad;
 };
 
+#ifdef __CUDACC__
+template <bool COH>
+__device__ __forceinline__ TileDesc load_tile(const TileDesc *t) {
+  if constexpr (COH) {
+    static_assert(sizeof(TileDesc) == 32, "four 8-byte loads");
+    const long long *q = reinterpret_cast<const long long *>(t);
+    const int2 a = __ldcg(reinterpret_cast<const int2 *>(q + 2)), b = __ldcg(reinterpret_cast<const int2 *>(q + 3));
+    TileDesc d;
+    d.row0 = __ldcg(q);
+    d.refl = __ldcg(q + 1);
+    d.nrows = a.x;
+    d.kind = a.y;
+    d.off = b.x;
+    d.pad = b.y;
+    return d;
+  } else {
+    return *t;
+  }
+}
+#endif
+
 struct JobDesc {
   int64_t piv_row;     // first of the n pivot rows
   int32_t tile_begin;  // index into the tile array
@@ -60,6 +81,29 @@ __host__ __device__ inline void refl_rows(int kind, int j, int ht, int &lo, int 
     if (hi < 0) hi = 0;
   }
 }
+
+// Loads of kernel inputs. The launch-per-call kernels read their inputs through the
+// read-only cache (COH = false); the resident kernel runs while the host replaces inputs
+// and tables at reused addresses, so it reads them through L2 only (COH = true), where
+// another SM's stale L1 line cannot be hit.
+#ifdef __CUDACC__
+template <bool COH>
+__device__ __forceinline__ double ld_input(const double *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ double2 ld_input(const double2 *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+// State another CTA of the same launch writes (COH) or written before the launch.
+template <bool COH>
+__device__ __forceinline__ double ld_state(const double *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+#endif
 
 // ----------------------------------------------------------------- factor kernel
 // R is the element type of the factorization (double; float for the leaves of the
@@ -238,6 +282,87 @@ int refine_rows_per_chunk(int n);
 size_t refine_smem_bytes(int n, int kb);
 cudaError_t launch_refine_batch(const RefineParams &p, int ntasks, size_t smem_bytes, cudaStream_t s);
 
+// -------------------------------------------------------- resident persistent kernel
+// The resident server keeps one persistent kernel on the GPU and admits requests into it
+// while it runs (resident.cu, server.cu). The host appends each admitted request's chain
+// jobs to a ring in device memory and then advances `tail`, both by copies on its upload
+// stream (the copy of `tail` lands after the entries and tables it publishes). CTAs claim
+// entries by compare-and-swap on `head`. Refinement tasks of mixed least-squares requests
+// are produced on the device: the CTA that finishes a request's factorization (or a step
+// of its refinement) reserves entries of a second ring (`dtail`), fills them and releases
+// each with its sequence number. A CTA with nothing to claim polls (bounded); when it has
+// seen no work for a while and no CTA is busy, it sets `quit` and the whole kernel ends;
+// the host launches it again when work arrives. Completion is written to mapped host
+// memory: the request's status, then its admission sequence number.
+struct ResCtl {
+  unsigned long long head, tail;    // host ring: next entry to claim, entries published
+  unsigned long long dhead, dtail;  // device ring: next entry to claim, entries reserved
+  int32_t busy;                     // CTAs running a claimed job
+  int32_t quit;                     // set by a CTA to end the launch (reset by the host)
+  int32_t stop;                     // set by the host: end once idle, without waiting
+  int32_t pad;
+};
+
+struct ResEntry {  // host ring: chain job `job` of the request in slot `slot`
+  int32_t slot, job;
+};
+
+struct ResTask {   // device ring: refinement task of (slot, group) for `step`
+  int32_t slot, group, step, task;
+  uint32_t seq;    // low 32 bits of (ring index + 1), written last
+  int32_t pad[3];
+};
+
+struct ResItemDev {  // one admitted request, in the slot table (device memory)
+  BatchInst inst;
+  const BatchJob *jobs;
+  const TileDesc *tiles;
+  int32_t *counters;   // arrival counters of the request's jobs
+  RefineInst *rinst;   // refinement groups (mixed least-squares requests)
+  int32_t *pending;    // groups still refining
+  int64_t m;
+  int32_t nchains, ngroups, nt, seq;
+};
+
+struct ResParams {
+  ResCtl *ctl;
+  const ResEntry *ring;
+  ResTask *dring;
+  const ResItemDev *items;
+  int32_t *hstatus, *hdone;  // mapped host memory, one word per slot
+  int32_t *err;              // device error word
+  unsigned long long ring_mask, dring_mask;  // capacities - 1 (powers of two)
+  int64_t idle_polls;        // consecutive empty polls before a CTA tries to end the launch
+  int64_t refine_rows;       // rows per refinement task
+  int32_t max_steps;
+  double tol;
+};
+
+cudaError_t launch_resident(const ResParams &p, int grid, size_t smem_bytes, cudaStream_t s);
+
+// One request planned for the resident kernel (host side, tsqr_api.cu): the batched
+// planner's tables for this one item and the size of its device block.
+struct ResidentPlan {
+  size_t bytes = 0;  // device block (workspaces, tables, counters)
+  size_t smem = 0;   // shared memory its jobs need
+  int cmax = 1;
+  int32_t nchains = 0, njobs = 0, ngroups = 0, nt = 0;
+  bool wy = false;
+  void *impl = nullptr;  // the planner's state (resident_plan_free)
+};
+tsqr_status resident_plan(const tsqr_batch_item &it, int32_t chain_tiles, ResidentPlan &out);
+// Binds the plan to its device block at `base` and enqueues on s the uploads that make it
+// runnable: tables, zeroed counters and status words, the library copy of B. Fills `dev`
+// (its slot, seq and pending pointer set by the caller afterwards).
+tsqr_status resident_upload(const ResidentPlan &p, char *base, cudaStream_t s, ResItemDev &dev);
+void resident_plan_free(ResidentPlan &p);
+// Dynamic shared memory of the resident kernel at `ctas_per_sm` CTAs per SM: the per-CTA
+// budget of the batched planner (a request fits when its plan's smem is at most this).
+size_t resident_smem_bytes(int ctas_per_sm);
+int64_t refine_rows_per_task();
+int32_t refine_max_steps();
+double refine_tolerance();
+
 // host side of the batched path (tsqr_api.cu), also driven by the server (server.cu)
 tsqr_status batch_solve_internal(const tsqr_batch_item *items, int32_t count, int32_t chain_tiles, int32_t arity,
                                  cudaStream_t s, int32_t *status, int32_t *status_async, double *info,
@@ -247,6 +372,9 @@ size_t batch_item_bytes(const tsqr_batch_item &it);  // device workspace estimat
 int32_t resolve_batch_prec(const tsqr_batch_item &it);  // TSQR_FP64 or TSQR_MIXED
 const char *last_error_text();
 size_t live_free_bytes();  // device memory free now, counting the pool's unused reserve
+// failure injection (tsqr_debug_fail_allocations): true while injected failures remain,
+// consuming one
+bool debug_take_allocation_failure();
 // the calling thread's error message (tsqr_last_error) for entry points outside tsqr_api.cu
 tsqr_status set_last_error(tsqr_status s, const char *fmt, ...);
 void clear_last_error();
