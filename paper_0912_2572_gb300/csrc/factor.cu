@@ -24,6 +24,7 @@
 //   * the reflector's scalar chain runs on its own warp, overlapped with the dot
 //     products (run_job below), and the column dealing rotates with the step so that no
 //     sub-partition's FP64 pipe carries more than its share.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -36,7 +37,7 @@ namespace tsqr {
 namespace {
 
 // ------------------------------------ FP32 chains: compact-WY panels on tensor cores
-// The same chain job as run_job_f32r (same register tile, same reflector storage and R),
+// The same chain job as run_job_f32s (same register tile, same reflector storage and R),
 // blocked: the columns are factored in panels of 16 (one register slot), each column step
 // touching only the panel's columns, and the panel's 16 reflectors are then applied to the
 // trailing columns at once in compact-WY form (paper §2.2: the blocked Householder update):
@@ -599,10 +600,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
           }
         } else {
           switch (in.n <= 16 ? 1 : (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8))) {
-            case 1: run_job_f32r<1>(fp, jd, smraw); break;
-            case 2: if (CMAX >= 2) run_job_f32r<(CMAX >= 2 ? 2 : 1)>(fp, jd, smraw); break;
-            case 4: if (CMAX >= 4) run_job_f32r<(CMAX >= 4 ? 4 : 1)>(fp, jd, smraw); break;
-            default: if (CMAX >= 8) run_job_f32r<(CMAX >= 8 ? 8 : 1)>(fp, jd, smraw); break;
+            case 1: run_job_f32s<1>(fp, jd, smraw); break;
+            case 2: if (CMAX >= 2) run_job_f32s<(CMAX >= 2 ? 2 : 1)>(fp, jd, smraw); break;
+            case 4: if (CMAX >= 4) run_job_f32s<(CMAX >= 4 ? 4 : 1)>(fp, jd, smraw); break;
+            default: if (CMAX >= 8) run_job_f32s<(CMAX >= 8 ? 8 : 1)>(fp, jd, smraw); break;
           }
         }
         // hand the chain's triangle to the FP64 tree storage
@@ -725,7 +726,12 @@ cudaError_t device_error_word(int32_t **ptr) {
 
 size_t factor_smem_bytes(int nc, int ldt, size_t elem) {
   const size_t ncp = (size_t)((nc + 7) & ~7);
-  if (elem == sizeof(float)) return sizeof(float) * ((size_t)kF32TileRows + 3 * ncp + (size_t)nc * (ncp + 1));
+  // FP32 register-tile chains: the one-barrier job's two tail buffers and scalar sets, or
+  // the compact-WY job's pivot column, Gram row and pivot rows; then the chain's R (the
+  // compact-WY job's panel buffers come on top, f32wy_smem_extra_bytes)
+  if (elem == sizeof(float))
+    return sizeof(float) * (std::max((size_t)2 * kF32TileRows + 8, (size_t)kF32TileRows + 3 * ncp) +
+                            (size_t)nc * (ncp + 1));
   return elem * ((size_t)nc * (size_t)ldt + 2 * ncp);
 }
 

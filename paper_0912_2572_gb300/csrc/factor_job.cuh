@@ -364,82 +364,147 @@ __device__ __forceinline__ void run_job(const FactorParamsT<double> &p, const Jo
 //     the leaf's first tile leaves it there, each triangle-on-tile step reads and
 //     rewrites its pivot row there, and R goes to global memory once, at the end;
 //   * the slot range of a step is the same for the two half-warps of a warp (their
-//     shuffles must match); a boundary slot is guarded per half-warp.
-template <int CPT, int T0>
-__device__ __forceinline__ void f32_gram(const float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j, int hw,
-                                         int hl, int nc, float *Pg) {
-  constexpr int NA = CPT - T0;
+//     shuffles must match); a boundary slot is guarded per half-warp;
+//   * one block barrier per column step. Every half-warp owns whole columns, so it needs
+//     nobody else's results to finish a step on them: it reduces its own Gram entries over
+//     its 16 lanes, computes its own coefficients and new pivot-row entries, and updates
+//     its own columns. Only the reflector crosses half-warps: the owner of column j + 1,
+//     once that column is updated, computes reflector j + 1 (tail norm, one rsqrt, one
+//     division) and publishes its tail and scalars, which the step's barrier makes
+//     visible. Tail and scalars are double-buffered by step parity (a buffer is rewritten
+//     only after the next barrier, when every reader is done with it). An earlier form of
+//     the job published the pivot column (barrier), reduced the Gram row into shared
+//     memory (barrier), let warp 0 turn it into coefficients (barrier) and then updated:
+//     bound by those hand-offs, not by its FMAs, it took about 2,700 cycles per step at
+//     n = 128 with one CTA per SM and 3,300 with two, against 1,950 and 2,500 here.
+
+// Lowest lane holding the total of value i after treduce16<C> (the total is replicated on
+// the 16 / C lanes above it).
+template <int C>
+__device__ __forceinline__ int treduce16_lane(int i) {
+  int l = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int half = (C >> s) >> 1;
+    if (half >= 1 && (i & half)) l |= (8 >> s);
+  }
+  return l;
+}
+
+// Register element v[t][r] with a runtime r (an unrolled select keeps v in registers).
+template <int CPT>
+__device__ __forceinline__ float f32s_get(const float (&v)[CPT][kF32Rpt], int t, int r) {
+  float out = 0.f;
+#pragma unroll
+  for (int tt = 0; tt < CPT; ++tt)
+#pragma unroll
+    for (int rr = 0; rr < kF32Rpt; ++rr)
+      if (tt == t && rr == r) out = v[tt][rr];
+  return out;
+}
+template <int CPT>
+__device__ __forceinline__ void f32s_set(float (&v)[CPT][kF32Rpt], int t, int r, float x) {
+#pragma unroll
+  for (int tt = 0; tt < CPT; ++tt)
+#pragma unroll
+    for (int rr = 0; rr < kF32Rpt; ++rr)
+      if (tt == t && rr == r) v[tt][rr] = x;
+}
+
+// Step j for this warp's NA highest column slots (t = CPT - NA .. CPT - 1; the lower slots
+// hold only columns <= j). x: the tail of pivot column j on this lane's rows; Rs: the chain's
+// R (row j is the pivot row of a triangle-on-tile step); for the leaf tile (GE) the pivot row
+// is the tile's own row j, which lane j mod 16 of each half-warp holds. pub(column) publishes
+// reflector j+1 from the registers of slot T0 (its owner half-warp only).
+template <int CPT, int NA, bool GE, typename PUB>
+__device__ __forceinline__ void f32s_step(float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j, int nc,
+                                          int hw, int hl, float *Rs, int ldr, float tau, float scale, float ts,
+                                          PUB &pub) {
+  constexpr int T0 = CPT - NA;
   constexpr int C = pow2ceil(NA);
-  float acc[C];
+  const int lane = threadIdx.x & 31;
+  float g[C];
 #pragma unroll
-  for (int t = 0; t < C; ++t) acc[t] = 0.f;
+  for (int i = 0; i < C; ++i) g[i] = 0.f;
 #pragma unroll
-  for (int t = 0; t < NA; ++t)
+  for (int i = 0; i < NA; ++i)
 #pragma unroll
-    for (int r = 0; r < kF32Rpt; ++r) acc[t] = fmaf(x[r], v[T0 + t][r], acc[t]);
+    for (int r = 0; r < kF32Rpt; ++r) g[i] = fmaf(x[r], v[T0 + i][r], g[i]);
   int idx;
-  const float s = treduce16<C, float>(acc, hl, idx);
-  const int c = hw + 16 * (T0 + idx);
-  if ((hl & (16 / C - 1)) == 0 && idx < NA && c >= j && c < nc) Pg[c] = s;
-}
-
-template <int CPT, int T0>
-__device__ __forceinline__ void f32_update(float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j, int hw,
-                                           int nc, const float *CF) {
+  const float gt = treduce16<C, float>(g, hl, idx);
+  const int c_me = hw + 16 * (T0 + idx);
+  const bool ok = idx < NA && c_me > j && c_me < nc;
+  if constexpr (GE) {  // the leaf tile's pivot row j goes to Rs, where every lane of the half-warp reads it
+    if (hl == (j & 15))
 #pragma unroll
-  for (int t = T0; t < CPT; ++t) {
-    const int c = hw + 16 * t;
-    if (c <= j || c >= nc) continue;  // the first slot may hold column j or an earlier one
-    const float cf = CF[c];
+      for (int i = 0; i < NA; ++i) {
+        const int c = hw + 16 * (T0 + i);
+        if (c > j && c < nc) Rs[j * ldr + c] = f32s_get<CPT>(v, T0 + i, j >> 4);
+      }
+    __syncwarp();
+  }
+  float cf_me = 0.f, pk = 0.f;
+  if (ok) {
+    const float p0 = Rs[j * ldr + c_me];
+    const float w = fmaf(scale, gt, p0);
+    cf_me = ts * w;
+    pk = fmaf(-tau, w, p0);
+  }
+  __syncwarp();  // every replica has read p0 before one of them overwrites it
+  if (ok && (hl & (16 / C - 1)) == 0) Rs[j * ldr + c_me] = pk;
+  if constexpr (GE) {  // the new pivot row back into the registers of its lane
+    __syncwarp();
+    if (hl == (j & 15))
 #pragma unroll
-    for (int r = 0; r < kF32Rpt; ++r) v[t][r] = fmaf(-cf, x[r], v[t][r]);
+      for (int i = 0; i < NA; ++i) {
+        const int c = hw + 16 * (T0 + i);
+        if (c > j && c < nc) f32s_set<CPT>(v, T0 + i, j >> 4, Rs[j * ldr + c]);
+      }
+  }
+  // the rank-1 update, slot T0 first: column j + 1 is always in its owner warp's lowest
+  // active slot, so reflector j + 1 is published before the other slots are updated. A
+  // slot's coefficient comes from the lane that reduced it.
+#pragma unroll
+  for (int i = 0; i < NA; ++i) {
+    const float cf = __shfl_sync(0xffffffffu, cf_me, (lane & 16) + treduce16_lane<C>(i));
+#pragma unroll
+    for (int r = 0; r < kF32Rpt; ++r) v[T0 + i][r] = fmaf(-cf, x[r], v[T0 + i][r]);
+    if (i == 0) pub(v[T0]);
   }
 }
 
-template <int CPT>
-__device__ __forceinline__ void f32_gram_dispatch(const float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j,
-                                                  int t0, int hw, int hl, int nc, float *Pg) {
-  switch (t0) {
-    case 0: f32_gram<CPT, 0>(v, x, j, hw, hl, nc, Pg); return;
-#define TSQR_F32_GRAM(T) \
-    case T: if (CPT > T) f32_gram<CPT, (CPT > T ? T : 0)>(v, x, j, hw, hl, nc, Pg); return;
-    TSQR_F32_GRAM(1) TSQR_F32_GRAM(2) TSQR_F32_GRAM(3) TSQR_F32_GRAM(4) TSQR_F32_GRAM(5) TSQR_F32_GRAM(6)
-    TSQR_F32_GRAM(7)
-#undef TSQR_F32_GRAM
-    default: return;
+template <int CPT, bool GE, typename PUB>
+__device__ __forceinline__ void f32s_dispatch(int na, float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j,
+                                              int nc, int hw, int hl, float *Rs, int ldr, float tau, float scale,
+                                              float ts, PUB &pub) {
+  switch (na) {
+#define TSQR_F32S_CASE(NA)                                                                      \
+    case NA:                                                                                    \
+      if constexpr (CPT >= NA) f32s_step<CPT, NA, GE>(v, x, j, nc, hw, hl, Rs, ldr, tau, scale, ts, pub); \
+      return;
+    TSQR_F32S_CASE(1) TSQR_F32S_CASE(2) TSQR_F32S_CASE(3) TSQR_F32S_CASE(4)
+    TSQR_F32S_CASE(5) TSQR_F32S_CASE(6) TSQR_F32S_CASE(7) TSQR_F32S_CASE(8)
+#undef TSQR_F32S_CASE
+    default: return;  // no column after j in this warp (never the owner of column j + 1)
   }
 }
 
-template <int CPT>
-__device__ __forceinline__ void f32_update_dispatch(float (&v)[CPT][kF32Rpt], const float (&x)[kF32Rpt], int j,
-                                                    int t0, int hw, int nc, const float *CF) {
-  switch (t0) {
-    case 0: f32_update<CPT, 0>(v, x, j, hw, nc, CF); return;
-#define TSQR_F32_UPD(T) \
-    case T: if (CPT > T) f32_update<CPT, (CPT > T ? T : 0)>(v, x, j, hw, nc, CF); return;
-    TSQR_F32_UPD(1) TSQR_F32_UPD(2) TSQR_F32_UPD(3) TSQR_F32_UPD(4) TSQR_F32_UPD(5) TSQR_F32_UPD(6)
-    TSQR_F32_UPD(7)
-#undef TSQR_F32_UPD
-    default: return;
-  }
-}
-
-// One chain job (a leaf's GEQRT tile, then TSQRT tiles; at most 16 * CPT columns) with
-// register tiles. Shared memory: the pivot column (kF32TileRows), the Gram row (ncp),
-// two pivot-row buffers for the leaf tile (2 ncp) and the chain's R (n rows of ncp + 1).
+// One chain job with register tiles and one barrier per column step. Shared memory: two
+// pivot-tail buffers (2 kF32TileRows), two scalar sets (8) and the chain's R (n rows of
+// ncp + 1), within factor_smem_bytes(nc, ., 4).
 template <int CPT, bool COH = false>
-__device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, const JobDesc job, unsigned char *smraw) {
+__device__ __forceinline__ void run_job_f32s(const FactorParamsT<float> &p, const JobDesc job, unsigned char *smraw) {
   float *sm = reinterpret_cast<float *>(smraw);
   const int n = p.n, nc = p.nc;
   const int ncp = (nc + 7) & ~7;
-  float *xcol = sm;
-  float *PC = xcol + kF32TileRows;
-  float *PVb = PC + ncp;
   const int ldr = ncp + 1;    // odd: the end-of-chain column walk is conflict-free
-  float *Rs = PVb + 2 * ncp;  // R(i, c) at Rs[i * ldr + c]
+  float *xb = sm;             // tails of pivot columns j (buffer j mod 2)
+  float *sb = xb + 2 * kF32TileRows;  // tau, scale, tau * scale of reflector j (buffer j mod 2)
+  float *Rs = sb + 8;         // R(i, c) at Rs[i * ldr + c]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int hw = tid >> 4, hl = tid & 15;
   const int hw_hi = 2 * warp + 1;  // the larger column offset of the warp's half-warps
+  const unsigned hmask = 0xffffu << (lane & 16);
   const int64_t pr = job.piv_row;
   float v[CPT][kF32Rpt];
 
@@ -448,7 +513,6 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
     const int ht = td.nrows;
     const int64_t r0 = td.row0;
     const bool ge = (td.kind == GEQRT);
-    // load the tile (A is FP64, rounded here); rows past ht and columns past nc are 0
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
       const int c = hw + 16 * t;
@@ -462,99 +526,60 @@ __device__ __forceinline__ void run_job_f32r(const FactorParamsT<float> &p, cons
         v[t][r] = val;
       }
     }
+    __syncthreads();  // the previous tile's readers of the buffers are done
+
+    // reflector jn (column jn's owner half-warp, given the registers of column jn): its
+    // tail, norm and scalars, published
+    int jn = 0;
+    auto pub = [&](float (&w)[kF32Rpt]) {
+      if (jn >= n || hw != (jn & 15)) return;
+      const int b = jn & 1, rn = jn >> 4;
+      // the tail (rows below the pivot of a leaf tile, all rows of a tile under a
+      // triangle) goes out as it is summed
+      float s2 = 0.f, wn = 0.f;
+#pragma unroll
+      for (int r = 0; r < kF32Rpt; ++r) {
+        float val = w[r];
+        if (r == rn) wn = val;
+        if (ge && hl + 16 * r <= jn) val = 0.f;
+        s2 = fmaf(val, val, s2);
+        xb[b * kF32TileRows + hl + 16 * r] = val;
+      }
+      const float alpha = ge ? __shfl_sync(hmask, wn, (lane & 16) + (jn & 15)) : Rs[jn * ldr + jn];
+#pragma unroll
+      for (int m = 8; m >= 1; m >>= 1) s2 += __shfl_xor_sync(hmask, s2, m);
+      const Refl<float> rf = reflector<float>(alpha, s2);
+      if (hl == 0) {
+        sb[4 * b] = rf.tau;
+        sb[4 * b + 1] = rf.scale;
+        sb[4 * b + 2] = rf.ts;
+        p.tau[td.refl + jn] = rf.tau;
+        p.scl[td.refl + jn] = rf.scale;
+        if (!ge) Rs[jn * ldr + jn] = rf.beta;
+      }
+      if (ge && hl == (jn & 15))
+#pragma unroll
+        for (int r = 0; r < kF32Rpt; ++r)
+          if (r == rn) w[r] = rf.beta;
+    };
+    pub(v[0]);
     __syncthreads();
 
     for (int j = 0; j < n; ++j) {
-      const int tj = j >> 4, jl = j & 15;
-      float *PV = ge ? PVb + (j & 1) * ncp : Rs + j * ldr;
-      // (A) publish the pivot column (its owner half-warp) and, for the leaf tile, the
-      //     pivot row (its owner lane in every half-warp)
-      if (hw == jl) {
-#pragma unroll
-        for (int t = 0; t < CPT; ++t)
-          if (t == tj)
-#pragma unroll
-            for (int r = 0; r < kF32Rpt; ++r) xcol[hl + 16 * r] = v[t][r];
-      }
-      if (ge && hl == jl) {
-#pragma unroll
-        for (int r = 0; r < kF32Rpt; ++r)
-          if (r == tj)
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) {
-              const int c = hw + 16 * t;
-              if (c >= j && c < nc) PV[c] = v[t][r];
-            }
-      }
-      __syncthreads();
-      // (B) the tail of column j on this lane's rows, then the Gram row
+      const int b = j & 1;
       float x[kF32Rpt];
 #pragma unroll
-      for (int r = 0; r < kF32Rpt; ++r) {
-        const int i = hl + 16 * r;
-        x[r] = (ge && i <= j) ? 0.f : xcol[i];
-      }
-      {
-        const int d = j - hw_hi;
-        f32_gram_dispatch<CPT>(v, x, j, d <= 0 ? 0 : (d + 15) >> 4, hw, hl, nc, PC);
-      }
+      for (int r = 0; r < kF32Rpt; ++r) x[r] = xb[b * kF32TileRows + hl + 16 * r];
+      const float tau = sb[4 * b], scale = sb[4 * b + 1], ts = sb[4 * b + 2];
+      jn = j + 1;
+      const int d = j - hw_hi;
+      const int na = CPT - (d < 0 ? 0 : (d >> 4) + 1);
+      if (ge)
+        f32s_dispatch<CPT, true>(na, v, x, j, nc, hw, hl, Rs, ldr, tau, scale, ts, pub);
+      else
+        f32s_dispatch<CPT, false>(na, v, x, j, nc, hw, hl, Rs, ldr, tau, scale, ts, pub);
       __syncthreads();
-      // (C) warp 0: the reflector's scalars, the update coefficients and the new pivot row.
-      //     Up to 64 columns all loads go first (the columns are independent, and stores
-      //     between loads would serialize them: about 6% faster chains at n <= 64); at 128
-      //     columns the extra live registers cost more than that.
-      if (warp == 0) {
-        const Refl<float> rf = reflector<float>(PV[j], PC[j]);
-        if constexpr (CPT <= 4) {
-          constexpr int QN = (16 * CPT + 31) / 32;
-          float pk[QN], g[QN];
-#pragma unroll
-          for (int q = 0; q < QN; ++q) {
-            const int c = j + 1 + lane + 32 * q;
-            pk[q] = (c < nc) ? PV[c] : 0.f;
-            g[q] = (c < nc) ? PC[c] : 0.f;
-          }
-#pragma unroll
-          for (int q = 0; q < QN; ++q) {
-            const int c = j + 1 + lane + 32 * q;
-            const float w = fmaf(rf.scale, g[q], pk[q]);
-            if (c < nc) {
-              PC[c] = rf.ts * w;
-              PV[c] = fmaf(-rf.tau, w, pk[q]);
-            }
-          }
-        } else {
-          for (int c = j + 1 + lane; c < nc; c += 32) {
-            const float pk = PV[c];
-            const float w = fmaf(rf.scale, PC[c], pk);
-            PC[c] = rf.ts * w;
-            PV[c] = fmaf(-rf.tau, w, pk);
-          }
-        }
-        if (lane == 0) {
-          PV[j] = rf.beta;
-          p.tau[td.refl + j] = rf.tau;
-          p.scl[td.refl + j] = rf.scale;
-        }
-      }
-      __syncthreads();
-      // (D) the rank-1 update; on the leaf tile the owner lane of row j takes the new row
-      {
-        const int d = j + 1 - hw_hi;
-        f32_update_dispatch<CPT>(v, x, j, d <= 0 ? 0 : (d + 15) >> 4, hw, nc, PC);
-      }
-      if (ge && hl == jl) {
-#pragma unroll
-        for (int r = 0; r < kF32Rpt; ++r)
-          if (r == tj)
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) {
-              const int c = hw + 16 * t;
-              if (c >= j && c < nc) v[t][r] = PV[c];
-            }
-      }
     }
-    __syncthreads();
     // the leaf tile's R (rows < n, upper part; right-hand-side columns in full) becomes
     // the chain's R in shared memory
     if (ge) {

@@ -176,10 +176,10 @@ __device__ void run_chain(const ResParams &p, int slot, int jb, unsigned char *s
       fp.nc = in.n;
       fp.ldt = in.ldt;
       switch (in.n <= 16 ? 1 : (in.n <= 32 ? 2 : (in.n <= 64 ? 4 : 8))) {
-        case 1: run_job_f32r<1, true>(fp, jd, smraw); break;
-        case 2: run_job_f32r<2, true>(fp, jd, smraw); break;
-        case 4: run_job_f32r<4, true>(fp, jd, smraw); break;
-        default: run_job_f32r<8, true>(fp, jd, smraw); break;
+        case 1: run_job_f32s<1, true>(fp, jd, smraw); break;
+        case 2: run_job_f32s<2, true>(fp, jd, smraw); break;
+        case 4: run_job_f32s<4, true>(fp, jd, smraw); break;
+        default: run_job_f32s<8, true>(fp, jd, smraw); break;
       }
       // hand the chain's triangle to the FP64 tree storage
       const float *Vs = static_cast<const float *>(in.V) + bj.piv_row;
