@@ -668,6 +668,10 @@ cudaError_t launch_factor_c(const FactorParamsT<double> &p, int njobs, cudaStrea
 
 cudaError_t launch_factor_any(const FactorParamsT<double> &p, int njobs, int ctas_per_sm, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
+  // up to 16 columns (one column slot per half-warp) a step keeps at most half of a CTA's
+  // worker warps busy: the 64-register build lets a fourth CTA join where its tile fits
+  // (the plan, made for three, is unchanged)
+  if (ctas_per_sm >= 3 && p.nc <= 16) return launch_factor_t<1, 4>(p, njobs, s);
   if (ctas_per_sm >= 3) return launch_factor_c<3>(p, njobs, s);
   return launch_factor_c<2>(p, njobs, s);
 }

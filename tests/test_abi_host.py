@@ -212,6 +212,9 @@ def test_tile_capacity_choice(lib):
     # the leaf height caps the tile
     info, _, _ = describe(lib, 100_000, 16, 100, 2, 0)
     assert info["tile_rows"] == 100
+    # small widths: the three-CTA plan with 512-row tiles, the apply kernels' cap
+    info, _, _ = describe(lib, 1_000_000, 8, 1024, 2, 2)
+    assert info["cps"] == 3 and info["tile_rows"] == 512
 
 
 def test_server_entry_points_reject_bad_arguments(lib):

@@ -64,11 +64,12 @@ def test_fp64_peak_probe_is_plausible(cuda_lib):
     assert 0.3 < tf < 3.0
 
 
-@pytest.mark.parametrize("n", [1, 8, 16, 24, 32, 48, 64])
+@pytest.mark.parametrize("n", [1, 8, 16, 17, 24, 32, 48, 64])
 def test_three_cta_plan_widths(cuda_lib, n):
     """The default tile of the widths that take three CTAs per SM (tiles of at least 2n
-    rows), on a ragged m: R and the thin Q against the oracle, and the plan is the
-    three-CTA one."""
+    rows; up to 16 columns the chain launch runs the 64-register build, which lets a fourth
+    CTA join where its tile fits), on a ragged m: R and the thin Q against the oracle, and
+    the plan is the three-CTA one."""
     import paper_0912_2572_gb300 as ts
     m = 60_013
     info = ts.plan_describe(m, n, 1 << 20)
