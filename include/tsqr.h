@@ -512,7 +512,8 @@ tsqr_status tsqr_server_destroy(tsqr_server *srv);
 
 /*
  * tsqr_set_mixed_wy_min_n — the FP32 leaf chains of mixed-precision items (tsqr_lstsq with
- * TSQR_MIXED, batch and server items) with at least `min_n` columns (and more than 16)
+ * TSQR_MIXED, batch items and the launching server's; the resident server always runs the
+ * unblocked chains) with at least `min_n` columns (and more than 16)
  * are factored in panels of 16 columns whose 16 reflectors are applied to the trailing
  * columns at once in compact-WY form, I - V T V^T (paper §2.2's blocked Householder
  * update), with V^T C and V (T^T W) on the tensor cores as 3xTF32 products (FP32 operands
