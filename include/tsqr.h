@@ -503,6 +503,15 @@ tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t str
  */
 tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, int32_t ctas_per_sm,
                                         int32_t idle_us, tsqr_server **srv);
+
+/*
+ * tsqr_debug_resident_ring_entries — test hook: both work rings of resident servers created
+ * after the call hold `entries` entries (a power of two >= 16; 0 restores the default of
+ * 2^20), so that a test can make them wrap around within a few requests. A request with
+ * more chain jobs or refinement tasks per step than a ring holds is refused at submission
+ * (TSQR_ERR_UNSUPPORTED). Errors: TSQR_ERR_ARG for any other value.
+ */
+tsqr_status tsqr_debug_resident_ring_entries(int64_t entries);
 tsqr_status tsqr_server_submit(tsqr_server *srv, const tsqr_batch_item *item, int64_t *ticket);
 tsqr_status tsqr_server_poll(tsqr_server *srv, int32_t max, int64_t *tickets, double *latency_s,
                              int32_t *status, int32_t *count);

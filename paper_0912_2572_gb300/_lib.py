@@ -66,6 +66,7 @@ SIGNATURES = {
     "tsqr_batch_plan_destroy": (_i32, [_vp]),
     "tsqr_server_create": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "tsqr_server_create_resident": (_i32, [_i64, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    "tsqr_debug_resident_ring_entries": (_i32, [_i64]),
     "tsqr_server_submit": (_i32, [_vp, ctypes.POINTER(BatchItem), ctypes.POINTER(_i64)]),
     "tsqr_server_poll": (_i32, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),

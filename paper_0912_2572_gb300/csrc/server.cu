@@ -102,6 +102,9 @@ class Arena {
 constexpr int32_t kResSlots = 4096;
 constexpr unsigned long long kRingCap = 1ull << 20;   // host ring entries (chain jobs)
 constexpr unsigned long long kDringCap = 1ull << 20;  // device ring entries (refinement tasks)
+// Test hook (tsqr_debug_resident_ring_entries): both rings of resident servers created
+// afterwards get this many entries (0: the defaults above), so that tests wrap them.
+std::atomic<unsigned long long> g_ring_entries{0};
 
 struct ResLive {
   SrvReq req;
@@ -129,6 +132,7 @@ struct ResState {
   size_t smem = 0;
   int grid = 0;
   int64_t idle_polls = 64;
+  unsigned long long ring_cap = kRingCap, dring_cap = kDringCap;  // powers of two
   unsigned long long tail = 0;
   int64_t dtasks = 0, nlive = 0, max_live = 0, launches = 0;
   int32_t next_seq = 0;
@@ -272,8 +276,8 @@ static bool res_admit(tsqr_server *S, ResState &R) {
   for (const ResLive &L : R.live)
     if (L.active) oldest = std::min(oldest, L.first);
   const int64_t need_d = (int64_t)p.ngroups * p.nt;
-  if (R.free_slots.empty() || R.tail + (unsigned long long)p.nchains - oldest > kRingCap ||
-      R.dtasks + need_d > (int64_t)kDringCap)
+  if (R.free_slots.empty() || R.tail + (unsigned long long)p.nchains - oldest > R.ring_cap ||
+      R.dtasks + need_d > (int64_t)R.dring_cap)
     return false;
   size_t off = 0;
   if (!R.alloc.alloc(p.bytes, off)) {
@@ -304,8 +308,8 @@ static bool res_admit(tsqr_server *S, ResState &R) {
     for (int32_t j = 0; j < p.nchains; ++j) ent[(size_t)j] = {slot, j};
     size_t done = 0;
     while (e == cudaSuccess && done < ent.size()) {
-      const unsigned long long pos = (R.tail + done) & (kRingCap - 1);
-      const size_t cnt = std::min(ent.size() - done, (size_t)(kRingCap - pos));
+      const unsigned long long pos = (R.tail + done) & (R.ring_cap - 1);
+      const size_t cnt = std::min(ent.size() - done, (size_t)(R.ring_cap - pos));
       e = res_copy(R.ring + pos, ent.data() + done, sizeof(tsqr::ResEntry) * cnt, R.up);
       done += cnt;
     }
@@ -353,8 +357,8 @@ static void resident_loop(tsqr_server *S) {
   kp.hstatus = R.dstatus;
   kp.hdone = R.ddone;
   kp.err = R.err;
-  kp.ring_mask = kRingCap - 1;
-  kp.dring_mask = kDringCap - 1;
+  kp.ring_mask = R.ring_cap - 1;
+  kp.dring_mask = R.dring_cap - 1;
   kp.idle_polls = R.idle_polls;
   kp.refine_rows = tsqr::refine_rows_per_task();
   kp.max_steps = tsqr::refine_max_steps();
@@ -495,8 +499,9 @@ tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, 
   for (int32_t q = kResSlots - 1; q >= 0; --q) R.free_slots.push_back(q);
   e = cudaMalloc(&R.arena, arena);
   if (e == cudaSuccess) e = cudaMalloc(&R.ctl, sizeof(tsqr::ResCtl));
-  if (e == cudaSuccess) e = cudaMalloc(&R.ring, sizeof(tsqr::ResEntry) * kRingCap);
-  if (e == cudaSuccess) e = cudaMalloc(&R.dring, sizeof(tsqr::ResTask) * kDringCap);
+  if (const unsigned long long cap = g_ring_entries.load()) R.ring_cap = R.dring_cap = cap;
+  if (e == cudaSuccess) e = cudaMalloc(&R.ring, sizeof(tsqr::ResEntry) * R.ring_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&R.dring, sizeof(tsqr::ResTask) * R.dring_cap);
   if (e == cudaSuccess) e = cudaMalloc(&R.items, sizeof(tsqr::ResItemDev) * kResSlots);
   if (e == cudaSuccess) e = cudaHostAlloc(&R.hdone, sizeof(int32_t) * kResSlots, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostAlloc(&R.hstatus, sizeof(int32_t) * kResSlots, cudaHostAllocMapped);
@@ -507,7 +512,7 @@ tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, 
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&R.ks, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R.kev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(R.ctl, 0, sizeof(tsqr::ResCtl), R.up);
-  if (e == cudaSuccess) e = cudaMemsetAsync(R.dring, 0, sizeof(tsqr::ResTask) * kDringCap, R.up);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.dring, 0, sizeof(tsqr::ResTask) * R.dring_cap, R.up);
   if (e == cudaSuccess) e = cudaStreamSynchronize(R.up);  // before any launch
   if (e != cudaSuccess) {
     const tsqr_status st = tsqr::set_last_error(e == cudaErrorMemoryAllocation ? TSQR_ERR_OOM : TSQR_ERR_CUDA,
@@ -521,6 +526,12 @@ tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, 
   R.alloc.reset(arena);
   S->worker = std::thread(resident_loop, S);
   *out = S;
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_debug_resident_ring_entries(int64_t entries) {
+  if (entries != 0 && (entries < 16 || (entries & (entries - 1)) != 0)) return TSQR_ERR_ARG;
+  g_ring_entries.store((unsigned long long)entries);
   return TSQR_OK;
 }
 
@@ -541,6 +552,10 @@ tsqr_status tsqr_server_submit(tsqr_server *S, const tsqr_batch_item *item, int6
     if (p->bytes > S->res->arena_bytes)
       return tsqr::set_last_error(TSQR_ERR_UNSUPPORTED, "request needs %zu bytes of the %zu-byte arena", p->bytes,
                                   S->res->arena_bytes);
+    if ((unsigned long long)p->nchains > S->res->ring_cap ||
+        (unsigned long long)p->ngroups * (unsigned long long)p->nt > S->res->dring_cap)
+      return tsqr::set_last_error(TSQR_ERR_UNSUPPORTED, "request has more jobs (%d chains, %d tasks) than a ring holds",
+                                  p->nchains, p->ngroups * p->nt);
     r.bytes = p->bytes;
     r.plan = p;
   }

@@ -159,3 +159,33 @@ def test_resident_singular_and_failure_injection(cuda_lib):
         assert np.array_equal(to_host(R), R1)
         if X1 is not None:
             assert np.array_equal(to_host(X), X1)
+
+
+def test_resident_rings_wrap_around(cuda_lib):
+    """Rings of 16 entries (the test hook): 40 FP64 and mixed requests of a few chain jobs
+    and refinement tasks each wrap both rings several times; admission waits for room in
+    them; every result equals the request solved alone. A request with more chain jobs than
+    a ring holds is refused at submission."""
+    import paper_0912_2572_gb300 as ts
+    lib = cuda_lib
+    reqs = mixed_requests(40, 27, mlo=2000, mhi=20_000, ns=(16, 32, 64))
+    items = [_item(A, B, ts.MIXED if i % 2 else ts.FP64, want_r=False) for i, (A, B) in enumerate(reqs)]
+    try:
+        assert lib.tsqr_debug_resident_ring_entries(16) == 0
+        assert lib.tsqr_debug_resident_ring_entries(24) == 1  # not a power of two
+        with ts.Server(resident=True, chain_tiles=8, idle_us=2_000) as srv:
+            outs, done = _serve(srv, items)
+            big = inputs.gaussian(200_000, 16, 28)
+            with pytest.raises(ts.TSQRError) as e:
+                srv.submit(_item(big, None, ts.MIXED, want_r=True))
+            assert e.value.status == 6
+            stats = srv.stats()
+    finally:
+        lib.tsqr_debug_resident_ring_entries(0)
+    assert all(st == 0 for _, st in done.values())
+    assert stats["completed"] == len(items) and stats["bytes_in_flight"] == 0
+    for t, (i, (_, X)) in outs.items():
+        assert np.array_equal(to_host(X), _alone(items[i], 8)[1]), f"request {i}"
+        if i % 8 == 0:
+            A, B = reqs[i]
+            assert rel(to_host(X), oracle.lstsq(A, B)) <= 1e-10
