@@ -94,7 +94,9 @@ def parse(argv=None):
     p.add_argument("--cluster", type=int, default=1,
                    help="1: the binary tree's latency-bound levels in thread-block clusters (TSQR_CLUSTER)")
     p.add_argument("--decades", type=float, default=6.0)
-    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=20,
+                   help="end-to-end steps (the pipeline's fill and drain, one input and one output "
+                        "copy that nothing overlaps, are spread over them)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="skip the factorization autotuner report")
