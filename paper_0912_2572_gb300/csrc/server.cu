@@ -333,9 +333,14 @@ static bool res_admit(tsqr_server *S, ResState &R) {
   return true;
 }
 
-// Every request in flight fails (the kernel reported a lost work entry, or a launch
-// failed); the rings start over empty.
+// Every request in flight fails (the kernel reported a lost work entry, or a launch or an
+// upload failed); the rings start over empty once no launch is running (a running one ends
+// by itself within its bounded polls: nothing new is published for it).
 static void res_fail_all(tsqr_server *S, ResState &R, int32_t status) {
+  if (R.running) {
+    cudaEventSynchronize(R.kev);
+    R.running = false;
+  }
   cudaStreamSynchronize(R.up);
   for (int32_t q = 0; q < (int32_t)R.live.size(); ++q)
     if (R.live[q].active) res_finish(S, R, q, status);
