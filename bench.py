@@ -42,12 +42,13 @@ FP64_SM_FLOPS_PER_CLK = 4.0   # 2 DFMA per clock per SM on GB300 (measured: 1.20
 # buffers; the steps' kernels are ordered one after another by an event chain, so one
 # step's result copy and the next steps' input copies overlap the kernels in between.
 # Host-device copy bandwidth on the GB300 machines varies from run to run (a 2 GB copy takes
-# 10 ms or, now and then, 30-60 ms), and a third stream absorbs more of that: measured at
-# 4M x 64 on one box through tsqr_qr_solve_host, 84.3 / 79.9 ms per step with three
-# streams against 94.4 / 86.7 / 89.8 / 90.4 with two (without the event chain: 89.6 with
-# two, because concurrent steps finish together and their copies then queue while the GPU
-# idles; 101.8 with one stream)
-E2E_SLOTS = 3
+# 10 ms or, now and then, 30-60 ms), and more streams absorb more of that: measured at
+# 4M x 64 through tsqr_qr_solve_host, on one box 84.3 / 79.9 ms per step with three streams
+# against 94.4 / 86.7 / 89.8 / 90.4 with two; on another, 20 steps each, 87.2 / 92.5 /
+# 85.7 / 82.1 with four against 99.7 / 97.4 / 80.7 / 87.6 with three (without the event
+# chain: 89.6 with two, because concurrent steps finish together and their copies then
+# queue while the GPU idles; 101.8 with one stream)
+E2E_SLOTS = 4
 CHAIN_DRAM_BYTES_PER_ROW_N64 = (547.427328e6 + 502.893824e6) / 1048576  # ncu, chain launch at m = 1M, n = 64
 
 
