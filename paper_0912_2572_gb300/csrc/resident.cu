@@ -70,7 +70,7 @@ struct Claim {
 };
 
 // Thread 0 of a CTA: the next job, or kClaimExit. Refinement tasks come first (they end
-// requests already under way), then new chain jobs.
+// requests already under way), then chain jobs of short requests, then of long ones.
 __device__ Claim claim_next(const ResParams &p) {
   ResCtl *ctl = p.ctl;
   unsigned sleep_ns = 2000;
@@ -94,14 +94,22 @@ __device__ Claim claim_next(const ResParams &p) {
       }
       return {kClaimRefine, __ldcg(&e->slot), __ldcg(&e->group), __ldcg(&e->step), __ldcg(&e->task)};
     }
-    const unsigned long long h = *(volatile unsigned long long *)&ctl->head;
-    const unsigned long long t = ld_acquire_u64(&ctl->tail);
-    if (h < t) {
-      if (atomicCAS(&ctl->head, h, h + 1) != h) continue;
+    // chain jobs: the ring of short requests first
+    bool lost = false;
+    for (int c = 0; c < 2 && !lost; ++c) {
+      const unsigned long long h = *(volatile unsigned long long *)&ctl->head[c];
+      const unsigned long long t = ld_acquire_u64(&ctl->tail[c]);
+      if (h >= t) continue;
+      if (atomicCAS(&ctl->head[c], h, h + 1) != h) {
+        lost = true;  // another CTA took it: poll again from the top
+        break;
+      }
       atomicAdd(&ctl->busy, 1);
-      const int2 e = __ldcg(reinterpret_cast<const int2 *>(p.ring + (h & p.ring_mask)));
+      const ResEntry *ring = p.ring + (unsigned long long)c * (p.ring_mask + 1);
+      const int2 e = __ldcg(reinterpret_cast<const int2 *>(ring + (h & p.ring_mask)));
       return {kClaimChain, e.x, e.y, 0, 0};
     }
+    if (lost) continue;
     // nothing to claim
     ++empty;
     const bool stop = *(volatile int32_t *)&ctl->stop != 0;
@@ -109,8 +117,10 @@ __device__ Claim claim_next(const ResParams &p) {
       // end the launch only when no CTA is busy and both rings are empty (busy first: a
       // job's refinement tasks are reserved before its CTA leaves `busy`)
       const int b = ld_acquire_i32(&ctl->busy);
-      const bool empty_rings = *(volatile unsigned long long *)&ctl->dhead == *(volatile unsigned long long *)&ctl->dtail &&
-                               *(volatile unsigned long long *)&ctl->head == ld_acquire_u64(&ctl->tail);
+      auto vol = [](const unsigned long long *q) { return *(const volatile unsigned long long *)q; };
+      const bool empty_rings = vol(&ctl->dhead) == vol(&ctl->dtail) &&
+                               vol(&ctl->head[0]) == ld_acquire_u64(&ctl->tail[0]) &&
+                               vol(&ctl->head[1]) == ld_acquire_u64(&ctl->tail[1]);
       if ((b == 0 && empty_rings) || polls >= kIdleGiveUp) {
         atomicExch(&ctl->quit, 1);
         return {kClaimExit, 0, 0, 0, 0};

@@ -111,7 +111,8 @@ struct ResLive {
   size_t off = 0, bytes = 0;
   int32_t seq = 0;
   bool active = false;
-  unsigned long long first = 0;  // its first host-ring entry
+  int cls = 0;                   // its host ring (0: at most kResSmallChains chain jobs)
+  unsigned long long first = 0;  // its first entry in that ring
   int64_t dtasks = 0;            // device-ring entries it can hold at once
 };
 
@@ -133,7 +134,8 @@ struct ResState {
   int grid = 0;
   int64_t idle_polls = 64;
   unsigned long long ring_cap = kRingCap, dring_cap = kDringCap;  // powers of two
-  unsigned long long tail = 0;
+  unsigned long long tail[2] = {0, 0};
+  bool published[2] = {false, false};  // a ring's tail moved since its last copy
   int64_t dtasks = 0, nlive = 0, max_live = 0, launches = 0;
   int32_t next_seq = 0;
   std::vector<ResLive> live;
@@ -272,11 +274,12 @@ static cudaError_t res_copy(void *dst, const void *src, size_t bytes, cudaStream
 static bool res_admit(tsqr_server *S, ResState &R) {
   SrvReq r = S->pending.front();
   const tsqr::ResidentPlan &p = *r.plan;
-  unsigned long long oldest = R.tail;
+  const int cls = p.nchains <= tsqr::kResSmallChains ? 0 : 1;
+  unsigned long long oldest = R.tail[cls];  // entries before it belong to completed requests
   for (const ResLive &L : R.live)
-    if (L.active) oldest = std::min(oldest, L.first);
+    if (L.active && L.cls == cls) oldest = std::min(oldest, L.first);
   const int64_t need_d = (int64_t)p.ngroups * p.nt;
-  if (R.free_slots.empty() || R.tail + (unsigned long long)p.nchains - oldest > R.ring_cap ||
+  if (R.free_slots.empty() || R.tail[cls] + (unsigned long long)p.nchains - oldest > R.ring_cap ||
       R.dtasks + need_d > (int64_t)R.dring_cap)
     return false;
   size_t off = 0;
@@ -306,11 +309,12 @@ static bool res_admit(tsqr_server *S, ResState &R) {
     // the request's chain jobs into the host ring (two pieces where it wraps)
     std::vector<tsqr::ResEntry> ent((size_t)p.nchains);
     for (int32_t j = 0; j < p.nchains; ++j) ent[(size_t)j] = {slot, j};
+    tsqr::ResEntry *ring = R.ring + (size_t)cls * R.ring_cap;
     size_t done = 0;
     while (e == cudaSuccess && done < ent.size()) {
-      const unsigned long long pos = (R.tail + done) & (R.ring_cap - 1);
+      const unsigned long long pos = (R.tail[cls] + done) & (R.ring_cap - 1);
       const size_t cnt = std::min(ent.size() - done, (size_t)(R.ring_cap - pos));
-      e = res_copy(R.ring + pos, ent.data() + done, sizeof(tsqr::ResEntry) * cnt, R.up);
+      e = res_copy(ring + pos, ent.data() + done, sizeof(tsqr::ResEntry) * cnt, R.up);
       done += cnt;
     }
   }
@@ -319,7 +323,8 @@ static bool res_admit(tsqr_server *S, ResState &R) {
   L.off = off;
   L.bytes = p.bytes;
   L.seq = seq;
-  L.first = R.tail;
+  L.cls = cls;
+  L.first = R.tail[cls];
   L.dtasks = need_d;
   L.active = true;
   R.dtasks += need_d;
@@ -329,7 +334,8 @@ static bool res_admit(tsqr_server *S, ResState &R) {
     res_finish(S, R, slot, (int32_t)(st != TSQR_OK ? st : TSQR_ERR_CUDA));
     return true;
   }
-  R.tail += (unsigned long long)p.nchains;
+  R.tail[cls] += (unsigned long long)p.nchains;
+  R.published[cls] = true;
   return true;
 }
 
@@ -348,7 +354,8 @@ static void res_fail_all(tsqr_server *S, ResState &R, int32_t status) {
   const int32_t zero = 0;
   cudaMemcpyAsync(R.err, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, R.ks);
   cudaStreamSynchronize(R.ks);
-  R.tail = 0;
+  R.tail[0] = R.tail[1] = 0;
+  R.published[0] = R.published[1] = false;
 }
 
 static void resident_loop(tsqr_server *S) {
@@ -390,14 +397,12 @@ static void resident_loop(tsqr_server *S) {
       progress = true;
     }
     // admission into the running kernel
-    bool published = false;
-    while (!S->pending.empty() && res_admit(S, R)) {
-      published = true;
-      progress = true;
-    }
-    if (published) {
-      const unsigned long long t = R.tail;  // staged by the copy before the call returns
-      if (res_copy(&R.ctl->tail, &t, sizeof(t), R.up) != cudaSuccess) res_fail_all(S, R, (int32_t)TSQR_ERR_CUDA);
+    while (!S->pending.empty() && res_admit(S, R)) progress = true;
+    for (int c = 0; c < 2; ++c) {
+      if (!R.published[c]) continue;
+      R.published[c] = false;
+      const unsigned long long t = R.tail[c];  // staged by the copy before the call returns
+      if (res_copy(&R.ctl->tail[c], &t, sizeof(t), R.up) != cudaSuccess) res_fail_all(S, R, (int32_t)TSQR_ERR_CUDA);
     }
     // a launch whenever requests are in flight and none is running
     if (!R.running && R.nlive > 0) {
@@ -505,7 +510,7 @@ tsqr_status tsqr_server_create_resident(int64_t max_bytes, int32_t chain_tiles, 
   e = cudaMalloc(&R.arena, arena);
   if (e == cudaSuccess) e = cudaMalloc(&R.ctl, sizeof(tsqr::ResCtl));
   if (const unsigned long long cap = g_ring_entries.load()) R.ring_cap = R.dring_cap = cap;
-  if (e == cudaSuccess) e = cudaMalloc(&R.ring, sizeof(tsqr::ResEntry) * R.ring_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&R.ring, sizeof(tsqr::ResEntry) * 2 * R.ring_cap);
   if (e == cudaSuccess) e = cudaMalloc(&R.dring, sizeof(tsqr::ResTask) * R.dring_cap);
   if (e == cudaSuccess) e = cudaMalloc(&R.items, sizeof(tsqr::ResItemDev) * kResSlots);
   if (e == cudaSuccess) e = cudaHostAlloc(&R.hdone, sizeof(int32_t) * kResSlots, cudaHostAllocMapped);

@@ -285,17 +285,22 @@ cudaError_t launch_refine_batch(const RefineParams &p, int ntasks, size_t smem_b
 // -------------------------------------------------------- resident persistent kernel
 // The resident server keeps one persistent kernel on the GPU and admits requests into it
 // while it runs (resident.cu, server.cu). The host appends each admitted request's chain
-// jobs to a ring in device memory and then advances `tail`, both by copies on its upload
-// stream (the copy of `tail` lands after the entries and tables it publishes). CTAs claim
-// entries by compare-and-swap on `head`. Refinement tasks of mixed least-squares requests
+// jobs to a ring in device memory and then advances that ring's `tail`, both by copies on
+// its upload stream (the copy of `tail` lands after the entries and tables it publishes).
+// There are two host rings, one for requests of at most kResSmallChains chain jobs and one
+// for larger ones; CTAs claim from the small ring first, so a short request does not wait
+// behind the chain jobs of a long one. CTAs claim entries by compare-and-swap on `head`.
+// Refinement tasks of mixed least-squares requests
 // are produced on the device: the CTA that finishes a request's factorization (or a step
 // of its refinement) reserves entries of a second ring (`dtail`), fills them and releases
 // each with its sequence number. A CTA with nothing to claim polls (bounded); when it has
 // seen no work for a while and no CTA is busy, it sets `quit` and the whole kernel ends;
 // the host launches it again when work arrives. Completion is written to mapped host
 // memory: the request's status, then its admission sequence number.
+constexpr int kResSmallChains = 8;  // requests of at most this many chain jobs: ring 0
+
 struct ResCtl {
-  unsigned long long head, tail;    // host ring: next entry to claim, entries published
+  unsigned long long head[2], tail[2];  // host rings: next entry to claim, entries published
   unsigned long long dhead, dtail;  // device ring: next entry to claim, entries reserved
   int32_t busy;                     // CTAs running a claimed job
   int32_t quit;                     // set by a CTA to end the launch (reset by the host)
@@ -326,7 +331,7 @@ struct ResItemDev {  // one admitted request, in the slot table (device memory)
 
 struct ResParams {
   ResCtl *ctl;
-  const ResEntry *ring;
+  const ResEntry *ring;      // host ring c at ring + c * (ring_mask + 1), c = 0 (small), 1
   ResTask *dring;
   const ResItemDev *items;
   int32_t *hstatus, *hdone;  // mapped host memory, one word per slot

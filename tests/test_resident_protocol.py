@@ -1,7 +1,8 @@
 """Host model of the resident server's work protocol (the kernel k_resident and the worker
-that feeds it). The worker writes an admitted request's chain entries into the host ring
-and only then advances `tail`; a CTA claims an entry by compare-and-swap on `head` (device
-ring first, by compare-and-swap on `dhead`) after reading `tail`, and runs the job while
+that feeds it). The worker writes an admitted request's chain entries into one of two host
+rings (short requests, of few chain jobs, into ring 0) and only then advances that ring's
+`tail`; a CTA claims an entry by compare-and-swap on `head` (device ring first, by
+compare-and-swap on `dhead`, then ring 0, then ring 1) after reading `tail`, and runs the job while
 counted `busy`. The job that ends a request's factorization, or the last task of a
 refinement step, reserves the next step's tasks on the device ring (`dtail`) and releases
 each entry afterwards; a claimer waits for the release. A CTA that finds nothing to claim
@@ -21,11 +22,14 @@ import random
 import pytest
 
 
+SMALL = 3  # requests of at most this many chain jobs go to ring 0
+
+
 class State:
     def __init__(self, reqs):
-        self.ring = []          # host ring entries (req, chain); None until written
-        self.tail = 0
-        self.head = 0
+        self.ring = [[], []]    # host rings: entries (req, chain); None until written
+        self.tail = [0, 0]
+        self.head = [0, 0]
         self.dring = []         # device ring: (req, step, task) once released, None while reserved
         self.dhead = 0
         self.busy = 0
@@ -62,23 +66,30 @@ def cta(st, idle_limit, mistakes):
             yield from run_task(st, *entry)
             empty = 0
             continue
-        limit = len(st.ring) if "read_before_tail" in mistakes else st.tail
-        if st.head < limit:
-            idx = st.head
+        claimed = False
+        for c in (0, 1):
+            limit = len(st.ring[c]) if "read_before_tail" in mistakes else st.tail[c]
+            if st.head[c] >= limit:
+                continue
+            idx = st.head[c]
             if "nonatomic_claim" in mistakes:
                 yield
-            st.head = idx + 1
+            st.head[c] = idx + 1
             st.busy += 1
-            entry = st.ring[idx]
+            entry = st.ring[c][idx]
+            claimed = True
             if entry is None:
                 st.errors.append("host-ring entry read before it was written")
                 st.busy -= 1
-                continue
+                break
             yield from run_chain(st, *entry)
             empty = 0
+            break
+        if claimed:
             continue
         empty += 1
-        if empty >= idle_limit and st.busy == 0 and st.dhead == len(st.dring) and st.head == st.tail:
+        if (empty >= idle_limit and st.busy == 0 and st.dhead == len(st.dring) and st.head[0] == st.tail[0]
+                and st.head[1] == st.tail[1]):
             st.quit = True
             return
         yield
@@ -135,18 +146,19 @@ def run(nreq=12, ctas=6, idle_limit=3, mistakes=(), seed=0, max_ticks=200_000):
     launches = 0
     progs = []
     for _ in range(max_ticks):
-        # the worker: write a request's entries one per tick, then advance tail
+        # the worker: write a request's entries one per tick, then advance its ring's tail
         if writing:
-            i, entry = writing.pop(0)
-            st.ring[i] = entry
+            c, i, entry = writing.pop(0)
+            st.ring[c][i] = entry
             if not writing:
-                st.tail = len(st.ring)
+                st.tail[c] = len(st.ring[c])
         elif pending and rng.random() < 0.05:
             r = pending.pop(0)
             admitted += 1
-            for c in range(reqs[r]["chains"]):
-                st.ring.append(None)
-                writing.append((len(st.ring) - 1, (r, c)))
+            c = 0 if reqs[r]["chains"] <= SMALL else 1
+            for j in range(reqs[r]["chains"]):
+                st.ring[c].append(None)
+                writing.append((c, len(st.ring[c]) - 1, (r, j)))
         # a launch whenever requests are in flight and none runs
         if not progs and len(st.done) < admitted and ("no_relaunch" not in mistakes or launches == 0):
             st.quit = False
