@@ -1,8 +1,10 @@
 // The resident persistent kernel of the resident server (sm_103a; the paper has no
 // counterpart). It runs the batched engine's jobs (k_factor_batch: FP64 and FP32 chains,
 // the wait-free reduction tree, R and X of each request) and the refinement tasks of the
-// mixed path (k_refine_batch) from two work rings, while the host appends requests to one
-// of them. The ring protocol is described with ResCtl in tsqr_internal.h.
+// mixed path (k_refine_batch) from three work rings: two the host appends requests' chain
+// jobs to while the kernel runs (short requests, long ones) and one for the refinement
+// tasks the kernel queues itself. The ring protocol is described with ResCtl in
+// tsqr_internal.h.
 //
 // Every request's tables, counters and inputs live at addresses the host reuses for later
 // requests while this kernel runs, so every such read goes through L2 (the COH builds of
@@ -12,7 +14,7 @@
 // release it (a handful of stores away) at most kSeqWaitPolls polls, then sets the timeout
 // bit of the device error word and drops the entry; the host then fails the requests in
 // flight. A CTA that finds nothing to claim sleeps between polls (2-32 us); after
-// idle_polls empty polls in a row, if no CTA is busy and both rings are empty, it ends
+// idle_polls empty polls in a row, if no CTA is busy and every ring is empty, it ends
 // the launch (quit); a CTA that has waited kIdleGiveUp polls ends it as well, whatever
 // the others are doing, so no launch outlives a stalled request by much. Ending a launch
 // loses nothing: entries not yet claimed stay in the rings for the next launch.
