@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_factor_batch(const BatchParams 
         fp.n = in.n;
         fp.nc = in.n + in.k;
         fp.ldt = chain ? in.ldt : in.ldt_tree;
-        run_job<CMAX, false>(fp, jd, smraw);
+        run_job<CMAX, true>(fp, jd, smraw);
       }
       if (bj.parent < 0) {
         __threadfence();

@@ -197,8 +197,9 @@ __device__ __forceinline__ void bar_arrive_n(int id, int count) {
 
 // EARLY_PF: the scalar warp loads the next pivot row at the start of the step (its L2
 // latency overlaps the norm and the reflector, which matters on tree nodes, where the
-// update is short) instead of after the coefficients (fewer live registers: the batched
-// kernel, at its register cap, keeps that order).
+// update is short) instead of after the coefficients (fewer live registers: the resident
+// kernel, at its register cap, keeps that order). The row is not written before step j+1,
+// so both orders load the same values and give bitwise the same results.
 //
 // COH: inputs and descriptors are read through L2 only (the resident kernel, whose inputs
 // and tables change while it runs); otherwise A goes through the read-only cache.
