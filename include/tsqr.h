@@ -483,6 +483,8 @@ tsqr_status tsqr_server_create(int64_t max_bytes, int32_t max_batch, int32_t str
  * when a launch slot frees up. FP64 and mixed requests both run inside the kernel: the
  * refinement steps of mixed least-squares requests are queued by the kernel itself. The
  * kernel ends after idle_us without work and is launched again when requests arrive.
+ * Short requests (at most 8 chain jobs) go to a ring of their own that the kernel serves
+ * first, so they do not wait behind the chain jobs of a long request.
  * Results are bitwise those of tsqr_batch_solve on the request alone (same plan, same
  * arithmetic; the compact-WY leaf of tsqr_set_mixed_wy_min_n is not used here).
  *
