@@ -119,6 +119,9 @@ def parse(argv=None):
                         "-1: the library default)")
     p.add_argument("--profile-batch", type=int, default=0, metavar="N",
                    help="only run N mixed batches of 32 served-mix requests (a small case for ncu)")
+    p.add_argument("--profile-chains", type=int, default=0, metavar="N",
+                   help="only run N batches of 304 mixed one-chain items (4,096 x n each, R only: the "
+                        "FP32 leaf chains without a tree) and report the time per column step")
     return p.parse_args(argv)
 
 
@@ -879,6 +882,23 @@ def bench_ours(args):
         rows = sum(r["m"] for r in pool)
         print(json.dumps({"profile_batch": {"requests": len(pool), "rows": rows,
                                             "phases_ms": {k: ms for k, ms in prof}}}), flush=True)
+        return 0
+
+    if args.profile_chains:
+        # one chain of 32 tiles of 128 rows per item, two CTAs per SM on every SM: the FP32
+        # column step's latency with the GPU full, with no FP64 tree above the chains
+        n, count = args.n, 2 * torch.cuda.get_device_properties(local).multi_processor_count
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(5)
+        items = [{"A": torch.randn((n, 4096), dtype=torch.float64, device="cuda", generator=gen).t(),
+                  "prec": ts.MIXED} for _ in range(count)]
+        for _ in range(args.profile_chains):
+            ts.batch_solve(items)
+        torch.cuda.synchronize()
+        _, prof = ts.profile_collect(lambda: ts.batch_solve(items))
+        ms = sum(t for k, t in prof if k == "batch")
+        print(json.dumps({"profile_chains": {"items": count, "m": 4096, "n": n, "batch_ms": ms,
+                                             "us_per_column_step": ms * 1e3 / (32 * n)}}), flush=True)
         return 0
 
     m, n = args.m, args.n
