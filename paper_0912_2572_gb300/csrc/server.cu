@@ -140,6 +140,7 @@ struct ResState {
   int32_t next_seq = 0;
   std::vector<ResLive> live;
   std::vector<int32_t> free_slots;
+  std::vector<int32_t> active;  // slots of the requests in flight (any order)
 };
 
 struct SrvSlot {
@@ -254,6 +255,12 @@ static void res_finish(tsqr_server *S, ResState &R, int32_t slot, int32_t status
   L.active = false;
   L.req.plan.reset();
   R.free_slots.push_back(slot);
+  for (size_t a = 0; a < R.active.size(); ++a)
+    if (R.active[a] == slot) {
+      R.active[a] = R.active.back();
+      R.active.pop_back();
+      break;
+    }
   S->cv_done.notify_all();
 }
 
@@ -276,8 +283,8 @@ static bool res_admit(tsqr_server *S, ResState &R) {
   const tsqr::ResidentPlan &p = *r.plan;
   const int cls = p.nchains <= tsqr::kResSmallChains ? 0 : 1;
   unsigned long long oldest = R.tail[cls];  // entries before it belong to completed requests
-  for (const ResLive &L : R.live)
-    if (L.active && L.cls == cls) oldest = std::min(oldest, L.first);
+  for (const int32_t q : R.active)
+    if (R.live[q].cls == cls) oldest = std::min(oldest, R.live[q].first);
   const int64_t need_d = (int64_t)p.ngroups * p.nt;
   if (R.free_slots.empty() || R.tail[cls] + (unsigned long long)p.nchains - oldest > R.ring_cap ||
       R.dtasks + need_d > (int64_t)R.dring_cap)
@@ -327,6 +334,7 @@ static bool res_admit(tsqr_server *S, ResState &R) {
   L.first = R.tail[cls];
   L.dtasks = need_d;
   L.active = true;
+  R.active.push_back(slot);
   R.dtasks += need_d;
   R.nlive += 1;
   R.max_live = std::max(R.max_live, R.nlive);
@@ -348,8 +356,7 @@ static void res_fail_all(tsqr_server *S, ResState &R, int32_t status) {
     R.running = false;
   }
   cudaStreamSynchronize(R.up);
-  for (int32_t q = 0; q < (int32_t)R.live.size(); ++q)
-    if (R.live[q].active) res_finish(S, R, q, status);
+  while (!R.active.empty()) res_finish(S, R, R.active.back(), status);
   cudaMemsetAsync(R.ctl, 0, sizeof(tsqr::ResCtl), R.ks);
   const int32_t zero = 0;
   cudaMemcpyAsync(R.err, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, R.ks);
@@ -379,11 +386,13 @@ static void resident_loop(tsqr_server *S) {
   for (;;) {
     bool progress = false;
     // completions: the kernel writes the status, then the request's sequence number
-    for (int32_t q = 0; q < (int32_t)R.live.size(); ++q) {
-      ResLive &L = R.live[q];
-      if (!L.active) continue;
-      if (__atomic_load_n(R.hdone + q, __ATOMIC_ACQUIRE) != L.seq) continue;
-      res_finish(S, R, q, __atomic_load_n(R.hstatus + q, __ATOMIC_ACQUIRE));
+    for (size_t a = 0; a < R.active.size();) {
+      const int32_t q = R.active[a];
+      if (__atomic_load_n(R.hdone + q, __ATOMIC_ACQUIRE) != R.live[q].seq) {
+        ++a;
+        continue;
+      }
+      res_finish(S, R, q, __atomic_load_n(R.hstatus + q, __ATOMIC_ACQUIRE));  // moves the last slot here
       progress = true;
     }
     // the launch ended (idle, or a lost entry: the error word says which)
