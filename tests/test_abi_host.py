@@ -225,6 +225,16 @@ def test_server_entry_points_reject_bad_arguments(lib):
     assert lib.tsqr_server_create(0, 16, 2, -1, 0, ctypes.byref(h)) == 1    # chain_tiles < 0
     assert lib.tsqr_server_create(0, 16, 2, 0, 3, ctypes.byref(h)) == 1     # ctas_per_sm > 2
     assert lib.tsqr_server_create(0, 16, 2, 0, 0, None) == 1
+    # the resident server: bad chain_tiles, ctas_per_sm, idle_us or output, before any CUDA call
+    assert lib.tsqr_server_create_resident(0, -1, 0, 1000, ctypes.byref(h)) == 1
+    assert lib.tsqr_server_create_resident(0, 0, 3, 1000, ctypes.byref(h)) == 1
+    assert lib.tsqr_server_create_resident(0, 0, 0, -1, ctypes.byref(h)) == 1
+    assert lib.tsqr_server_create_resident(0, 0, 0, 1000, None) == 1
+    # its ring-size test hook: powers of two from 16, or 0 for the default
+    for bad in (1, 8, 24, 100, -16):
+        assert lib.tsqr_debug_resident_ring_entries(bad) == 1
+    assert lib.tsqr_debug_resident_ring_entries(64) == 0
+    assert lib.tsqr_debug_resident_ring_entries(0) == 0
     assert not h.value
     c = ctypes.c_int32(0)
     assert lib.tsqr_server_submit(None, None, None) == 1
